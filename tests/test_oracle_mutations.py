@@ -1,0 +1,105 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that the
+independent pins catch each one. A pin that a wrong oracle also passes would
+be worthless; these tests show that the pins are sharp enough."""
+import numpy as np
+import pytest
+
+from oracle import dwf, force, gamma, wilson
+from synthetic import gauge_field, gaussian_spinor
+from tests.brute import dwf_dense, wilson_dense
+
+BC_AP = (1.0, 1.0, 1.0, -1.0)
+DIMS = (4, 2, 2, 4)
+
+
+def _wilson_brute_error():
+    U = gauge_field(DIMS, "haar", 301)
+    psi = gaussian_spinor(DIMS, 302)
+    D = wilson_dense(U, DIMS, 0.2, BC_AP)
+    out = wilson.dirac(U, psi, 0.2, BC_AP)
+    return np.abs(out.reshape(-1) - D @ psi.reshape(-1)).max()
+
+
+def test_unmutated_oracle_passes():
+    assert _wilson_brute_error() < 1e-12
+
+
+@pytest.mark.parametrize("mutation", ["swap_projectors", "drop_conj", "bc_forward_only",
+                                      "link_not_shifted", "gamma_sign"])
+def test_wilson_mutations_are_caught(monkeypatch, mutation):
+    if mutation == "swap_projectors":
+        monkeypatch.setattr(wilson, "one_minus_gamma", gamma.one_plus_gamma)
+    elif mutation == "drop_conj":
+        monkeypatch.setattr(wilson, "colour_apply_dag",
+                            lambda u, f: np.einsum("...ba,...sb->...sa", u, f))
+    elif mutation == "bc_forward_only":
+        orig = wilson.shift
+        monkeypatch.setattr(wilson, "shift",
+                            lambda f, mu, sign, bc: orig(f, mu, sign, bc if sign > 0 else (1, 1, 1, 1)))
+    elif mutation == "link_not_shifted":
+        monkeypatch.setattr(wilson.np, "roll", _roll_no_links(np.roll))
+    elif mutation == "gamma_sign":
+        g = gamma.GAMMA.copy()
+        g[2] = -g[2]
+        monkeypatch.setattr(gamma, "GAMMA", g)
+        monkeypatch.setattr(wilson, "one_minus_gamma", lambda mu: gamma.ID4 - g[mu])
+        monkeypatch.setattr(wilson, "one_plus_gamma", lambda mu: gamma.ID4 + g[mu])
+    assert _wilson_brute_error() > 1e-3
+
+
+def _roll_no_links(orig_roll):
+    def roll(a, shift, axis=None):
+        if a.ndim >= 6 and a.shape[-1] == 3 and a.shape[-2] == 3 and shift == 1:
+            return a  # the link array: forget to take U(x - mu)
+        return orig_roll(a, shift, axis=axis)
+    return roll
+
+
+def test_dwf_chirality_swap_is_caught(monkeypatch):
+    dims, Ls = (2, 2, 2, 4), 4
+    U = gauge_field(dims, "haar", 303)
+    psi = gaussian_spinor(dims, 304, lead=(Ls,))
+    D = dwf_dense(U, dims, Ls, 1.8, 0.02, BC_AP)
+    good = dwf.dirac(U, psi, 1.8, 0.02, BC_AP)
+    assert np.abs(good.reshape(-1) - D @ psi.reshape(-1)).max() < 1e-12
+    monkeypatch.setattr(dwf, "P_MINUS", gamma.P_PLUS)
+    monkeypatch.setattr(dwf, "P_PLUS", gamma.P_MINUS)
+    bad = dwf.dirac(U, psi, 1.8, 0.02, BC_AP)
+    assert np.abs(bad.reshape(-1) - D @ psi.reshape(-1)).max() > 1e-3
+
+
+@pytest.mark.parametrize("mutation", ["sign", "no_phase", "transpose"])
+def test_force_mutations_are_caught(monkeypatch, mutation):
+    """A wrong force formula fails the finite-difference pin."""
+    dims = (2, 2, 2, 4)
+    m = 0.05
+    U = gauge_field(dims, "haar", 305)
+    phi = gaussian_spinor(dims, 306)
+    if mutation == "transpose":
+        orig_outer = force._outer_spin_sum
+        monkeypatch.setattr(force, "_outer_spin_sum", lambda a, b: np.swapaxes(orig_outer(a, b), -1, -2))
+    X, _ = force.solve_normal(U, phi, m, BC_AP, tol=1e-14)
+    Y = wilson.dirac(U, X, m, BC_AP)
+    if mutation == "no_phase":
+        orig = wilson.shift
+        monkeypatch.setattr(force.wilson, "shift", lambda f, mu, s, bc: orig(f, mu, s, (1, 1, 1, 1)))
+    _, F = force.force_terms(U, X, Y, BC_AP)
+    if mutation == "sign":
+        F = -F
+    rng = np.random.default_rng(307)
+    from synthetic import random_su3_algebra
+    T = random_su3_algebra(rng, U.size // 9).reshape(U.shape)
+    analytic = np.einsum("...ab,...ba->...", T, F).sum().real
+    D0 = wilson_dense
+    eps = 1e-5
+
+    def S(u):
+        D = D0(u, dims, m, BC_AP)
+        return np.vdot(phi.reshape(-1), np.linalg.solve(D.conj().T @ D, phi.reshape(-1))).real
+
+    def ex(h, e):
+        w, v = np.linalg.eigh(h)
+        return np.einsum("...ij,...j,...kj->...ik", v, np.exp(1j * e * w), v.conj())
+
+    fd = (S(ex(T, eps) @ U) - S(ex(T, -eps) @ U)) / (2 * eps)
+    assert abs(fd - analytic) > 1e-3 * abs(fd)
