@@ -1,0 +1,460 @@
+#!/usr/bin/env python
+"""Benchmark: even-odd preconditioned Wilson CG to a 1e-10 FP64 true residual
+on a 24^3 x 48 lattice (links exp(0.3 i H), m = 0.01), FP16-storage inner
+Dslash with FP64 reliable updates, on one GB300.
+
+One step = one full solve of D_W x = b from resident FP64 inputs: link
+preparation (FP64 and FP16 / 12-real device layouts), source preparation
+b_hat = b_e + H_eo b_o / 2c, CG on M_hat^dag M_hat with source M_hat^dag b_hat,
+reconstruction of x_o. The headline value is the Dslash throughput sustained
+inside the step: (hops in the step) x 1320 flop x Vh / step time. The JSON
+line also carries the FP64 and FP32-inner solve times (the mixed vs FP64
+comparison), the roofline of the dominant kernel (the FP16 hop), the oracle
+CPU baseline and the end-to-end number through host buffers.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lqcd|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Dslash GFLOP/s & HBM-roofline %; mixed vs FP64 CG time to 1e-10 residual"
+FLOP_PER_SITE = 1320
+BC = (1.0, 1.0, 1.0, -1.0)
+WORKLOAD = "wilson_eo_cg_24x24x24x48_m0.01_exp0.3_tol1e-10"
+PROFILE_JSON = os.path.join(ROOT, "profiles", "hop_f16r12_24x24x24x48.json")
+DSLASH_SOURCES = ["dslash_kernels.cuh", "lqcd_common.cuh", "dslash_launch.cuh", "dslash_f16.cu"]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["lqcd", "reference"], default="lqcd")
+    ap.add_argument("--dims", type=int, nargs=4, default=[24, 24, 24, 48])
+    ap.add_argument("--mass", type=float, default=0.01)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_inputs(dims):
+    from synthetic import config_seed, gauge_field, gaussian_spinor
+    U = gauge_field(dims, "exp", config_seed(1, 0), eps=0.3)
+    b = gaussian_spinor(dims, config_seed(1, 1), lead=(1,))
+    return U, b
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle timing
+
+def oracle_gflops(U, b, mass, napply=1):
+    """FP64 oracle M_hat^dag M_hat (4 even-odd hops) on the bench's own fields."""
+    from oracle import wilson
+    dims = (U.shape[3], U.shape[2], U.shape[1], U.shape[0])
+    vh = int(np.prod(dims)) // 2
+    be = wilson.restrict(b[0], 0)
+    t0 = time.perf_counter()
+    for _ in range(napply):
+        wilson.schur_dag_schur(U, be, mass, BC)
+    dt = time.perf_counter() - t0
+    return 4 * napply * FLOP_PER_SITE * vh / dt / 1e9, dt
+
+
+def threads_used():
+    # numpy einsum/roll in the oracle run on the calling thread
+    return 1
+
+
+# ------------------------------------------------------------------ lqcd arm
+
+def dslash_sources_hash():
+    h = hashlib.sha256()
+    for f in DSLASH_SOURCES:
+        with open(os.path.join(ROOT, "paper_1512_03487_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def run_lqcd(args, world, rank, local):
+    import torch
+
+    import paper_1512_03487_gb300 as L
+    from paper_1512_03487_gb300 import fields as F
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dims = tuple(args.dims)
+    mass = args.mass
+    U, b = make_inputs(dims)
+    V = int(np.prod(dims))
+    vh = V // 2
+    lat = L.lattice(dims, bc=BC)
+    op64 = L.operator(mass=mass, prec=L.LQCD_F64, recon=18)
+    stream = torch.cuda.current_stream()
+
+    # resident FP64 inputs in the user layout
+    U_dev = torch.from_numpy(np.ascontiguousarray(U).view(np.float64).reshape(-1)).to(dev)
+    b_dev = torch.from_numpy(np.ascontiguousarray(b).view(np.float64).reshape(-1)).to(dev)
+    g64 = F.empty(L.lqcd_gauge_bytes(lat, L.LQCD_F64, 18))
+    gs = {p: F.empty(L.lqcd_gauge_bytes(lat, p, 12)) for p in (L.LQCD_F32, L.LQCD_F16)}
+    bfull = F.empty(L.lqcd_spinor_bytes(lat, L.LQCD_F64, L.LQCD_FULL))
+    bhat = F.empty(L.lqcd_spinor_bytes(lat, L.LQCD_F64, L.LQCD_EVEN))
+    src = F.empty(L.lqcd_spinor_bytes(lat, L.LQCD_F64, L.LQCD_EVEN))
+    x = F.empty(L.lqcd_spinor_bytes(lat, L.LQCD_F64, L.LQCD_FULL))
+    tmp = F.empty(L.lqcd_operator_workspace_bytes(lat, op64, L.LQCD_EVEN))
+    prms = {p: L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=p, sloppy_recon=12 if p else 18,
+                               delta=0.1, check_interval=32) for p in (0, 1, 2)}
+    ws = F.empty(max(L.lqcd_cg_workspace_bytes(lat, op64, prms[p], L.LQCD_EVEN) for p in (0, 1, 2)))
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step(sloppy):
+        """One solve of D_W x = b from the resident FP64 inputs; returns hops executed."""
+        L.lqcd_gauge_pack(g64, L.LQCD_F64, 18, U_dev, lat)
+        gsl = g64
+        if sloppy:
+            gsl = gs[sloppy]
+            L.lqcd_gauge_pack(gsl, sloppy, 12, U_dev, lat)
+        L.lqcd_spinor_pack(bfull, L.LQCD_F64, L.LQCD_FULL, b_dev, lat)
+        L.lqcd_eo_prepare(bhat, bfull, g64, lat, op64, tmp)
+        L.lqcd_M(src, bhat, g64, lat, op64, L.LQCD_EVEN, 1, tmp)
+        info = L.lqcd_cg_solve(x, src, g64, gsl, lat, op64, prms[sloppy], L.LQCD_EVEN, ws)
+        L.lqcd_eo_reconstruct(x, bfull, g64, lat, op64, tmp)
+        return 1 + 2 + 4 * (info.iterations + info.reliable_updates) + 1, info
+
+    def timed(fn, *a):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn(*a)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    # ---- headline: FP16-inner mixed precision solve
+    for _ in range(args.warmup):
+        step(2)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = L.lqcd_launch_count()
+    total_ms, total_hops, infos = 0.0, 0, []
+    for _ in range(args.steps):
+        ms, (hops, info) = timed(step, 2)
+        total_ms += ms
+        total_hops += hops
+        infos.append(info)
+    launches = L.lqcd_launch_count() - launches0
+    clk = clocks.stop()
+    barrier(world)
+    max_ms = allreduce_max(total_ms, world)
+    flops_all = allreduce_sum(float(total_hops) * FLOP_PER_SITE * vh, world)
+    value = flops_all / (max_ms * 1e-3) / 1e9
+
+    # the solve must meet the FP64 true residual of the full system (checked on the device result)
+    res = full_residual(L, F, lat, op64, g64, x, b_dev, tmp)
+
+    # ---- mixed vs FP64 comparison (one timed solve each after one warm-up)
+    cgcmp = {}
+    for name, p in (("fp64", 0), ("mixed_fp32", 1), ("mixed_fp16", 2)):
+        if p != 2:
+            step(p)
+        ms, (hops, info) = timed(step, p)
+        cgcmp[name] = {"ms": round(ms, 3), "iterations": info.iterations,
+                       "reliable_updates": info.reliable_updates,
+                       "true_rel_residual_normal_eq": info.true_rel_residual,
+                       "dslash_gflops": round(hops * FLOP_PER_SITE * vh / (ms * 1e-3) / 1e9, 1)}
+    cgcmp["speedup_fp16_vs_fp64"] = round(cgcmp["fp64"]["ms"] / cgcmp["mixed_fp16"]["ms"], 2)
+    cgcmp["speedup_fp32_vs_fp64"] = round(cgcmp["fp64"]["ms"] / cgcmp["mixed_fp32"]["ms"], 2)
+
+    # ---- roofline of the dominant kernel: FP16 hop, 12-real links, one checkerboard
+    roof = hop_roofline(L, F, lat, gs[2], flush, stream, vh)
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(L, F, lat, op64, U, b, prms[2], ws, tmp, x, gs[2], g64, bfull, bhat, src, flush,
+                      stream, vh, args, world)
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "GFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 arithmetic on f16 storage, f64 reliable updates",
+        "data": "synthetic (seeded exp(0.3 i H) links, Gaussian source)",
+        "config": {"workload": WORKLOAD, "lattice": list(dims), "mass": mass, "bc": list(BC),
+                   "solver": "even-odd CG on M_hat^dag M_hat, FP16+norm / 12-real inner, delta 0.1",
+                   "tol": 1e-10, "l2": "flushed (512 MB write) before every timed step",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "full_system_rel_residual": res,
+        "iterations_per_step": infos[-1].iterations, "reliable_updates_per_step": infos[-1].reliable_updates,
+        "cg": cgcmp,
+        "roofline": roof,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        gf, dt = oracle_gflops(U, b, mass, 1)
+        line["cpu_baseline"] = {"value": round(gf, 4), "unit": "GFLOP/s", "cores": threads_used(),
+                                "kind": "oracle",
+                                "sample": f"one M_hat^dag M_hat application (4 even-odd hops) of the FP64 numpy "
+                                          f"oracle on the same {dims} fields, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def full_residual(L, F, lat, op64, g64, x, b_dev, tmp):
+    """||b - D_W x|| / ||b|| of the step's result, computed with the FP64 operator
+    and compared in the host layout (padding sites never enter)."""
+    import torch
+    dx = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
+    L.lqcd_M(dx, x, g64, lat, op64, L.LQCD_FULL, 0, None)
+    a = torch.empty_like(b_dev)
+    L.lqcd_spinor_unpack(a, dx, L.LQCD_F64, L.LQCD_FULL, lat)
+    return float(torch.linalg.vector_norm(a - b_dev) / torch.linalg.vector_norm(b_dev))
+
+
+def hop_roofline(L, F, lat, g16, flush, stream, vh, launches=20):
+    import torch
+    op = L.operator(prec=L.LQCD_F16, recon=12)
+    rng = np.random.default_rng(5)
+    shape = F.host_spinor_shape(lat, L.LQCD_ODD)
+    host = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    fin = F.spinor_to_device(host, lat, L.LQCD_F16, L.LQCD_ODD)
+    out = F.empty(L.lqcd_spinor_bytes(lat, L.LQCD_F16, L.LQCD_EVEN))
+    for _ in range(3):
+        L.lqcd_dslash(out, fin, g16, lat, op, L.LQCD_EVEN, 0)
+    times = []
+    for _ in range(launches):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.lqcd_dslash(out, fin, g16, lat, op, L.LQCD_EVEN, 0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    t = float(np.mean(times)) * 1e-3
+    bytes_per_site = 8 * 24 + 52 + 52  # 8 links (12 halves) + input and output FP16 spinor with norm
+    achieved = bytes_per_site * vh / t / 1e9
+    peak, peak_src = measured_peak()
+    traffic = None
+    try:
+        with open(PROFILE_JSON) as fh:
+            prof = json.load(fh)
+        if prof.get("source_hash") == dslash_sources_hash() and list(prof.get("lattice", [])) == list(lat.dims):
+            traffic = prof.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return {"bound": "hbm", "kernel": "hop_kernel<F16, recon 12> (one checkerboard, cold L2)",
+            "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "peak_source": peak_src, "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_site * vh,
+            "launch_us": round(t * 1e6, 2), "gflops": round(FLOP_PER_SITE * vh / t / 1e9, 1)}
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback 6.8 TB/s (of fallback)"
+
+
+def run_e2e(L, F, lat, op64, U, b, prm, ws, tmp, x, g16, g64, bfull, bhat, src, flush, stream, vh, args, world):
+    """Same solve through the C ABI from pinned host buffers: H2D of the FP64
+    gauge field and source, pack, solve, reconstruct, D2H of the solution."""
+    import torch
+    U_h = torch.from_numpy(np.ascontiguousarray(U).view(np.float64).reshape(-1)).pin_memory()
+    b_h = torch.from_numpy(np.ascontiguousarray(b).view(np.float64).reshape(-1)).pin_memory()
+    x_h = torch.empty(b_h.numel(), dtype=torch.float64).pin_memory()
+    staging = torch.empty(U_h.numel(), dtype=torch.float64, device=bfull.device)
+
+    def e2e_step():
+        L.lqcd_gauge_upload(g64, L.LQCD_F64, 18, U_h, staging, lat)
+        L.lqcd_gauge_pack(g16, L.LQCD_F16, 12, staging, lat)
+        L.lqcd_spinor_upload(bfull, L.LQCD_F64, L.LQCD_FULL, b_h, staging, lat)
+        L.lqcd_eo_prepare(bhat, bfull, g64, lat, op64, tmp)
+        L.lqcd_M(src, bhat, g64, lat, op64, L.LQCD_EVEN, 1, tmp)
+        info = L.lqcd_cg_solve(x, src, g64, g16, lat, op64, prm, L.LQCD_EVEN, ws)
+        L.lqcd_eo_reconstruct(x, bfull, g64, lat, op64, tmp)
+        L.lqcd_spinor_download(x_h, x, L.LQCD_F64, L.LQCD_FULL, staging, lat)
+        return 1 + 2 + 4 * (info.iterations + info.reliable_updates) + 1
+
+    for _ in range(max(1, args.warmup // 2)):
+        e2e_step()
+    total, hops = 0.0, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hops += e2e_step()
+        torch.cuda.synchronize()
+        total += time.perf_counter() - t0
+    total = allreduce_max(total, world)
+    flops = allreduce_sum(float(hops) * FLOP_PER_SITE * vh, world)
+    return {"value": round(flops / total / 1e9, 1), "unit": "GFLOP/s",
+            "h2d_bytes_per_step": int(U_h.numel() * 8 + b_h.numel() * 8),
+            "d2h_bytes_per_step": int(x_h.numel() * 8), "ms_per_step": round(total / args.steps * 1e3, 3)}
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args, world, rank):
+    """The FP64 numpy oracle, as it stands, timed on the host cores on the same
+    workload and metric; each step is a bounded sample (one M_hat application,
+    two even-odd hops)."""
+    if rank != 0:
+        return
+    from oracle import wilson
+    dims = tuple(args.dims)
+    U, b = make_inputs(dims)
+    vh = int(np.prod(dims)) // 2
+    be = wilson.restrict(b[0], 0)
+    for _ in range(args.warmup):
+        wilson.schur(U, be, args.mass, BC)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        wilson.schur(U, be, args.mass, BC)
+    dt = time.perf_counter() - t0
+    value = 2 * args.steps * FLOP_PER_SITE * vh / dt / 1e9
+    line = {"metric": METRIC, "value": round(value, 4), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": list(dims), "mass": args.mass},
+            "impl": "reference",
+            "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": threads_used(),
+                             "kind": "oracle",
+                             "sample": "per step one M_hat application (2 even-odd hops) of the FP64 numpy oracle"},
+            "e2e": {"value": round(value, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ distributed plumbing
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(v, world):
+    return _allreduce(v, world, "max")
+
+
+def allreduce_sum(v, world):
+    return _allreduce(v, world, "sum")
+
+
+def _allreduce(v, world, op):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    run_lqcd(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

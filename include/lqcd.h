@@ -1,0 +1,251 @@
+/*
+ * lqcd.h -- C ABI of the GB300 lattice-QCD fermion library.
+ *
+ * The library applies the Wilson-Dirac operator and its five-dimensional
+ * domain-wall variant (the operators the Grid paper, arXiv:1512.03487,
+ * benchmarks in Sec. 3 and lists in Sec. 4), solves M^dag M x = b by
+ * even-odd preconditioned conjugate gradient in FP64 or in mixed precision
+ * with FP64 reliable updates, and computes the pseudofermion force.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every call returns an int status: LQCD_OK (0) or a negative LQCD_ERR_*
+ *    code. lqcd_last_error() gives a thread-local message for the last error.
+ *  - Pointers named *_dev are device pointers (cudaMalloc / torch memory)
+ *    borrowed for the duration of the call; the caller owns them. Host
+ *    pointers (named *_host) are read or written before the call returns
+ *    when the call synchronises, otherwise they must stay valid until the
+ *    stream reaches the copy. Nothing is allocated on the device by the
+ *    library except where a call says so; scratch space is passed in as a
+ *    workspace of the size a *_workspace_bytes() query returns.
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream. Calls enqueue work on it and return without synchronising
+ *    unless stated (the solvers synchronise; they return iteration counts).
+ *  - Gamma matrices (chiral basis): gamma_k = [[0, -i sigma_k], [i sigma_k, 0]]
+ *    for k = x, y, z, gamma_t = [[0, 1], [1, 0]], gamma_5 = diag(1, 1, -1, -1).
+ *
+ * Layouts
+ * -------
+ *  Host ("user") layout, complex FP64 as interleaved (re, im) doubles:
+ *    gauge   U[t][z][y][x][mu][row][col]                       (mu = x, y, z, t)
+ *    spinor  psi[i5][t][z][y][x][spin][colour]                  (subset LQCD_FULL)
+ *            psi[i5][t][z][y][x/2][spin][colour]                (LQCD_EVEN / LQCD_ODD:
+ *                                                                sites of one parity in
+ *                                                                lexicographic order)
+ *    i5 runs over the inner extent n5 (L_s of a domain-wall field, or the
+ *    right-hand sides of a multi-RHS field).
+ *  Device layout (opaque to callers; produced by the pack calls): one
+ *    checkerboard (parity) at a time, structure-of-arrays, site fastest so
+ *    that consecutive threads touch consecutive addresses:
+ *      spinor  chunk c of site j at chunk_base + c * stride + j, site
+ *              j = cb * n5 + i5 (i5 fastest), stride = n_sites rounded up to 32.
+ *              FP64: 12 chunks of double2; FP32: 6 chunks of float4;
+ *              FP16: 3 chunks of 8 halves followed by one float norm per site
+ *              (value = half * norm, norm = max |component| of the site).
+ *              A LQCD_FULL field is the even checkerboard followed by the odd.
+ *      gauge   [parity][mu][chunk][cb]; 18-real links store the full 3x3
+ *              matrix, 12-real links store rows 0 and 1 and rebuild
+ *              row 2 = conj(row0 x row1) (exact for SU(3)).
+ */
+#ifndef LQCD_H
+#define LQCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define LQCD_OK                 0
+#define LQCD_ERR_ARG           -1  /* invalid argument (size, alignment, enum) */
+#define LQCD_ERR_CUDA          -2  /* a CUDA runtime call failed */
+#define LQCD_ERR_NOT_CONVERGED -3  /* solver hit maxiter above the tolerance */
+#define LQCD_ERR_NAN           -4  /* a reduction produced NaN / Inf / a non-positive p^dag A p */
+#define LQCD_ERR_TIMEOUT       -5  /* solver exceeded its wall-clock limit */
+#define LQCD_ERR_UNSUPPORTED   -6  /* valid but not implemented combination */
+#define LQCD_ERR_WORKSPACE     -7  /* workspace too small */
+
+/* ---------------------------------------------------------------- enums */
+#define LQCD_F64 0   /* storage precision: FP64, FP64 arithmetic */
+#define LQCD_F32 1   /* FP32 storage, FP32 arithmetic */
+#define LQCD_F16 2   /* FP16 storage (+ FP32 norm per spinor site), FP32 arithmetic */
+
+#define LQCD_EVEN 0  /* field subset: even checkerboard */
+#define LQCD_ODD  1  /* odd checkerboard */
+#define LQCD_FULL 2  /* both checkerboards */
+
+#define LQCD_WILSON 0
+#define LQCD_DWF    1
+
+#define LQCD_FORCE_TA   0  /* traceless Hermitian F, dS = eps tr(T F) for U -> exp(i eps T) U */
+#define LQCD_FORCE_GRAD 1  /* conjugate-Wirtinger gradient G, dS = Re sum conj(dU) G */
+
+/* ---------------------------------------------------------------- structs */
+
+/* Lattice geometry (Grid paper, Sec. 2.4: a Grid object describes a 4D or 5D,
+ * possibly single-checkerboard, Cartesian lattice). */
+typedef struct {
+    int dims[4];     /* Lx, Ly, Lz, Lt; every extent >= 2, Lx even */
+    int n5;          /* inner extent: L_s (domain wall) or number of RHS; >= 1 */
+    double bc[4];    /* boundary phase per direction, +1 (periodic) or -1 */
+} lqcd_lattice;
+
+/* Operator parameters. Wilson: D_W = (4 + mass) - H/2. Domain wall (Shamir):
+ * D_DW = (5 - M5) - P_- S_up - P_+ S_down - H/2 with mf corners. */
+typedef struct {
+    int kind;        /* LQCD_WILSON or LQCD_DWF */
+    double mass;     /* Wilson bare mass m */
+    double M5;       /* domain-wall height */
+    double mf;       /* domain-wall quark mass */
+    int prec;        /* storage precision of the gauge field and spinors */
+    int recon;       /* 18 or 12 reals per stored link */
+} lqcd_operator;
+
+typedef struct {
+    double tol;            /* target true relative residual ||b - A x|| / ||b|| (per RHS) */
+    int maxiter;           /* iteration cap (>= 1) */
+    int sloppy_prec;       /* LQCD_F64: plain FP64 CG; LQCD_F32 / LQCD_F16: mixed precision */
+    int sloppy_recon;      /* 18 or 12: link format of gauge_sloppy */
+    double delta;          /* reliable-update threshold on ||r|| / max ||r|| (e.g. 0.1) */
+    int check_interval;    /* iterations per captured chunk between host checks (0 = 16) */
+    int use_graph;         /* 1: replay chunks as a captured CUDA graph; 0: plain launches */
+    double timeout_ms;     /* wall-clock limit; 0 = none */
+} lqcd_solver_params;
+
+typedef struct {
+    int iterations;           /* inner iterations executed */
+    int reliable_updates;     /* FP64 residual recomputations (including the final check) */
+    double true_rel_residual; /* max over RHS of ||b - A x|| / ||b|| in FP64 at exit */
+    double time_ms;           /* wall time of the solve */
+    int status;               /* same as the return value */
+} lqcd_solve_info;
+
+/* ---------------------------------------------------------------- library */
+
+/* Version string of the library. */
+const char* lqcd_version(void);
+/* Message describing the last error on this host thread ("" if none). */
+const char* lqcd_last_error(void);
+/* Number of kernel launches issued by this library in this process (graph
+ * replays count every kernel node they run). */
+uint64_t lqcd_launch_count(void);
+
+/* ---------------------------------------------------------------- sizes */
+
+/* Bytes of a device spinor field (Sec. 2.4 layout transformation: SoA,
+ * site fastest). subset: LQCD_EVEN / LQCD_ODD / LQCD_FULL. 0 on bad input. */
+size_t lqcd_spinor_bytes(const lqcd_lattice* lat, int prec, int subset);
+/* Bytes of a device gauge field (4 directions, both parities). */
+size_t lqcd_gauge_bytes(const lqcd_lattice* lat, int prec, int recon);
+
+/* ---------------------------------------------------------------- layout */
+
+/* Convert a spinor in the host layout (already in device memory, src_dev,
+ * complex FP64) into the device layout dst_dev of precision prec. FP16
+ * rounds each site to the nearest half after scaling by the site norm. */
+int lqcd_spinor_pack(void* dst_dev, int prec, int subset, const double* src_dev,
+                     const lqcd_lattice* lat, void* stream);
+/* Inverse of lqcd_spinor_pack (widening to FP64). */
+int lqcd_spinor_unpack(double* dst_dev, const void* src_dev, int prec, int subset,
+                       const lqcd_lattice* lat, void* stream);
+/* Convert a host-layout FP64 gauge field in device memory to the device
+ * layout with prec and recon (12: rows 0, 1 only). */
+int lqcd_gauge_pack(void* dst_dev, int prec, int recon, const double* src_dev,
+                    const lqcd_lattice* lat, void* stream);
+/* Inverse of lqcd_gauge_pack (12-real links are rebuilt). */
+int lqcd_gauge_unpack(double* dst_dev, const void* src_dev, int prec, int recon,
+                      const lqcd_lattice* lat, void* stream);
+/* Host-pointer variants: copy src_host into the device staging buffer
+ * staging_dev (at least the host-layout size: 24 doubles per spinor site,
+ * 72 per gauge site) with cudaMemcpyAsync, then pack. Unpack variants pack
+ * into staging_dev and copy back to dst_host; they synchronise the stream. */
+int lqcd_spinor_upload(void* dst_dev, int prec, int subset, const double* src_host,
+                       double* staging_dev, const lqcd_lattice* lat, void* stream);
+int lqcd_spinor_download(double* dst_host, const void* src_dev, int prec, int subset,
+                         double* staging_dev, const lqcd_lattice* lat, void* stream);
+int lqcd_gauge_upload(void* dst_dev, int prec, int recon, const double* src_host,
+                      double* staging_dev, const lqcd_lattice* lat, void* stream);
+
+/* ---------------------------------------------------------------- operators */
+
+/* Hopping term (Grid paper Sec. 2.6 stencil: spin-project, SU(3) x
+ * half-spinor, reconstruct, accumulate; Sec. 3 "Wilson kernel"):
+ *   out(x) = sum_mu (1 - gamma_mu) U_mu(x) in(x+mu) + (1 + gamma_mu) U_mu(x-mu)^dag in(x-mu)
+ * (dagger = 1 swaps 1 -+ gamma). out_subset LQCD_EVEN / LQCD_ODD: out lives
+ * on that checkerboard and in on the other; LQCD_FULL: both are full fields.
+ * With n5 > 1 the same links act on every i5 (the "L_s replicated Wilson
+ * dslash" of Sec. 3, Table 4; also multi-RHS). gauge_dev and the spinors
+ * share op->prec; op->recon selects the link format. out and in must not
+ * alias. */
+int lqcd_dslash(void* out_dev, const void* in_dev, const void* gauge_dev,
+                const lqcd_lattice* lat, const lqcd_operator* op,
+                int out_subset, int dagger, void* stream);
+
+/* Dirac operator. subset LQCD_FULL: out = D in (D_W or D_DW). subset
+ * LQCD_EVEN: out = M_hat in, the even-odd Schur complement
+ *   Wilson  M_hat = (4 + m) - H_eo H_oe / (4 (4 + m))
+ *   DWF     M_hat = M5op - H_eo M5op^-1 H_oe / 4
+ * with dagger giving the adjoint. tmp_dev: workspace of
+ * lqcd_operator_workspace_bytes() bytes. */
+int lqcd_M(void* out_dev, const void* in_dev, const void* gauge_dev,
+           const lqcd_lattice* lat, const lqcd_operator* op, int subset, int dagger,
+           void* tmp_dev, void* stream);
+/* out = M^dag M in (subset FULL) or M_hat^dag M_hat in (subset EVEN). */
+int lqcd_MdagM(void* out_dev, const void* in_dev, const void* gauge_dev,
+               const lqcd_lattice* lat, const lqcd_operator* op, int subset,
+               void* tmp_dev, void* stream);
+size_t lqcd_operator_workspace_bytes(const lqcd_lattice* lat, const lqcd_operator* op, int subset);
+
+/* Even-odd helpers (FP64 fields, op->prec must be LQCD_F64):
+ *   b_hat_e = b_e + H_eo A_oo^-1 b_o / 2            (prepare)
+ *   x_o     = A_oo^-1 (b_o + H_oe x_e / 2)          (reconstruct, writes the
+ *                                                    odd half of x_full)
+ * with A_oo = 4 + m (Wilson) or M5op (DWF). b_full / x_full are LQCD_FULL. */
+int lqcd_eo_prepare(void* bhat_even_dev, const void* b_full_dev, const void* gauge_dev,
+                    const lqcd_lattice* lat, const lqcd_operator* op, void* tmp_dev, void* stream);
+int lqcd_eo_reconstruct(void* x_full_dev, const void* b_full_dev, const void* gauge_dev,
+                        const lqcd_lattice* lat, const lqcd_operator* op, void* tmp_dev, void* stream);
+
+/* ---------------------------------------------------------------- solvers */
+
+/* Conjugate gradient (Grid paper Sec. 4 lists CG) for A x = b with
+ * A = M^dag M (subset LQCD_FULL) or M_hat^dag M_hat (subset LQCD_EVEN), x0 = 0.
+ * x_dev, b_dev: FP64 fields (op->prec == LQCD_F64) of that subset.
+ * gauge_dev: FP64 gauge in op->recon. gauge_sloppy_dev: gauge in
+ * (params->sloppy_prec, params->sloppy_recon), used by the inner iteration;
+ * may equal gauge_dev when sloppy_prec is LQCD_F64. With a Wilson operator
+ * and n5 > 1 every i5 is an independent system (multi-RHS, own scalars,
+ * shared link loads); with a domain-wall operator n5 = L_s is one system.
+ * Mixed precision: the iteration runs in the sloppy format; x accumulates
+ * in FP64; whenever ||r|| falls below delta times its maximum since the last
+ * update, or below tol, r = b - A x is recomputed in FP64. Exit only when
+ * every system's FP64 true residual is <= tol. Synchronises the stream.
+ * workspace_dev: lqcd_cg_workspace_bytes() bytes, 256-byte aligned. */
+size_t lqcd_cg_workspace_bytes(const lqcd_lattice* lat, const lqcd_operator* op,
+                               const lqcd_solver_params* params, int subset);
+int lqcd_cg_solve(void* x_dev, const void* b_dev, const void* gauge_dev,
+                  const void* gauge_sloppy_dev, const lqcd_lattice* lat,
+                  const lqcd_operator* op, const lqcd_solver_params* params, int subset,
+                  lqcd_solve_info* info, void* workspace_dev, size_t workspace_bytes,
+                  void* stream);
+
+/* ---------------------------------------------------------------- force */
+
+/* Pseudofermion force for S = phi^dag (M^dag M)^-1 phi with M = D_W (Grid
+ * paper Sec. 4 lists HMC; formula is the textbook derivative):
+ *   X = (M^dag M)^-1 phi, Y = M X (FP64 LQCD_FULL fields, n5 == 1),
+ *   A = sum_spin X(x+mu) ((1 - gamma_mu) Y(x))^dag,
+ *   B = sum_spin ((1 + gamma_mu) X(x)) Y(x+mu)^dag,  both times the link's boundary phase,
+ *   kind LQCD_FORCE_GRAD: out = A^dag + B               (dS = Re sum conj(dU) out)
+ *   kind LQCD_FORCE_TA:   out = TA[i (U A - B U^dag - h.c.) / 2]  (traceless Hermitian)
+ * out_dev: FP64 gauge field in the device layout with recon 18 (unpack it
+ * with lqcd_gauge_unpack). gauge_dev: FP64, op->recon. */
+int lqcd_force(void* out_dev, const void* gauge_dev, const void* X_dev, const void* Y_dev,
+               const lqcd_lattice* lat, const lqcd_operator* op, int kind, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LQCD_H */

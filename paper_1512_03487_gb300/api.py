@@ -1,0 +1,182 @@
+"""Thin Python binding of the C ABI in ``include/lqcd.h``.
+
+Every ``lqcd_*`` function here has the name and argument order of the C entry
+point; it only marshals arguments (torch tensors -> device pointers, the
+current torch stream -> cudaStream_t) and turns a non-zero status into
+:class:`LqcdError`. All computation happens in the CUDA library. PyTorch is
+used for device memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _lib
+from ._lib import (  # noqa: F401  (re-exported constants and structs)
+    LQCD_DWF, LQCD_EVEN, LQCD_F16, LQCD_F32, LQCD_F64, LQCD_FORCE_GRAD, LQCD_FORCE_TA, LQCD_FULL,
+    LQCD_ODD, LQCD_WILSON, lqcd_lattice, lqcd_operator, lqcd_solve_info, lqcd_solver_params,
+)
+
+lib = _lib.load()
+
+
+class LqcdError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"lqcd status {status}: {message}")
+        self.status = status
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        raise LqcdError(status, lib.lqcd_last_error().decode())
+
+
+def _ptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()  # torch tensor
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream or None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+# ------------------------------------------------------------------ structs
+
+def lattice(dims: Sequence[int], n5: int = 1, bc: Sequence[float] = (1.0, 1.0, 1.0, -1.0)) -> lqcd_lattice:
+    lat = lqcd_lattice()
+    for k in range(4):
+        lat.dims[k] = int(dims[k])
+        lat.bc[k] = float(bc[k])
+    lat.n5 = int(n5)
+    return lat
+
+
+def operator(kind: int = LQCD_WILSON, mass: float = 0.0, M5: float = 1.8, mf: float = 0.02,
+             prec: int = LQCD_F64, recon: int = 18) -> lqcd_operator:
+    return lqcd_operator(kind=kind, mass=mass, M5=M5, mf=mf, prec=prec, recon=recon)
+
+
+def solver_params(tol: float = 1e-10, maxiter: int = 10000, sloppy_prec: int = LQCD_F64,
+                  sloppy_recon: int = 18, delta: float = 0.1, check_interval: int = 16,
+                  use_graph: int = 1, timeout_ms: float = 0.0) -> lqcd_solver_params:
+    return lqcd_solver_params(tol=tol, maxiter=maxiter, sloppy_prec=sloppy_prec, sloppy_recon=sloppy_recon,
+                              delta=delta, check_interval=check_interval, use_graph=use_graph,
+                              timeout_ms=timeout_ms)
+
+
+# ------------------------------------------------------------------ library
+
+def lqcd_version() -> str:
+    return lib.lqcd_version().decode()
+
+
+def lqcd_last_error() -> str:
+    return lib.lqcd_last_error().decode()
+
+
+def lqcd_launch_count() -> int:
+    return int(lib.lqcd_launch_count())
+
+
+def lqcd_spinor_bytes(lat, prec, subset) -> int:
+    return int(lib.lqcd_spinor_bytes(C.byref(lat), prec, subset))
+
+
+def lqcd_gauge_bytes(lat, prec, recon) -> int:
+    return int(lib.lqcd_gauge_bytes(C.byref(lat), prec, recon))
+
+
+def lqcd_operator_workspace_bytes(lat, op, subset) -> int:
+    return int(lib.lqcd_operator_workspace_bytes(C.byref(lat), C.byref(op), subset))
+
+
+def lqcd_cg_workspace_bytes(lat, op, params, subset) -> int:
+    return int(lib.lqcd_cg_workspace_bytes(C.byref(lat), C.byref(op), C.byref(params), subset))
+
+
+# ------------------------------------------------------------------ layout
+
+def lqcd_spinor_pack(dst, prec, subset, src, lat, stream=None):
+    _check(lib.lqcd_spinor_pack(_ptr(dst), prec, subset, _ptr(src), C.byref(lat), _stream(stream)))
+
+
+def lqcd_spinor_unpack(dst, src, prec, subset, lat, stream=None):
+    _check(lib.lqcd_spinor_unpack(_ptr(dst), _ptr(src), prec, subset, C.byref(lat), _stream(stream)))
+
+
+def lqcd_gauge_pack(dst, prec, recon, src, lat, stream=None):
+    _check(lib.lqcd_gauge_pack(_ptr(dst), prec, recon, _ptr(src), C.byref(lat), _stream(stream)))
+
+
+def lqcd_gauge_unpack(dst, src, prec, recon, lat, stream=None):
+    _check(lib.lqcd_gauge_unpack(_ptr(dst), _ptr(src), prec, recon, C.byref(lat), _stream(stream)))
+
+
+def lqcd_spinor_upload(dst, prec, subset, src_host, staging, lat, stream=None):
+    _check(lib.lqcd_spinor_upload(_ptr(dst), prec, subset, _ptr(src_host), _ptr(staging), C.byref(lat),
+                                  _stream(stream)))
+
+
+def lqcd_spinor_download(dst_host, src, prec, subset, staging, lat, stream=None):
+    _check(lib.lqcd_spinor_download(_ptr(dst_host), _ptr(src), prec, subset, _ptr(staging), C.byref(lat),
+                                    _stream(stream)))
+
+
+def lqcd_gauge_upload(dst, prec, recon, src_host, staging, lat, stream=None):
+    _check(lib.lqcd_gauge_upload(_ptr(dst), prec, recon, _ptr(src_host), _ptr(staging), C.byref(lat),
+                                 _stream(stream)))
+
+
+# ------------------------------------------------------------------ operators
+
+def lqcd_dslash(out, inp, gauge, lat, op, out_subset, dagger, stream=None):
+    _check(lib.lqcd_dslash(_ptr(out), _ptr(inp), _ptr(gauge), C.byref(lat), C.byref(op), out_subset,
+                           int(dagger), _stream(stream)))
+
+
+def lqcd_M(out, inp, gauge, lat, op, subset, dagger, tmp, stream=None):
+    _check(lib.lqcd_M(_ptr(out), _ptr(inp), _ptr(gauge), C.byref(lat), C.byref(op), subset, int(dagger),
+                      _ptr(tmp), _stream(stream)))
+
+
+def lqcd_MdagM(out, inp, gauge, lat, op, subset, tmp, stream=None):
+    _check(lib.lqcd_MdagM(_ptr(out), _ptr(inp), _ptr(gauge), C.byref(lat), C.byref(op), subset, _ptr(tmp),
+                          _stream(stream)))
+
+
+def lqcd_eo_prepare(bhat, b_full, gauge, lat, op, tmp, stream=None):
+    _check(lib.lqcd_eo_prepare(_ptr(bhat), _ptr(b_full), _ptr(gauge), C.byref(lat), C.byref(op), _ptr(tmp),
+                               _stream(stream)))
+
+
+def lqcd_eo_reconstruct(x_full, b_full, gauge, lat, op, tmp, stream=None):
+    _check(lib.lqcd_eo_reconstruct(_ptr(x_full), _ptr(b_full), _ptr(gauge), C.byref(lat), C.byref(op),
+                                   _ptr(tmp), _stream(stream)))
+
+
+def lqcd_cg_solve(x, b, gauge, gauge_sloppy, lat, op, params, subset, workspace, stream=None,
+                  raise_on_error=True) -> lqcd_solve_info:
+    info = lqcd_solve_info()
+    nbytes = workspace.numel() * workspace.element_size()
+    st = lib.lqcd_cg_solve(_ptr(x), _ptr(b), _ptr(gauge), _ptr(gauge_sloppy), C.byref(lat), C.byref(op),
+                           C.byref(params), subset, C.byref(info), _ptr(workspace), nbytes, _stream(stream))
+    if raise_on_error:
+        _check(st)
+    return info
+
+
+def lqcd_force(out, gauge, X, Y, lat, op, kind, stream=None):
+    _check(lib.lqcd_force(_ptr(out), _ptr(gauge), _ptr(X), _ptr(Y), C.byref(lat), C.byref(op), kind,
+                          _stream(stream)))

@@ -1,0 +1,535 @@
+// Conjugate gradient on M^dag M (or M_hat^dag M_hat), plain FP64 or mixed
+// precision with FP64 reliable updates.
+//
+// The Grid paper lists CG among its algorithms (Sec. 4) and relies on global
+// reductions for it (Sec. 1); the iteration is the textbook Hestenes-Stiefel
+// form. Mixed precision follows the reliable-update scheme of Sleijpen and
+// van der Vorst (1996) as used for lattice QCD by Clark et al. (2010): the
+// inner iteration runs with a sloppy (FP32 or FP16-storage) operator, x is
+// accumulated in FP64, and whenever the iterated |r| falls below delta times
+// its maximum since the last update (or below the tolerance) the residual
+// r = b - A x is recomputed with the FP64 operator.
+//
+// Every scalar (alpha, beta, the convergence and update decisions) lives on
+// the device and is produced by the last block of the reducing kernel, so an
+// iteration is a fixed sequence of launches with no host round trip:
+//   Mp = M p        (|Mp|^2 = p^dag A p reduced in the epilogue -> alpha)
+//   Ap = M^dag Mp
+//   x_s += alpha p, r_s -= alpha Ap   (|r_s|^2 -> beta, or pause)
+//   p = r_s + beta p
+// A chunk of such iterations is captured once as a CUDA graph and replayed;
+// kernels return immediately once the control block is paused, so the host
+// only looks at the control block between chunks.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "lqcd_internal.h"
+
+namespace lqcd {
+
+struct VecArgs {
+  Geom g;
+  int full;
+  int bpp;            // blocks per parity
+  double* x64;        // FP64 solution
+  const double* b64;  // FP64 source
+  double* r64;        // FP64 residual
+  const double* ax64; // FP64 A x
+  void* xs;           // sloppy-vector solution increment (VF)
+  void* rs;           // sloppy-vector residual (VF)
+  void* p;            // search direction (SF)
+  const void* ap;     // A p (SF)
+  int64_t hb64, hbv, hbs;  // bytes of one checkerboard per format
+  SysState* sys;
+  ReduceCtx red;
+  const Control* gate;
+};
+
+__device__ __forceinline__ bool vec_site(const VecArgs& a, int& parity, int64_t& j, int64_t& first) {
+  int blk = blockIdx.x;
+  parity = 0;
+  if (a.full) {
+    parity = blk >= a.bpp ? 1 : 0;
+    blk -= parity * a.bpp;
+  }
+  first = (int64_t)blk * BLAS_BLOCK;
+  j = first + threadIdx.x;
+  return j < a.g.nsites;
+}
+
+template <typename T> __device__ __forceinline__ double site_norm2(const Spinor<T>& s) {
+  T acc = T(0);
+#pragma unroll
+  for (int k = 0; k < 12; k++) acc = fma(s.v[k].r, s.v[k].r, fma(s.v[k].i, s.v[k].i, acc));
+  return (double)acc;
+}
+
+template <typename TD, typename TS> __device__ __forceinline__ void convert(const Spinor<TS>& a, Spinor<TD>& b) {
+#pragma unroll
+  for (int k = 0; k < 12; k++) b.v[k] = mk((TD)a.v[k].r, (TD)a.v[k].i);
+}
+
+#define PAR_PTR(ptr, hb) ((ptr) ? (decltype(ptr))((char*)(ptr) + parity * (hb)) : (ptr))
+
+// r = b, r_s = b, p = b, x_s = 0, x = 0; |b|^2 -> initial state
+template <int VF, int SF>
+__global__ void __launch_bounds__(BLAS_BLOCK) k_init(VecArgs a) {
+  using TV = typename PrecTraits<VF>::real;
+  using TS = typename PrecTraits<SF>::real;
+  int parity;
+  int64_t j, first;
+  double red = 0.0;
+  if (vec_site(a, parity, j, first)) {
+    Spinor<double> b;
+    SpinorIO<LQCD_F64>::load(PAR_PTR(a.b64, a.hb64), a.g.sstride, j, b);
+    SpinorIO<LQCD_F64>::store(PAR_PTR(a.r64, a.hb64), a.g.sstride, j, b);
+    Spinor<double> z;
+    zero(z);
+    SpinorIO<LQCD_F64>::store(PAR_PTR(a.x64, a.hb64), a.g.sstride, j, z);
+    Spinor<TV> bv, zv;
+    convert(b, bv);
+    zero(zv);
+    SpinorIO<VF>::store(PAR_PTR(a.rs, a.hbv), a.g.sstride, j, bv);
+    SpinorIO<VF>::store(PAR_PTR(a.xs, a.hbv), a.g.sstride, j, zv);
+    Spinor<TS> bs;
+    convert(b, bs);
+    SpinorIO<SF>::store(PAR_PTR(a.p, a.hbs), a.g.sstride, j, bs);
+    red = site_norm2(b);
+  }
+  block_reduce_finalize<BLAS_BLOCK>(red, first, a.red);
+}
+
+// x_s += alpha p; r_s -= alpha Ap; |r_s|^2 -> beta or pause
+template <int VF, int SF>
+__global__ void __launch_bounds__(BLAS_BLOCK) k_update(VecArgs a) {
+  using TV = typename PrecTraits<VF>::real;
+  using TS = typename PrecTraits<SF>::real;
+  if (gate_closed(a.gate)) return;
+  int parity;
+  int64_t j, first;
+  double red = 0.0;
+  if (vec_site(a, parity, j, first)) {
+    const TV alpha = (TV)a.sys[sys_of(j, a.red.nsys)].alpha;
+    Spinor<TS> p, ap;
+    SpinorIO<SF>::load(PAR_PTR(a.p, a.hbs), a.g.sstride, j, p);
+    SpinorIO<SF>::load(PAR_PTR(a.ap, a.hbs), a.g.sstride, j, ap);
+    Spinor<TV> x, r;
+    void* xs = PAR_PTR(a.xs, a.hbv);
+    void* rs = PAR_PTR(a.rs, a.hbv);
+    SpinorIO<VF>::load(xs, a.g.sstride, j, x);
+    SpinorIO<VF>::load(rs, a.g.sstride, j, r);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      x.v[k] = mk(fma(alpha, (TV)p.v[k].r, x.v[k].r), fma(alpha, (TV)p.v[k].i, x.v[k].i));
+      r.v[k] = mk(fma(-alpha, (TV)ap.v[k].r, r.v[k].r), fma(-alpha, (TV)ap.v[k].i, r.v[k].i));
+    }
+    SpinorIO<VF>::store(xs, a.g.sstride, j, x);
+    SpinorIO<VF>::store(rs, a.g.sstride, j, r);
+    red = site_norm2(r);
+  }
+  block_reduce_finalize<BLAS_BLOCK>(red, first, a.red);
+}
+
+// p = r_s + beta p
+template <int VF, int SF>
+__global__ void __launch_bounds__(BLAS_BLOCK) k_pupdate(VecArgs a) {
+  using TV = typename PrecTraits<VF>::real;
+  using TS = typename PrecTraits<SF>::real;
+  if (gate_closed(a.gate)) return;
+  int parity;
+  int64_t j, first;
+  if (!vec_site(a, parity, j, first)) return;
+  const TS beta = (TS)a.sys[sys_of(j, a.red.nsys)].beta;
+  Spinor<TV> r;
+  SpinorIO<VF>::load(PAR_PTR(a.rs, a.hbv), a.g.sstride, j, r);
+  void* pp = PAR_PTR(a.p, a.hbs);
+  Spinor<TS> p;
+  SpinorIO<SF>::load(pp, a.g.sstride, j, p);
+#pragma unroll
+  for (int k = 0; k < 12; k++) p.v[k] = mk(fma(beta, p.v[k].r, (TS)r.v[k].r), fma(beta, p.v[k].i, (TS)r.v[k].i));
+  SpinorIO<SF>::store(pp, a.g.sstride, j, p);
+}
+
+// x += x_s (FP64); x_s = 0
+template <int VF>
+__global__ void __launch_bounds__(BLAS_BLOCK) k_accumulate(VecArgs a) {
+  using TV = typename PrecTraits<VF>::real;
+  int parity;
+  int64_t j, first;
+  if (!vec_site(a, parity, j, first)) return;
+  Spinor<double> x;
+  double* xp = PAR_PTR(a.x64, a.hb64);
+  SpinorIO<LQCD_F64>::load(xp, a.g.sstride, j, x);
+  Spinor<TV> xs, z;
+  void* xsp = PAR_PTR(a.xs, a.hbv);
+  SpinorIO<VF>::load(xsp, a.g.sstride, j, xs);
+#pragma unroll
+  for (int k = 0; k < 12; k++) x.v[k] = mk(x.v[k].r + (double)xs.v[k].r, x.v[k].i + (double)xs.v[k].i);
+  zero(z);
+  SpinorIO<LQCD_F64>::store(xp, a.g.sstride, j, x);
+  SpinorIO<VF>::store(xsp, a.g.sstride, j, z);
+}
+
+// r = b - A x (FP64), r_s = r; |r|^2 -> done flags, beta, resume
+template <int VF>
+__global__ void __launch_bounds__(BLAS_BLOCK) k_residual(VecArgs a) {
+  using TV = typename PrecTraits<VF>::real;
+  int parity;
+  int64_t j, first;
+  double red = 0.0;
+  if (vec_site(a, parity, j, first)) {
+    Spinor<double> b, ax;
+    SpinorIO<LQCD_F64>::load(PAR_PTR(a.b64, a.hb64), a.g.sstride, j, b);
+    SpinorIO<LQCD_F64>::load(PAR_PTR(a.ax64, a.hb64), a.g.sstride, j, ax);
+#pragma unroll
+    for (int k = 0; k < 12; k++) b.v[k] = b.v[k] - ax.v[k];
+    SpinorIO<LQCD_F64>::store(PAR_PTR(a.r64, a.hb64), a.g.sstride, j, b);
+    Spinor<TV> rv;
+    convert(b, rv);
+    SpinorIO<VF>::store(PAR_PTR(a.rs, a.hbv), a.g.sstride, j, rv);
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 12; k++) s = fma(b.v[k].r, b.v[k].r, fma(b.v[k].i, b.v[k].i, s));
+    red = s;
+  }
+  block_reduce_finalize<BLAS_BLOCK>(red, first, a.red);
+}
+#undef PAR_PTR
+
+// ------------------------------------------------------------------ host side
+
+struct Workspace {
+  Control* ctrl;
+  SysState* sys;
+  double* partials;
+  unsigned int* counter;
+  double* r64;
+  double* ax64;
+  double* mid64;
+  void* t1_64;
+  void* t2_64;
+  void* rs;
+  void* xs;
+  void* p;
+  void* ap;
+  void* mp;
+  void* t1_s;
+  void* t2_s;
+  size_t total;
+};
+
+static int vec_prec(int sloppy) { return sloppy == LQCD_F64 ? LQCD_F64 : LQCD_F32; }
+
+static int64_t max_blocks(const Geom& g, int subset) {
+  const int64_t per = (g.nsites + 63) / 64;  // smallest block size used by reducing kernels is >= 64
+  return subset == LQCD_FULL ? 2 * per : per;
+}
+
+static Workspace carve(void* base, const Geom& g, const lqcd_operator& op, const lqcd_solver_params& p, int subset,
+                       int nsys) {
+  Workspace w;
+  memset(&w, 0, sizeof(w));
+  size_t o = 0;
+  char* b = static_cast<char*>(base);
+  auto take = [&](size_t bytes) -> void* {
+    void* r = b ? b + o : nullptr;
+    o += round_up((int64_t)bytes, 256);
+    return r;
+  };
+  const int VF = vec_prec(p.sloppy_prec), SF = p.sloppy_prec;
+  w.ctrl = (Control*)take(sizeof(Control));
+  w.sys = (SysState*)take(sizeof(SysState) * MAX_SYS);
+  w.partials = (double*)take(sizeof(double) * nsys * max_blocks(g, subset));
+  w.counter = (unsigned int*)take(64);
+  w.r64 = (double*)take(field_bytes(g, LQCD_F64, subset));
+  w.ax64 = (double*)take(field_bytes(g, LQCD_F64, subset));
+  w.mid64 = (double*)take(field_bytes(g, LQCD_F64, subset));
+  if (subset == LQCD_EVEN) {
+    w.t1_64 = take(cb_spinor_bytes(g, LQCD_F64));
+    if (op.kind == LQCD_DWF) w.t2_64 = take(cb_spinor_bytes(g, LQCD_F64));
+  }
+  w.rs = take(field_bytes(g, VF, subset));
+  w.xs = take(field_bytes(g, VF, subset));
+  w.p = take(field_bytes(g, SF, subset));
+  w.ap = take(field_bytes(g, SF, subset));
+  w.mp = take(field_bytes(g, SF, subset));
+  if (subset == LQCD_EVEN) {
+    w.t1_s = take(cb_spinor_bytes(g, SF));
+    if (op.kind == LQCD_DWF) w.t2_s = take(cb_spinor_bytes(g, SF));
+  }
+  w.total = o;
+  return w;
+}
+
+static int validate(const lqcd_lattice* lat, const lqcd_operator* op, const lqcd_solver_params* p, int subset,
+                    Geom* g) {
+  int st = make_geom(lat, g);
+  if (st) return st;
+  if ((st = check_operator(op, *g))) return st;
+  if (!p) return fail(LQCD_ERR_ARG, "null solver params");
+  if (op->prec != LQCD_F64) return fail(LQCD_ERR_ARG, "cg: x, b and gauge must be LQCD_F64 (op->prec)");
+  if (p->sloppy_prec != LQCD_F64 && p->sloppy_prec != LQCD_F32 && p->sloppy_prec != LQCD_F16)
+    return fail(LQCD_ERR_ARG, "cg: bad sloppy precision %d", p->sloppy_prec);
+  if (p->sloppy_recon != 18 && p->sloppy_recon != 12) return fail(LQCD_ERR_ARG, "cg: bad sloppy recon");
+  if (!(p->tol > 0.0) || p->maxiter < 1) return fail(LQCD_ERR_ARG, "cg: tol must be > 0 and maxiter >= 1");
+  if (p->delta < 0.0 || p->delta >= 1.0) return fail(LQCD_ERR_ARG, "cg: delta must be in [0, 1)");
+  if (subset != LQCD_EVEN && subset != LQCD_FULL) return fail(LQCD_ERR_ARG, "cg: subset must be EVEN or FULL");
+  return LQCD_OK;
+}
+
+// Launch helpers for the (VF, SF) instantiations.
+enum VecKernel { VK_INIT, VK_UPDATE, VK_PUPDATE, VK_ACCUM, VK_RESIDUAL };
+
+template <int VF, int SF>
+static void launch_vec_t(VecKernel k, unsigned grid, const VecArgs& a, cudaStream_t s) {
+  switch (k) {
+    case VK_INIT: k_init<VF, SF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
+    case VK_UPDATE: k_update<VF, SF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
+    case VK_PUPDATE: k_pupdate<VF, SF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
+    case VK_ACCUM: k_accumulate<VF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
+    case VK_RESIDUAL: k_residual<VF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
+  }
+}
+
+static int launch_vec(VecKernel k, int sloppy, const VecArgs& a, cudaStream_t s) {
+  const unsigned grid = (unsigned)(a.full ? 2 * a.bpp : a.bpp);
+  if (grid == 0) return LQCD_OK;
+  if (sloppy == LQCD_F64) launch_vec_t<LQCD_F64, LQCD_F64>(k, grid, a, s);
+  else if (sloppy == LQCD_F32) launch_vec_t<LQCD_F32, LQCD_F32>(k, grid, a, s);
+  else launch_vec_t<LQCD_F32, LQCD_F16>(k, grid, a, s);
+  return after_launch("cg vector kernel");
+}
+
+// Kernel launches are counted when they run: a thread capturing a graph
+// suspends counting and the replay adds the graph's node count.
+extern thread_local bool g_count_suspended;
+
+struct Solver {
+  Geom g;
+  lqcd_operator op64, ops;
+  lqcd_solver_params prm;
+  int subset, nsys;
+  Workspace w;
+  const void* gauge64;
+  const void* gauge_s;
+  VecArgs va;
+  ReduceCtx rc_alpha, rc_update, rc_reliable;
+
+  int inner_iteration(cudaStream_t s) {
+    OpCtx cs{g, ops, gauge_s};
+    int st = op_apply(cs, w.mp, w.p, subset, 0, w.t1_s, w.t2_s, &rc_alpha, w.ctrl, s);
+    if (st) return st;
+    if ((st = op_apply(cs, w.ap, w.mp, subset, 1, w.t1_s, w.t2_s, nullptr, w.ctrl, s))) return st;
+    VecArgs a = va;
+    a.red = rc_update;
+    a.gate = w.ctrl;
+    if ((st = launch_vec(VK_UPDATE, prm.sloppy_prec, a, s))) return st;
+    a.gate = w.ctrl;
+    return launch_vec(VK_PUPDATE, prm.sloppy_prec, a, s);
+  }
+
+  int reliable_update(cudaStream_t s) {
+    VecArgs a = va;
+    int st = launch_vec(VK_ACCUM, prm.sloppy_prec, a, s);
+    if (st) return st;
+    OpCtx c64{g, op64, gauge64};
+    if ((st = op_apply(c64, w.mid64, a.x64, subset, 0, w.t1_64, w.t2_64, nullptr, nullptr, s))) return st;
+    if ((st = op_apply(c64, w.ax64, w.mid64, subset, 1, w.t1_64, w.t2_64, nullptr, nullptr, s))) return st;
+    a.red = rc_reliable;
+    if ((st = launch_vec(VK_RESIDUAL, prm.sloppy_prec, a, s))) return st;
+    a.gate = w.ctrl;
+    return launch_vec(VK_PUPDATE, prm.sloppy_prec, a, s);
+  }
+};
+
+}  // namespace lqcd
+
+using namespace lqcd;
+
+extern "C" {
+
+size_t lqcd_cg_workspace_bytes(const lqcd_lattice* lat, const lqcd_operator* op, const lqcd_solver_params* p,
+                               int subset) {
+  Geom g;
+  if (validate(lat, op, p, subset, &g)) return 0;
+  const int nsys = op->kind == LQCD_WILSON ? g.n5 : 1;
+  return carve(nullptr, g, *op, *p, subset, nsys).total;
+}
+
+int lqcd_cg_solve(void* x, const void* b, const void* gauge, const void* gauge_sloppy, const lqcd_lattice* lat,
+                  const lqcd_operator* op, const lqcd_solver_params* prm, int subset, lqcd_solve_info* info,
+                  void* workspace, size_t workspace_bytes, void* stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  lqcd_solve_info local;
+  memset(&local, 0, sizeof(local));
+  lqcd_solve_info* inf = info ? info : &local;
+  memset(inf, 0, sizeof(*inf));
+  auto finish = [&](int status) {
+    inf->status = status;
+    inf->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return status;
+  };
+  Solver S;
+  int st = validate(lat, op, prm, subset, &S.g);
+  if (st) return finish(st);
+  if (!x || !b || !gauge || !workspace || ((uintptr_t)workspace & 255) || ((uintptr_t)x & 15) ||
+      ((uintptr_t)b & 15))
+    return finish(fail(LQCD_ERR_ARG, "cg: null or misaligned pointer (workspace needs 256-byte alignment)"));
+  if (!gauge_sloppy) {
+    if (prm->sloppy_prec != LQCD_F64) return finish(fail(LQCD_ERR_ARG, "cg: gauge_sloppy required"));
+    gauge_sloppy = gauge;
+  }
+  S.prm = *prm;
+  if (S.prm.check_interval <= 0) S.prm.check_interval = 16;
+  S.subset = subset;
+  S.nsys = op->kind == LQCD_WILSON ? S.g.n5 : 1;
+  S.w = carve(workspace, S.g, *op, *prm, subset, S.nsys);
+  if (workspace_bytes < S.w.total)
+    return finish(fail(LQCD_ERR_WORKSPACE, "cg: workspace %zu < %zu bytes", workspace_bytes, S.w.total));
+  S.op64 = *op;
+  S.ops = *op;
+  S.ops.prec = prm->sloppy_prec;
+  S.ops.recon = prm->sloppy_recon;
+  S.gauge64 = gauge;
+  S.gauge_s = gauge_sloppy;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  const int VF = vec_prec(prm->sloppy_prec), SF = prm->sloppy_prec;
+  VecArgs& a = S.va;
+  memset(&a, 0, sizeof(a));
+  a.g = S.g;
+  a.full = subset == LQCD_FULL;
+  a.bpp = (int)((S.g.nsites + BLAS_BLOCK - 1) / BLAS_BLOCK);
+  a.x64 = (double*)x;
+  a.b64 = (const double*)b;
+  a.r64 = S.w.r64;
+  a.ax64 = S.w.ax64;
+  a.xs = S.w.xs;
+  a.rs = S.w.rs;
+  a.p = S.w.p;
+  a.ap = S.w.ap;
+  a.hb64 = (int64_t)cb_spinor_bytes(S.g, LQCD_F64);
+  a.hbv = (int64_t)cb_spinor_bytes(S.g, VF);
+  a.hbs = (int64_t)cb_spinor_bytes(S.g, SF);
+  a.sys = S.w.sys;
+  ReduceCtx base;
+  memset(&base, 0, sizeof(base));
+  base.partials = S.w.partials;
+  base.counter = S.w.counter;
+  base.sys = S.w.sys;
+  base.ctrl = S.w.ctrl;
+  base.nsys = S.nsys;
+  ReduceCtx rc_init = base;
+  rc_init.fin = FIN_INIT;
+  rc_init.tol2_rel = prm->tol * prm->tol;
+  rc_init.delta2 = prm->sloppy_prec == LQCD_F64 ? 0.0 : prm->delta * prm->delta;
+  S.rc_alpha = base;
+  S.rc_alpha.fin = FIN_ALPHA;
+  S.rc_update = base;
+  S.rc_update.fin = FIN_UPDATE;
+  S.rc_update.maxiter = prm->maxiter;
+  S.rc_reliable = base;
+  S.rc_reliable.fin = FIN_RELIABLE;
+  a.red = base;
+
+  cudaError_t e = cudaMemsetAsync(S.w.counter, 0, 64, s);
+  if (e != cudaSuccess) return finish(cuda_fail(e, "cg: memset"));
+  {
+    VecArgs ai = a;
+    ai.red = rc_init;
+    if ((st = launch_vec(VK_INIT, prm->sloppy_prec, ai, s))) return finish(st);
+  }
+
+  // Build the chunk: check_interval inner iterations, captured as a graph.
+  const int chunk = S.prm.check_interval;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t nodes_per_chunk = 0;
+  if (prm->use_graph) {
+    cudaStream_t cap;
+    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return finish(cuda_fail(e, "cg: stream create"));
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(cap);
+      return finish(cuda_fail(e, "cg: begin capture"));
+    }
+    g_count_suspended = true;
+    for (int i = 0; i < chunk && st == LQCD_OK; i++) st = S.inner_iteration(cap);
+    g_count_suspended = false;
+    e = cudaStreamEndCapture(cap, &graph);
+    cudaStreamDestroy(cap);
+    if (st) {
+      if (graph) cudaGraphDestroy(graph);
+      return finish(st);
+    }
+    if (e != cudaSuccess) return finish(cuda_fail(e, "cg: end capture"));
+    size_t n = 0;
+    cudaGraphGetNodes(graph, nullptr, &n);
+    nodes_per_chunk = n;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return finish(cuda_fail(e, "cg: graph instantiate"));
+  }
+  auto cleanup = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+  };
+
+  Control ctrl;
+  int reliable = 0;
+  int status = LQCD_OK;
+  for (;;) {
+    e = cudaMemcpyAsync(&ctrl, S.w.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { status = cuda_fail(e, "cg: control readback"); break; }
+    if (ctrl.reason & REASON_NAN) { status = fail(LQCD_ERR_NAN, "cg: NaN/Inf or non-positive p^dag A p"); break; }
+    if (ctrl.n_done == ctrl.nsys) break;
+    if (ctrl.iter >= prm->maxiter) {
+      // final FP64 check of where the iteration stands
+      reliable++;
+      if ((st = S.reliable_update(s))) { status = st; break; }
+      e = cudaMemcpyAsync(&ctrl, S.w.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) { status = cuda_fail(e, "cg: control readback"); break; }
+      if (ctrl.n_done != ctrl.nsys) status = fail(LQCD_ERR_NOT_CONVERGED, "cg: maxiter %d reached", prm->maxiter);
+      break;
+    }
+    if (ctrl.active == 0) {
+      // paused: convergence candidate or reliable update due
+      reliable++;
+      if ((st = S.reliable_update(s))) { status = st; break; }
+      continue;
+    }
+    if (prm->timeout_ms > 0) {
+      double el = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      if (el > prm->timeout_ms) { status = fail(LQCD_ERR_TIMEOUT, "cg: timeout after %.1f ms", el); break; }
+    }
+    if (exec) {
+      e = cudaGraphLaunch(exec, s);
+      if (e != cudaSuccess) { status = cuda_fail(e, "cg: graph launch"); break; }
+      count_launches(nodes_per_chunk);
+    } else {
+      for (int i = 0; i < chunk && st == LQCD_OK; i++) st = S.inner_iteration(s);
+      if (st) { status = st; break; }
+    }
+  }
+  cleanup();
+  // report
+  std::vector<SysState> sys(S.nsys);
+  e = cudaMemcpyAsync(sys.data(), S.w.sys, sizeof(SysState) * S.nsys, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess && status == LQCD_OK) status = cuda_fail(e, "cg: state readback");
+  double worst = 0.0;
+  for (int i = 0; i < S.nsys; i++) {
+    double rel = sys[i].rr0 > 0 ? std::sqrt(sys[i].rr_true / sys[i].rr0) : 0.0;
+    if (rel > worst || std::isnan(rel)) worst = rel;
+  }
+  inf->iterations = ctrl.iter;
+  inf->reliable_updates = reliable;
+  inf->true_rel_residual = worst;
+  return finish(status);
+}
+
+}  // extern "C"

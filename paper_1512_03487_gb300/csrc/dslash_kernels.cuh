@@ -1,0 +1,250 @@
+// Fused Wilson hopping kernel (and its L_s-replicated / multi-RHS form).
+//
+//   out(x) = sum_mu (1 - gamma_mu) U_mu(x) in(x + mu) + (1 + gamma_mu) U_mu(x - mu)^dag in(x - mu)
+//
+// One thread per output site j = cb * n5 + i5 of one checkerboard. For each
+// of the 8 directions the neighbour spinor is loaded (coalesced SoA chunks),
+// spin-projected to a half spinor (the paper's Compressor, Sec. 2.6, applied
+// in registers instead of to a halo), multiplied by the SU(3) link (2 colour
+// vectors), reconstructed to 4 spins and accumulated; the result is written
+// once with streaming stores (Sec. 2.6 "streaming stores are used in the
+// final write"). With n5 > 1 the n5 threads of a 4D site read the same link
+// address, so the link bytes are fetched once per site for all i5 (the
+// paper's L_s-fold gauge reuse, Sec. 3 Fig. xc30 caption).
+//
+// Gamma basis (chiral): gamma_mu = [[0, B_mu], [B_mu^dag, 0]] with
+// B_x = -i sigma_1, B_y = -i sigma_2, B_z = -i sigma_3, B_t = 1. For
+// (1 + S gamma_mu) psi (S = +-1) the upper half is h = psi_u + S B psi_l and
+// the lower half is S B^dag h, so only h is multiplied by the link.
+#pragma once
+
+#include "lqcd_common.cuh"
+
+namespace lqcd {
+
+enum Epilogue { EPI_PLAIN = 0, EPI_XPAY = 1, EPI_M5 = 2 };
+
+struct HopArgs {
+  void* out;
+  const void* in;
+  const void* gauge;
+  const void* x;          // epilogue operand, same format and subset as out
+  Geom g;
+  int out_parity;         // single-checkerboard launch: parity of out
+  int full;               // 1: out / in / x are full fields, grid covers both parities
+  int blocks_per_parity;
+  int64_t half_bytes;     // bytes of one checkerboard of a full field
+  double a, b;            // EPI_PLAIN: out = b H in; EPI_XPAY: out = a x + b H in
+  double m5d, mf;         // EPI_M5: out = M5op(x) + b H in, M5op diagonal m5d = 5 - M5
+  ReduceCtx red;          // |out|^2 per system when reducing
+  const Control* gate;    // kernel returns at once when gate->active == 0
+};
+
+template <int MU, int S, typename T>
+__device__ __forceinline__ void project(const Spinor<T>& s, Half<T>& h) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const cpx<T> p0 = s.v[c], p1 = s.v[3 + c], p2 = s.v[6 + c], p3 = s.v[9 + c];
+    cpx<T> h0, h1;
+    if (MU == 0) {         // h0 = p0 - S i p3, h1 = p1 - S i p2
+      h0 = S > 0 ? p0 + times_mi(p3) : p0 + times_i(p3);
+      h1 = S > 0 ? p1 + times_mi(p2) : p1 + times_i(p2);
+    } else if (MU == 1) {  // h0 = p0 - S p3, h1 = p1 + S p2
+      h0 = S > 0 ? p0 - p3 : p0 + p3;
+      h1 = S > 0 ? p1 + p2 : p1 - p2;
+    } else if (MU == 2) {  // h0 = p0 - S i p2, h1 = p1 + S i p3
+      h0 = S > 0 ? p0 + times_mi(p2) : p0 + times_i(p2);
+      h1 = S > 0 ? p1 + times_i(p3) : p1 + times_mi(p3);
+    } else {               // h0 = p0 + S p2, h1 = p1 + S p3
+      h0 = S > 0 ? p0 + p2 : p0 - p2;
+      h1 = S > 0 ? p1 + p3 : p1 - p3;
+    }
+    h.v[c] = h0;
+    h.v[3 + c] = h1;
+  }
+}
+
+// acc += (upper = w, lower = S B_mu^dag w)
+template <int MU, int S, typename T>
+__device__ __forceinline__ void accumulate(Spinor<T>& acc, const Half<T>& w) {
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const cpx<T> w0 = w.v[c], w1 = w.v[3 + c];
+    acc.v[c] = acc.v[c] + w0;
+    acc.v[3 + c] = acc.v[3 + c] + w1;
+    if (MU == 0) {         // lower2 = S i w1, lower3 = S i w0
+      acc.v[6 + c] = acc.v[6 + c] + (S > 0 ? times_i(w1) : times_mi(w1));
+      acc.v[9 + c] = acc.v[9 + c] + (S > 0 ? times_i(w0) : times_mi(w0));
+    } else if (MU == 1) {  // lower2 = S w1, lower3 = -S w0
+      acc.v[6 + c] = S > 0 ? acc.v[6 + c] + w1 : acc.v[6 + c] - w1;
+      acc.v[9 + c] = S > 0 ? acc.v[9 + c] - w0 : acc.v[9 + c] + w0;
+    } else if (MU == 2) {  // lower2 = S i w0, lower3 = -S i w1
+      acc.v[6 + c] = acc.v[6 + c] + (S > 0 ? times_i(w0) : times_mi(w0));
+      acc.v[9 + c] = acc.v[9 + c] + (S > 0 ? times_mi(w1) : times_i(w1));
+    } else {               // lower2 = S w0, lower3 = S w1
+      acc.v[6 + c] = S > 0 ? acc.v[6 + c] + w0 : acc.v[6 + c] - w0;
+      acc.v[9 + c] = S > 0 ? acc.v[9 + c] + w1 : acc.v[9 + c] - w1;
+    }
+  }
+}
+
+// w_a = U h_a
+template <typename T>
+__device__ __forceinline__ void link_mul(const Link<T>& u, const Half<T>& h, Half<T>& w) {
+#pragma unroll
+  for (int a = 0; a < 2; a++)
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+      cpx<T> s = cmul(u.v[3 * r], h.v[3 * a]);
+      s = cmadd(s, u.v[3 * r + 1], h.v[3 * a + 1]);
+      s = cmadd(s, u.v[3 * r + 2], h.v[3 * a + 2]);
+      w.v[3 * a + r] = s;
+    }
+}
+
+// w_a = U^dag h_a
+template <typename T>
+__device__ __forceinline__ void link_mul_dag(const Link<T>& u, const Half<T>& h, Half<T>& w) {
+#pragma unroll
+  for (int a = 0; a < 2; a++)
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+      cpx<T> s = cmadd_conj(mk(T(0), T(0)), u.v[r], h.v[3 * a]);
+      s = cmadd_conj(s, u.v[3 + r], h.v[3 * a + 1]);
+      s = cmadd_conj(s, u.v[6 + r], h.v[3 * a + 2]);
+      w.v[3 * a + r] = s;
+    }
+}
+
+template <typename T> __device__ __forceinline__ T bc_phase(const Geom& g, int mu);
+template <> __device__ __forceinline__ double bc_phase<double>(const Geom& g, int mu) { return g.bcd[mu]; }
+template <> __device__ __forceinline__ float bc_phase<float>(const Geom& g, int mu) { return g.bcf[mu]; }
+
+template <int MU, int P, int R, bool DAG>
+__device__ __forceinline__ void hop_dir(Spinor<typename PrecTraits<P>::real>& acc, const HopArgs& A,
+                                        const Coord& x, int64_t cb, int64_t i5, int parity,
+                                        const void* in) {
+  using T = typename PrecTraits<P>::real;
+  constexpr int SF = DAG ? +1 : -1;  // forward hop carries (1 + SF gamma_mu)
+  const int64_t n5 = A.g.n5;
+  {
+    bool wrap;
+    const int64_t nb = neighbour_cb<MU>(A.g, x, +1, wrap);
+    Spinor<T> s;
+    SpinorIO<P>::load(in, A.g.sstride, nb * n5 + i5, s);
+    Half<T> h;
+    project<MU, SF>(s, h);
+    if (wrap) {
+      const T ph = bc_phase<T>(A.g, MU);
+#pragma unroll
+      for (int k = 0; k < 6; k++) h.v[k] = ph * h.v[k];
+    }
+    Link<T> u;
+    LinkIO<P, R>::load(A.gauge, A.g.gstride, parity * 4 + MU, cb, u);
+    Half<T> w;
+    link_mul(u, h, w);
+    accumulate<MU, SF>(acc, w);
+  }
+  {
+    bool wrap;
+    const int64_t nb = neighbour_cb<MU>(A.g, x, -1, wrap);
+    Spinor<T> s;
+    SpinorIO<P>::load(in, A.g.sstride, nb * n5 + i5, s);
+    Half<T> h;
+    project<MU, -SF>(s, h);
+    if (wrap) {
+      const T ph = bc_phase<T>(A.g, MU);
+#pragma unroll
+      for (int k = 0; k < 6; k++) h.v[k] = ph * h.v[k];
+    }
+    Link<T> u;
+    LinkIO<P, R>::load(A.gauge, A.g.gstride, (1 - parity) * 4 + MU, nb, u);
+    Half<T> w;
+    link_mul_dag(u, h, w);
+    accumulate<MU, -SF>(acc, w);
+  }
+}
+
+// out_chi(s) += coefficient * x_chi(s'), chirality + = spins 0,1 (k < 6), - = spins 2,3.
+template <typename T>
+__device__ __forceinline__ void add_chiral(Spinor<T>& out, const Spinor<T>& xs, T coef, bool plus) {
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    const int kk = plus ? k : 6 + k;
+    out.v[kk] = out.v[kk] + coef * xs.v[kk];
+  }
+}
+
+template <int P, int R, bool DAG, int EPI, bool RED, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) hop_kernel(const HopArgs A) {
+  using T = typename PrecTraits<P>::real;
+  using IO = SpinorIO<P>;
+  if (gate_closed(A.gate)) return;
+  int parity = A.out_parity;
+  int blk = blockIdx.x;
+  if (A.full) {
+    parity = blk >= A.blocks_per_parity ? 1 : 0;
+    blk -= parity * A.blocks_per_parity;
+  }
+  const char* in = static_cast<const char*>(A.in) + (A.full ? (1 - parity) * A.half_bytes : 0);
+  char* out = static_cast<char*>(A.out) + (A.full ? parity * A.half_bytes : 0);
+  const char* xb = A.x ? static_cast<const char*>(A.x) + (A.full ? parity * A.half_bytes : 0) : nullptr;
+  const int64_t j = (int64_t)blk * BLOCK + threadIdx.x;
+  double red = 0.0;
+  if (j < A.g.nsites) {
+    const int64_t n5 = A.g.n5;
+    int64_t cb, i5;
+    if (n5 == 1) { cb = j; i5 = 0; } else { cb = j / n5; i5 = j - cb * n5; }
+    const Coord x = cb_to_coord(A.g, cb, parity);
+    Spinor<T> acc;
+    zero(acc);
+    hop_dir<0, P, R, DAG>(acc, A, x, cb, i5, parity, in);
+    hop_dir<1, P, R, DAG>(acc, A, x, cb, i5, parity, in);
+    hop_dir<2, P, R, DAG>(acc, A, x, cb, i5, parity, in);
+    hop_dir<3, P, R, DAG>(acc, A, x, cb, i5, parity, in);
+    const T b = (T)A.b;
+    Spinor<T> res;
+    if (EPI == EPI_PLAIN) {
+#pragma unroll
+      for (int k = 0; k < 12; k++) res.v[k] = b * acc.v[k];
+    } else if (EPI == EPI_XPAY) {
+      Spinor<T> xv;
+      IO::load(xb, A.g.sstride, j, xv);
+      const T a = (T)A.a;
+#pragma unroll
+      for (int k = 0; k < 12; k++) res.v[k] = mk(fma(a, xv.v[k].r, b * acc.v[k].r), fma(a, xv.v[k].i, b * acc.v[k].i));
+    } else {
+      // M5op(x)(s) = d x(s) - P_- x(s+1) - P_+ x(s-1), mf corners (dagger swaps directions)
+      Spinor<T> xv;
+      IO::load(xb, A.g.sstride, j, xv);
+      const T d = (T)A.m5d;
+#pragma unroll
+      for (int k = 0; k < 12; k++) res.v[k] = mk(fma(d, xv.v[k].r, b * acc.v[k].r), fma(d, xv.v[k].i, b * acc.v[k].i));
+      const bool top = i5 + 1 == n5, bottom = i5 == 0;
+      const int64_t jp = top ? j - (n5 - 1) : j + 1;
+      const int64_t jm = bottom ? j + (n5 - 1) : j - 1;
+      const T cp = top ? (T)A.mf : T(-1);
+      const T cm = bottom ? (T)A.mf : T(-1);
+      Spinor<T> xp, xm;
+      IO::load(xb, A.g.sstride, jp, xp);
+      IO::load(xb, A.g.sstride, jm, xm);
+      if (!DAG) {
+        add_chiral(res, xp, cp, false);
+        add_chiral(res, xm, cm, true);
+      } else {
+        add_chiral(res, xm, cm, false);
+        add_chiral(res, xp, cp, true);
+      }
+    }
+    IO::store(out, A.g.sstride, j, res);
+    if (RED) {
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < 12; k++) s = fma(res.v[k].r, res.v[k].r, fma(res.v[k].i, res.v[k].i, s));
+      red = (double)s;
+    }
+  }
+  if (RED) block_reduce_finalize<BLOCK>(red, (int64_t)blk * BLOCK, A.red);
+}
+
+}  // namespace lqcd

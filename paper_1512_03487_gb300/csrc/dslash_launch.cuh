@@ -1,0 +1,39 @@
+// Launch dispatch for the hop kernel; included by one translation unit per
+// precision so the instantiations compile in parallel.
+#pragma once
+
+#include "lqcd_internal.h"
+
+namespace lqcd {
+
+template <int P, int R, bool DAG, int EPI, bool RED>
+static int launch_hop_inst(const HopArgs& a, cudaStream_t s) {
+  const int64_t nb = (a.g.nsites + HOP_BLOCK - 1) / HOP_BLOCK;
+  const int64_t grid = a.full ? 2 * nb : nb;
+  if (grid == 0) return LQCD_OK;
+  hop_kernel<P, R, DAG, EPI, RED, HOP_BLOCK><<<(unsigned)grid, HOP_BLOCK, 0, s>>>(a);
+  return after_launch("hop_kernel");
+}
+
+template <int P, int R, bool DAG>
+static int launch_hop_epi(int epi, bool red, const HopArgs& a, cudaStream_t s) {
+  if (epi == EPI_PLAIN) return launch_hop_inst<P, R, DAG, EPI_PLAIN, false>(a, s);
+  if (epi == EPI_XPAY)
+    return red ? launch_hop_inst<P, R, DAG, EPI_XPAY, true>(a, s) : launch_hop_inst<P, R, DAG, EPI_XPAY, false>(a, s);
+  if (epi == EPI_M5)
+    return red ? launch_hop_inst<P, R, DAG, EPI_M5, true>(a, s) : launch_hop_inst<P, R, DAG, EPI_M5, false>(a, s);
+  return fail(LQCD_ERR_ARG, "bad epilogue %d", epi);
+}
+
+template <int P>
+static int launch_hop_prec(int recon, bool dagger, int epi, bool red, HopArgs a, cudaStream_t s) {
+  a.blocks_per_parity = (int)((a.g.nsites + HOP_BLOCK - 1) / HOP_BLOCK);
+  if (epi == EPI_PLAIN && red) return fail(LQCD_ERR_UNSUPPORTED, "plain hop with reduction");
+  if (recon == 18)
+    return dagger ? launch_hop_epi<P, 18, true>(epi, red, a, s) : launch_hop_epi<P, 18, false>(epi, red, a, s);
+  if (recon == 12)
+    return dagger ? launch_hop_epi<P, 12, true>(epi, red, a, s) : launch_hop_epi<P, 12, false>(epi, red, a, s);
+  return fail(LQCD_ERR_ARG, "bad recon %d", recon);
+}
+
+}  // namespace lqcd

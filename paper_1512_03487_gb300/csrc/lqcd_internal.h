@@ -1,0 +1,52 @@
+// Host-side internal interfaces shared by the library's translation units.
+#pragma once
+
+#include "dslash_kernels.cuh"
+#include "lqcd_common.cuh"
+
+namespace lqcd {
+
+// ---- hop launchers (one translation unit per precision)
+int launch_hop(int prec, int recon, bool dagger, int epi, bool reduce, HopArgs a, cudaStream_t s);
+int launch_hop_f64(int recon, bool dagger, int epi, bool reduce, HopArgs a, cudaStream_t s);
+int launch_hop_f32(int recon, bool dagger, int epi, bool reduce, HopArgs a, cudaStream_t s);
+int launch_hop_f16(int recon, bool dagger, int epi, bool reduce, HopArgs a, cudaStream_t s);
+
+// Blocks of the hop kernel per checkerboard (the reduction buffers are sized from it).
+constexpr int HOP_BLOCK = 128;
+constexpr int BLAS_BLOCK = 128;
+constexpr int M5_BLOCK = 128;
+
+// ---- fifth-dimension inverse M5op^-1 (domain wall), out and in checkerboard fields
+struct M5Args {
+  void* out;
+  const void* in;
+  Geom g;
+  double d;    // 5 - M5
+  double mf;
+  int dagger;
+  const Control* gate;
+};
+int launch_m5inv(int prec, const M5Args& a, cudaStream_t s);
+
+// ---- operators
+struct OpCtx {
+  Geom g;
+  lqcd_operator op;   // kind, mass, M5, mf, prec, recon
+  const void* gauge;
+};
+// out = M in (subset LQCD_FULL) or M_hat in (LQCD_EVEN), dagger; optional |out|^2
+// reduction and gate. t1, t2: odd checkerboard temporaries (EVEN subset).
+int op_apply(const OpCtx& c, void* out, const void* in, int subset, int dagger,
+             void* t1, void* t2, const ReduceCtx* red, const Control* gate, cudaStream_t s);
+// Bytes of the temporaries op_apply needs (t1 + t2) for a subset.
+size_t op_tmp_bytes(const Geom& g, int kind, int prec, int subset);
+// Bytes of a field of the given subset.
+size_t field_bytes(const Geom& g, int prec, int subset);
+int check_operator(const lqcd_operator* op, const Geom& g);
+
+// Host pointer offset helper.
+inline void* off(void* p, size_t bytes) { return static_cast<char*>(p) + bytes; }
+inline const void* off(const void* p, size_t bytes) { return static_cast<const char*>(p) + bytes; }
+
+}  // namespace lqcd

@@ -12,6 +12,9 @@ seed always produces the same field. Nothing here knows about Dirac operators.
 """
 from __future__ import annotations
 
+import concurrent.futures as cf
+import os
+
 import numpy as np
 
 #: Base seed; the workload with index ``k`` uses ``BASE_SEED + k``.
@@ -38,16 +41,21 @@ def _complex_gaussian(rng: np.random.Generator, shape) -> np.ndarray:
     return re_im[..., 0] + 1j * re_im[..., 1]
 
 
-def haar_su3(rng: np.random.Generator, n: int) -> np.ndarray:
-    """``n`` Haar-distributed SU(3) matrices, shape (n, 3, 3).
+def _chunked(fn, *arrays, chunk: int = 65536):
+    """Apply ``fn`` to matching row-chunks of ``arrays`` on a thread pool and
+    concatenate. numpy's batched linear algebra releases the GIL, so chunks run
+    in parallel; the result is identical to ``fn(*arrays)``."""
+    n = arrays[0].shape[0]
+    if n <= chunk:
+        return fn(*arrays)
+    starts = range(0, n, chunk)
+    workers = max(1, min(len(starts), os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(workers) as ex:
+        parts = list(ex.map(lambda s0: fn(*(a[s0:s0 + chunk] for a in arrays)), starts))
+    return np.concatenate(parts, axis=0)
 
-    A complex Gaussian 3x3 matrix is orthonormalised column by column
-    (Gram-Schmidt, i.e. the Q of a QR decomposition whose R has a positive
-    real diagonal), which is Haar on U(3); dividing by the principal cube root
-    of the determinant maps it to SU(3) and keeps left invariance, hence the
-    Haar measure on SU(3).
-    """
-    z = _complex_gaussian(rng, (n, 3, 3))
+
+def _su3_from_gaussian(z: np.ndarray) -> np.ndarray:
     q = np.empty_like(z)
     for j in range(3):
         v = z[:, :, j].copy()
@@ -61,13 +69,29 @@ def haar_su3(rng: np.random.Generator, n: int) -> np.ndarray:
     return q
 
 
-def random_su3_algebra(rng: np.random.Generator, n: int) -> np.ndarray:
-    """``n`` random traceless Hermitian 3x3 matrices H = (A + A^dag)/2 - tr/3."""
-    a = _complex_gaussian(rng, (n, 3, 3))
+def haar_su3(rng: np.random.Generator, n: int) -> np.ndarray:
+    """``n`` Haar-distributed SU(3) matrices, shape (n, 3, 3).
+
+    A complex Gaussian 3x3 matrix is orthonormalised column by column
+    (Gram-Schmidt, i.e. the Q of a QR decomposition whose R has a positive
+    real diagonal), which is Haar on U(3); dividing by the principal cube root
+    of the determinant maps it to SU(3) and keeps left invariance, hence the
+    Haar measure on SU(3).
+    """
+    z = _complex_gaussian(rng, (n, 3, 3))
+    return _chunked(_su3_from_gaussian, z)
+
+
+def _hermitian_from_gaussian(a: np.ndarray) -> np.ndarray:
     h = 0.5 * (a + np.conj(np.swapaxes(a, 1, 2)))
     tr = np.trace(h, axis1=1, axis2=2).real / 3.0
     h -= tr[:, None, None] * np.eye(3)[None]
     return h
+
+
+def random_su3_algebra(rng: np.random.Generator, n: int) -> np.ndarray:
+    """``n`` random traceless Hermitian 3x3 matrices H = (A + A^dag)/2 - tr/3."""
+    return _hermitian_from_gaussian(_complex_gaussian(rng, (n, 3, 3)))
 
 
 def exp_i_hermitian_su3(rng: np.random.Generator, n: int, eps: float) -> np.ndarray:
@@ -78,9 +102,12 @@ def exp_i_hermitian_su3(rng: np.random.Generator, n: int, eps: float) -> np.ndar
     up to rounding.
     """
     h = random_su3_algebra(rng, n)
-    w, v = np.linalg.eigh(h)
-    phase = np.exp(1j * eps * w)
-    return np.einsum("nij,nj,nkj->nik", v, phase, v.conj())
+
+    def expo(hc):
+        w, v = np.linalg.eigh(hc)
+        return np.einsum("nij,nj,nkj->nik", v, np.exp(1j * eps * w), v.conj())
+
+    return _chunked(expo, h)
 
 
 def gauge_field(dims, kind: str, seed: int, eps: float = 0.3) -> np.ndarray:

@@ -1,0 +1,113 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+declared in include/lqcd.h, sizes are consistent, and invalid arguments are
+rejected on the host before any CUDA call."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lqcd.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lqcd_[A-Za-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1512_03487_gb300 import api as a
+    return a
+
+
+def test_header_declares_expected_entry_points():
+    names = _declared_functions()
+    for n in ("lqcd_dslash", "lqcd_M", "lqcd_MdagM", "lqcd_cg_solve", "lqcd_force", "lqcd_spinor_pack"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(api):
+    names = _declared_functions()
+    missing = [n for n in names if not hasattr(api.lib, n)]
+    assert not missing, missing
+    # and the Python binding wraps each one under the same name
+    from paper_1512_03487_gb300 import _lib
+    assert sorted(_lib.SIGNATURES) == names
+
+
+def test_version_and_counter(api):
+    assert "sm_103a" in api.lqcd_version()
+    assert api.lqcd_launch_count() >= 0
+
+
+def test_sizes(api):
+    lat = api.lattice((4, 4, 4, 4))
+    vh = 128
+    assert api.lqcd_spinor_bytes(lat, api.LQCD_F64, api.LQCD_EVEN) == vh * 192
+    assert api.lqcd_spinor_bytes(lat, api.LQCD_F32, api.LQCD_FULL) == 2 * vh * 96
+    assert api.lqcd_spinor_bytes(lat, api.LQCD_F16, api.LQCD_ODD) == vh * 52
+    assert api.lqcd_gauge_bytes(lat, api.LQCD_F32, 12) == 8 * vh * 48
+    assert api.lqcd_gauge_bytes(lat, api.LQCD_F64, 18) == 8 * vh * 144
+    # ragged: Vh = 3 * 2 * 3 * 3 = 54 sites, padded to 64 per checkerboard
+    lat2 = api.lattice((6, 2, 3, 3), n5=1)
+    assert api.lqcd_spinor_bytes(lat2, api.LQCD_F32, api.LQCD_EVEN) == 64 * 96
+    # invalid geometry -> 0
+    assert api.lqcd_spinor_bytes(api.lattice((5, 4, 4, 4)), api.LQCD_F32, api.LQCD_EVEN) == 0
+    assert api.lqcd_spinor_bytes(lat, 7, api.LQCD_EVEN) == 0
+
+
+def test_workspace_queries(api):
+    lat = api.lattice((4, 4, 4, 8))
+    op = api.operator(mass=0.1)
+    prm = api.solver_params(sloppy_prec=api.LQCD_F16, sloppy_recon=12)
+    ws_even = api.lqcd_cg_workspace_bytes(lat, op, prm, api.LQCD_EVEN)
+    ws_full = api.lqcd_cg_workspace_bytes(lat, op, prm, api.LQCD_FULL)
+    assert 0 < ws_even < ws_full
+    assert api.lqcd_operator_workspace_bytes(lat, op, api.LQCD_EVEN) > 0
+    bad = api.solver_params(tol=-1.0)
+    assert api.lqcd_cg_workspace_bytes(lat, op, bad, api.LQCD_EVEN) == 0
+
+
+@pytest.mark.parametrize("case", ["odd_lx", "bad_bc", "bad_prec", "bad_recon", "null", "alias", "n5"])
+def test_invalid_arguments_rejected_on_host(api, case):
+    """Each call below fails in argument validation, before any CUDA call."""
+    lat = api.lattice((4, 4, 4, 4))
+    op = api.operator(mass=0.1, prec=api.LQCD_F32)
+    buf = 4096  # a fake, 16-byte aligned address never dereferenced
+    if case == "odd_lx":
+        lat = api.lattice((3, 4, 4, 4))
+    elif case == "bad_bc":
+        lat = api.lattice((4, 4, 4, 4), bc=(1, 1, 1, 0.5))
+    elif case == "bad_prec":
+        op = api.operator(prec=5)
+    elif case == "bad_recon":
+        op = api.operator(recon=8)
+    elif case == "n5":
+        lat = api.lattice((4, 4, 4, 4), n5=0)
+    args = (buf, buf + 4096 if case != "alias" else buf, buf + 8192)
+    if case == "null":
+        args = (0, buf, buf)
+    with pytest.raises(api.LqcdError) as ei:
+        api.lqcd_dslash(args[0], args[1], args[2], lat, op, api.LQCD_EVEN, 0, stream=0)
+    assert ei.value.status == -1
+    assert api.lqcd_last_error()
+
+
+def test_cg_rejects_bad_arguments_on_host(api):
+    lat = api.lattice((4, 4, 4, 4))
+    op = api.operator(prec=api.LQCD_F32)  # CG needs LQCD_F64 outer fields
+    prm = api.solver_params()
+    info = api.lqcd_solve_info()
+    st = api.lib.lqcd_cg_solve(4096, 8192, 12288, 12288, C.byref(lat), C.byref(op), C.byref(prm),
+                               api.LQCD_EVEN, C.byref(info), 1 << 20, 1 << 30, None)
+    assert st == -1 and info.status == -1
+    op = api.operator()
+    st = api.lib.lqcd_cg_solve(4096, 8192, 12288, 12288, C.byref(lat), C.byref(op), C.byref(prm),
+                               api.LQCD_EVEN, C.byref(info), 1 << 20 | 16, 1 << 30, None)
+    assert st == -1  # workspace not 256-byte aligned
+    st = api.lib.lqcd_cg_solve(4096, 8192, 12288, 12288, C.byref(lat), C.byref(op), C.byref(prm),
+                               api.LQCD_EVEN, C.byref(info), 1 << 20, 16, None)
+    assert st == -7  # workspace too small
