@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--mass", type=float, default=0.01)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", choices=["full", "step", "hop"], default="full",
+                    help="step: only the timed solves; hop: only the dominant kernel's roofline loop")
     return ap.parse_args()
 
 
@@ -212,6 +214,14 @@ def run_lqcd(args, world, rank, local):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1), out
 
+    if args.mode == "hop":
+        # profiling mode: only the dominant kernel's roofline loop
+        L.lqcd_gauge_pack(gs[2], L.LQCD_F16, 12, U_dev, lat)
+        roof = hop_roofline(L, F, lat, gs[2], flush, stream, vh, launches=args.steps)
+        if rank == 0:
+            print(json.dumps({"mode": "hop", "roofline": roof}), flush=True)
+        return
+
     # ---- headline: FP16-inner mixed precision solve
     for _ in range(args.warmup):
         step(2)
@@ -235,6 +245,13 @@ def run_lqcd(args, world, rank, local):
 
     # the solve must meet the FP64 true residual of the full system (checked on the device result)
     res = full_residual(L, F, lat, op64, g64, x, b_dev, tmp)
+    if args.mode == "step":
+        # profiling mode: only the timed solves
+        if rank == 0:
+            print(json.dumps({"mode": "step", "value": round(value, 1), "ms_per_step": max_ms / args.steps,
+                              "iterations": infos[-1].iterations, "full_system_rel_residual": res,
+                              "gpu_launches": int(launches)}), flush=True)
+        return
 
     # ---- mixed vs FP64 comparison (one timed solve each after one warm-up)
     cgcmp = {}
