@@ -3,7 +3,7 @@
 Each translation unit under ``csrc/`` is compiled by its own nvcc process (in
 parallel), then linked with ``nvcc -shared``. Objects are rebuilt only when a
 source or header is newer than the object. Usage: ``python
-paper_1512_03487_gb300.build [--force] [--verbose]``.
+paper_1512_03487_gb300/build.py [--force] [--verbose]``.
 """
 from __future__ import annotations
 
