@@ -87,7 +87,8 @@ extern "C" {
 /* Lattice geometry (Grid paper, Sec. 2.4: a Grid object describes a 4D or 5D,
  * possibly single-checkerboard, Cartesian lattice). */
 typedef struct {
-    int dims[4];     /* Lx, Ly, Lz, Lt; every extent >= 2, Lx even */
+    int dims[4];     /* Lx, Ly, Lz, Lt; every extent even and >= 2 (checkerboarding:
+                        a hop wrapping around an odd extent keeps its parity) */
     int n5;          /* inner extent: L_s (domain wall) or number of RHS; >= 1 */
     double bc[4];    /* boundary phase per direction, +1 (periodic) or -1 */
 } lqcd_lattice;
@@ -131,6 +132,11 @@ const char* lqcd_last_error(void);
 /* Number of kernel launches issued by this library in this process (graph
  * replays count every kernel node they run). */
 uint64_t lqcd_launch_count(void);
+/* Destroy the CUDA graphs the solver caches across calls (one per distinct
+ * set of buffers and parameters, at most 16, least recently used evicted).
+ * Call before freeing solver buffers whose addresses may be reused with
+ * other meanings, or at shutdown. */
+void lqcd_release_caches(void);
 
 /* ---------------------------------------------------------------- sizes */
 

@@ -60,6 +60,7 @@ SIGNATURES = {
     "lqcd_version": (C.c_char_p, []),
     "lqcd_last_error": (C.c_char_p, []),
     "lqcd_launch_count": (C.c_uint64, []),
+    "lqcd_release_caches": (None, []),
     "lqcd_spinor_bytes": (_SZ, [_LAT, _I, _I]),
     "lqcd_gauge_bytes": (_SZ, [_LAT, _I, _I]),
     "lqcd_spinor_pack": (_I, [_P, _I, _I, _P, _LAT, _P]),

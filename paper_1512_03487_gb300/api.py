@@ -90,6 +90,10 @@ def lqcd_launch_count() -> int:
     return int(lib.lqcd_launch_count())
 
 
+def lqcd_release_caches() -> None:
+    lib.lqcd_release_caches()
+
+
 def lqcd_spinor_bytes(lat, prec, subset) -> int:
     return int(lib.lqcd_spinor_bytes(C.byref(lat), prec, subset))
 

@@ -44,7 +44,11 @@ int make_geom(const lqcd_lattice* lat, Geom* g) {
     if (lat->bc[mu] != 1.0 && lat->bc[mu] != -1.0)
       return fail(LQCD_ERR_ARG, "boundary phase %g in direction %d is not +-1", lat->bc[mu], mu);
   }
-  if (lat->dims[0] % 2) return fail(LQCD_ERR_ARG, "Lx = %d must be even for checkerboarding", lat->dims[0]);
+  // A hop that wraps around an odd extent lands on a site of the same parity,
+  // so even-odd checkerboarding needs every extent even.
+  for (int mu = 0; mu < 4; mu++)
+    if (lat->dims[mu] % 2)
+      return fail(LQCD_ERR_ARG, "extent %d in direction %d must be even for checkerboarding", lat->dims[mu], mu);
   if (lat->n5 < 1) return fail(LQCD_ERR_ARG, "n5 = %d < 1", lat->n5);
   const int64_t V = (int64_t)lat->dims[0] * lat->dims[1] * lat->dims[2] * lat->dims[3];
   if (V / 2 * lat->n5 > (int64_t)1 << 31) return fail(LQCD_ERR_ARG, "lattice too large");

@@ -23,6 +23,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "lqcd_internal.h"
@@ -344,11 +345,95 @@ struct Solver {
   }
 };
 
+
+// ------------------------------------------------------------------ chunk-graph cache
+// Everything a captured chunk bakes into its launches (pointers, geometry,
+// operator, sloppy format, chunk length, iteration cap).
+struct GraphKey {
+  int device;
+  const void* x;
+  const void* b;
+  const void* gauge_s;
+  const void* ws;
+  lqcd_lattice lat;
+  lqcd_operator op;
+  int sloppy_prec, sloppy_recon, chunk, maxiter, subset;
+};
+
+struct GraphEntry {
+  GraphKey key;
+  cudaGraphExec_t exec;
+  uint64_t nodes;
+  uint64_t last_use;
+};
+
+static std::mutex g_graph_mutex;
+static std::vector<GraphEntry> g_graphs;
+static uint64_t g_graph_clock = 0;
+constexpr size_t MAX_GRAPHS = 16;
+
+static int chunk_graph(Solver& S, const GraphKey& key, cudaGraphExec_t* exec, uint64_t* nodes) {
+  std::lock_guard<std::mutex> lock(g_graph_mutex);
+  for (auto& e : g_graphs) {
+    if (memcmp(&e.key, &key, sizeof(GraphKey)) == 0) {
+      e.last_use = ++g_graph_clock;
+      *exec = e.exec;
+      *nodes = e.nodes;
+      return LQCD_OK;
+    }
+  }
+  cudaStream_t cap;
+  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "cg: stream create");
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cap);
+    return cuda_fail(e, "cg: begin capture");
+  }
+  int st = LQCD_OK;
+  g_count_suspended = true;
+  for (int i = 0; i < key.chunk && st == LQCD_OK; i++) st = S.inner_iteration(cap);
+  g_count_suspended = false;
+  e = cudaStreamEndCapture(cap, &graph);
+  cudaStreamDestroy(cap);
+  if (st) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cg: end capture");
+  size_t n = 0;
+  cudaGraphGetNodes(graph, nullptr, &n);
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cg: graph instantiate");
+  if (g_graphs.size() >= MAX_GRAPHS) {
+    size_t lru = 0;
+    for (size_t i = 1; i < g_graphs.size(); i++)
+      if (g_graphs[i].last_use < g_graphs[lru].last_use) lru = i;
+    cudaGraphExecDestroy(g_graphs[lru].exec);
+    g_graphs.erase(g_graphs.begin() + lru);
+  }
+  g_graphs.push_back(GraphEntry{key, ex, (uint64_t)n, ++g_graph_clock});
+  *exec = ex;
+  *nodes = n;
+  return LQCD_OK;
+}
+
+void release_graph_cache() {
+  std::lock_guard<std::mutex> lock(g_graph_mutex);
+  for (auto& e : g_graphs) cudaGraphExecDestroy(e.exec);
+  g_graphs.clear();
+}
+
 }  // namespace lqcd
 
 using namespace lqcd;
 
 extern "C" {
+
+void lqcd_release_caches(void) { release_graph_cache(); }
 
 size_t lqcd_cg_workspace_bytes(const lqcd_lattice* lat, const lqcd_operator* op, const lqcd_solver_params* p,
                                int subset) {
@@ -442,41 +527,28 @@ int lqcd_cg_solve(void* x, const void* b, const void* gauge, const void* gauge_s
     if ((st = launch_vec(VK_INIT, prm->sloppy_prec, ai, s))) return finish(st);
   }
 
-  // Build the chunk: check_interval inner iterations, captured as a graph.
+  // The chunk: check_interval inner iterations, captured once as a graph and
+  // cached across solves with the same buffers and parameters.
   const int chunk = S.prm.check_interval;
   cudaGraphExec_t exec = nullptr;
   uint64_t nodes_per_chunk = 0;
   if (prm->use_graph) {
-    cudaStream_t cap;
-    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return finish(cuda_fail(e, "cg: stream create"));
-    cudaGraph_t graph = nullptr;
-    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) {
-      cudaStreamDestroy(cap);
-      return finish(cuda_fail(e, "cg: begin capture"));
-    }
-    g_count_suspended = true;
-    for (int i = 0; i < chunk && st == LQCD_OK; i++) st = S.inner_iteration(cap);
-    g_count_suspended = false;
-    e = cudaStreamEndCapture(cap, &graph);
-    cudaStreamDestroy(cap);
-    if (st) {
-      if (graph) cudaGraphDestroy(graph);
-      return finish(st);
-    }
-    if (e != cudaSuccess) return finish(cuda_fail(e, "cg: end capture"));
-    size_t n = 0;
-    cudaGraphGetNodes(graph, nullptr, &n);
-    nodes_per_chunk = n;
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return finish(cuda_fail(e, "cg: graph instantiate"));
+    GraphKey key;
+    memset(&key, 0, sizeof(key));
+    cudaGetDevice(&key.device);
+    key.x = x;
+    key.b = b;
+    key.gauge_s = gauge_sloppy;
+    key.ws = workspace;
+    key.lat = *lat;
+    key.op = *op;
+    key.sloppy_prec = prm->sloppy_prec;
+    key.sloppy_recon = prm->sloppy_recon;
+    key.chunk = chunk;
+    key.maxiter = prm->maxiter;
+    key.subset = subset;
+    if ((st = chunk_graph(S, key, &exec, &nodes_per_chunk))) return finish(st);
   }
-  auto cleanup = [&]() {
-    if (exec) cudaGraphExecDestroy(exec);
-  };
-
   Control ctrl;
   int reliable = 0;
   int status = LQCD_OK;
@@ -515,7 +587,6 @@ int lqcd_cg_solve(void* x, const void* b, const void* gauge, const void* gauge_s
       if (st) { status = st; break; }
     }
   }
-  cleanup();
   // report
   std::vector<SysState> sys(S.nsys);
   e = cudaMemcpyAsync(sys.data(), S.w.sys, sizeof(SysState) * S.nsys, cudaMemcpyDeviceToHost, s);

@@ -51,9 +51,9 @@ def test_sizes(api):
     assert api.lqcd_spinor_bytes(lat, api.LQCD_F16, api.LQCD_ODD) == vh * 52
     assert api.lqcd_gauge_bytes(lat, api.LQCD_F32, 12) == 8 * vh * 48
     assert api.lqcd_gauge_bytes(lat, api.LQCD_F64, 18) == 8 * vh * 144
-    # ragged: Vh = 3 * 2 * 3 * 3 = 54 sites, padded to 64 per checkerboard
-    lat2 = api.lattice((6, 2, 3, 3), n5=1)
-    assert api.lqcd_spinor_bytes(lat2, api.LQCD_F32, api.LQCD_EVEN) == 64 * 96
+    # ragged: Vh = 6 * 2 * 2 * 6 / 2 = 72 sites, padded to 96 per checkerboard
+    lat2 = api.lattice((6, 2, 2, 6), n5=1)
+    assert api.lqcd_spinor_bytes(lat2, api.LQCD_F32, api.LQCD_EVEN) == 96 * 96
     # invalid geometry -> 0
     assert api.lqcd_spinor_bytes(api.lattice((5, 4, 4, 4)), api.LQCD_F32, api.LQCD_EVEN) == 0
     assert api.lqcd_spinor_bytes(lat, 7, api.LQCD_EVEN) == 0
@@ -71,7 +71,7 @@ def test_workspace_queries(api):
     assert api.lqcd_cg_workspace_bytes(lat, op, bad, api.LQCD_EVEN) == 0
 
 
-@pytest.mark.parametrize("case", ["odd_lx", "bad_bc", "bad_prec", "bad_recon", "null", "alias", "n5"])
+@pytest.mark.parametrize("case", ["odd_lx", "odd_lz", "bad_bc", "bad_prec", "bad_recon", "null", "alias", "n5"])
 def test_invalid_arguments_rejected_on_host(api, case):
     """Each call below fails in argument validation, before any CUDA call."""
     lat = api.lattice((4, 4, 4, 4))
@@ -79,6 +79,8 @@ def test_invalid_arguments_rejected_on_host(api, case):
     buf = 4096  # a fake, 16-byte aligned address never dereferenced
     if case == "odd_lx":
         lat = api.lattice((3, 4, 4, 4))
+    elif case == "odd_lz":
+        lat = api.lattice((4, 4, 5, 4))  # a hop wrapping in z would keep its parity
     elif case == "bad_bc":
         lat = api.lattice((4, 4, 4, 4), bc=(1, 1, 1, 0.5))
     elif case == "bad_prec":

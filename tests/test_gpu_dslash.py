@@ -60,11 +60,12 @@ def test_hop_matches_oracle(L, prec, recon, dagger, subset):
     assert rel_l2(got, expect) <= TOL[prec]
 
 
-@pytest.mark.parametrize("dims", [(4, 3, 5, 2), (2, 2, 2, 2), (8, 6, 2, 4)])
+@pytest.mark.parametrize("dims", [(4, 2, 6, 2), (2, 2, 2, 2), (8, 6, 2, 4)])
 @pytest.mark.parametrize("n5", [1, 3])
-def test_hop_odd_and_degenerate_shapes(L, dims, n5):
-    """Odd extents, extent-2 directions (forward and backward neighbour are the
-    same site) and an inner dimension n5 > 1 (L_s-replicated / multi-RHS hop)."""
+def test_hop_degenerate_shapes(L, dims, n5):
+    """Extent-2 directions (forward and backward neighbour are the same site),
+    a single partial block, and an inner dimension n5 > 1 (L_s-replicated /
+    multi-RHS hop)."""
     for subset in (0, 1, 2):
         got, expect = _hop_case(L, dims, n5, 0, 18, 0, subset, seed=7)
         assert rel_l2(got, expect) <= TOL[0]

@@ -1,0 +1,142 @@
+"""Parity at the benchmark sizes, in the launch configuration bench.py times.
+
+24^3 x 48 (the bench workload): every output of the FP16 and FP32 12-real hop
+against the oracle, and the mixed-precision solve's full-system FP64 residual.
+16^4 x L_s = 16 (domain wall) and 32^4 x 12 RHS: the L_s-replicated /
+multi-RHS hop on sampled slices. 16^4 force kernel on the same X, Y as the
+oracle.
+"""
+import numpy as np
+import pytest
+
+from oracle import force as oforce
+from oracle import wilson
+from synthetic import config_seed, gauge_field, gaussian_spinor
+from tests.layout import rel_l2
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+BC = (1.0, 1.0, 1.0, -1.0)
+DIMS = (24, 24, 24, 48)
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1512_03487_gb300 as L
+    from paper_1512_03487_gb300 import fields
+    L.fields = fields
+    return L
+
+
+@pytest.fixture(scope="module")
+def bench_fields():
+    U = gauge_field(DIMS, "exp", config_seed(1, 0), eps=0.3)
+    b = gaussian_spinor(DIMS, config_seed(1, 1), lead=(1,))
+    return U, b
+
+
+def _cb_flat(full, parity, dims):
+    """Sites of one parity of [..., T, Z, Y, X, 4, 3] in lexicographic order."""
+    X, Y, Z, T = dims
+    par = wilson.parity_field(dims).reshape(-1)
+    idx = np.nonzero(par == parity)[0]
+    return full.reshape(full.shape[:-6] + (X * Y * Z * T, 4, 3))[..., idx, :, :]
+
+
+@pytest.mark.parametrize("prec,tol", [(2, 3e-3), (1, 1e-5)])
+def test_bench_size_hop_all_outputs(L, bench_fields, prec, tol):
+    U, b = bench_fields
+    F = L.fields
+    lat = L.lattice(DIMS, bc=BC)
+    op = L.operator(prec=prec, recon=12)
+    g = F.gauge_to_device(U, lat, prec, 12)
+    src = _cb_flat(b, 1, DIMS).reshape(F.host_spinor_shape(lat, 1))
+    fin = F.spinor_to_device(src, lat, prec, 1)
+    out = F.empty(L.lqcd_spinor_bytes(lat, prec, 0))
+    L.lqcd_dslash(out, fin, g, lat, op, 0, 0)
+    got = F.spinor_to_host(out, lat, prec, 0)
+    expect = _cb_flat(wilson.hop_eo(U, b, BC, 0), 0, DIMS)
+    assert rel_l2(got, expect) <= tol
+
+
+def test_bench_size_mixed_solve_residual(L, bench_fields):
+    """The bench step (FP16 / 12-real inner, FP64 reliable updates) reaches a
+    full-system residual ||b - D_W x|| / ||b|| checked by the oracle."""
+    U, b = bench_fields
+    F = L.fields
+    m = 0.01
+    lat = L.lattice(DIMS, bc=BC)
+    op = L.operator(mass=m)
+    g64 = F.gauge_to_device(U, lat, 0, 18)
+    g16 = F.gauge_to_device(U, lat, 2, 12)
+    bd = F.spinor_to_device(b, lat, 0, 2)
+    tmp = F.empty(L.lqcd_operator_workspace_bytes(lat, op, 0))
+    bhat = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
+    src = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
+    L.lqcd_eo_prepare(bhat, bd, g64, lat, op, tmp)
+    L.lqcd_M(src, bhat, g64, lat, op, 0, 1, tmp)
+    prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=2, sloppy_recon=12, check_interval=32)
+    x = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
+    ws = F.empty(L.lqcd_cg_workspace_bytes(lat, op, prm, 0))
+    info = L.lqcd_cg_solve(x, src, g64, g16, lat, op, prm, 0, ws)
+    assert info.status == 0 and info.true_rel_residual <= 1e-10
+    L.lqcd_eo_reconstruct(x, bd, g64, lat, op, tmp)
+    xh = F.spinor_to_host(x, lat, 0, 2)
+    res = b - wilson.dirac(U, xh, m, BC)
+    # ||b - D x|| <= ||M_hat^-dag|| tol ||...||: the normal-equation tolerance 1e-10 bounds it loosely
+    assert np.linalg.norm(res) <= 1e-8 * np.linalg.norm(b)
+
+
+def test_dwf_size_hop_sampled_slices(L):
+    dims, Ls = (16, 16, 16, 16), 16
+    U = gauge_field(dims, "haar", config_seed(2, 0))
+    psi = gaussian_spinor(dims, config_seed(2, 1), lead=(Ls,))
+    F = L.fields
+    lat = L.lattice(dims, n5=Ls, bc=BC)
+    op = L.operator(kind=L.LQCD_DWF, M5=1.8, mf=0.02, prec=1, recon=12)
+    g = F.gauge_to_device(U, lat, 1, 12)
+    fin = F.spinor_to_device(_cb_flat(psi, 1, dims).reshape(F.host_spinor_shape(lat, 1)), lat, 1, 1)
+    out = F.empty(L.lqcd_spinor_bytes(lat, 1, 0))
+    L.lqcd_dslash(out, fin, g, lat, op, 0, 0)
+    got = F.spinor_to_host(out, lat, 1, 0)
+    for s in (0, 7, 15):
+        expect = _cb_flat(wilson.hop_eo(U, psi[s], BC, 0), 0, dims)
+        assert rel_l2(got[s].reshape(expect.shape), expect) <= 1e-5
+
+
+def test_multi_rhs_size_hop_sampled_rhs(L):
+    dims, n = (32, 32, 32, 32), 12
+    U = gauge_field(dims, "haar", config_seed(3, 0))
+    F = L.fields
+    lat = L.lattice(dims, n5=n, bc=BC)
+    op = L.operator(prec=2, recon=12)
+    g = F.gauge_to_device(U, lat, 2, 12)
+    rhs = gaussian_spinor(dims, config_seed(3, 1), lead=(n,))
+    fin = F.spinor_to_device(_cb_flat(rhs, 1, dims).reshape(F.host_spinor_shape(lat, 1)), lat, 2, 1)
+    del rhs
+    out = F.empty(L.lqcd_spinor_bytes(lat, 2, 0))
+    L.lqcd_dslash(out, fin, g, lat, op, 0, 0)
+    got = F.spinor_to_host(out, lat, 2, 0)
+    rhs = gaussian_spinor(dims, config_seed(3, 1), lead=(n,))
+    for k in (0, 11):
+        expect = _cb_flat(wilson.hop_eo(U, rhs[k], BC, 0), 0, dims)
+        assert rel_l2(got[k].reshape(expect.shape), expect) <= 3e-3
+
+
+def test_force_kernel_16x4(L):
+    dims = (16, 16, 16, 16)
+    U = gauge_field(dims, "haar", config_seed(4, 0))
+    X = gaussian_spinor(dims, config_seed(4, 1))
+    Y = gaussian_spinor(dims, config_seed(4, 2))
+    F = L.fields
+    lat = L.lattice(dims, bc=BC)
+    op = L.operator(mass=0.05)
+    g = F.gauge_to_device(U, lat, 0, 18)
+    out = F.empty(L.lqcd_gauge_bytes(lat, 0, 18))
+    L.lqcd_force(out, g, F.spinor_to_device(X[None], lat, 0, 2), F.spinor_to_device(Y[None], lat, 0, 2), lat, op,
+                 L.LQCD_FORCE_TA)
+    got = F.gauge_to_host(out, lat, 0, 18)
+    _, F_o = oforce.force_terms(U, X, Y, BC)
+    assert rel_l2(got, F_o) <= 1e-12
