@@ -26,6 +26,7 @@
 #include <mutex>
 #include <vector>
 
+#include "cg_site.cuh"
 #include "lqcd_internal.h"
 
 namespace lqcd {
@@ -60,141 +61,61 @@ __device__ __forceinline__ bool vec_site(const VecArgs& a, int& parity, int64_t&
   return j < a.g.nsites;
 }
 
-template <typename T> __device__ __forceinline__ double site_norm2(const Spinor<T>& s) {
-  T acc = T(0);
-#pragma unroll
-  for (int k = 0; k < 12; k++) acc = fma(s.v[k].r, s.v[k].r, fma(s.v[k].i, s.v[k].i, acc));
-  return (double)acc;
-}
-
-template <typename TD, typename TS> __device__ __forceinline__ void convert(const Spinor<TS>& a, Spinor<TD>& b) {
-#pragma unroll
-  for (int k = 0; k < 12; k++) b.v[k] = mk((TD)a.v[k].r, (TD)a.v[k].i);
-}
-
 #define PAR_PTR(ptr, hb) ((ptr) ? (decltype(ptr))((char*)(ptr) + parity * (hb)) : (ptr))
 
 // r = b, r_s = b, p = b, x_s = 0, x = 0; |b|^2 -> initial state
 template <int VF, int SF>
 __global__ void __launch_bounds__(BLAS_BLOCK) k_init(VecArgs a) {
-  using TV = typename PrecTraits<VF>::real;
-  using TS = typename PrecTraits<SF>::real;
   int parity;
   int64_t j, first;
   double red = 0.0;
-  if (vec_site(a, parity, j, first)) {
-    Spinor<double> b;
-    SpinorIO<LQCD_F64>::load(PAR_PTR(a.b64, a.hb64), a.g.sstride, j, b);
-    SpinorIO<LQCD_F64>::store(PAR_PTR(a.r64, a.hb64), a.g.sstride, j, b);
-    Spinor<double> z;
-    zero(z);
-    SpinorIO<LQCD_F64>::store(PAR_PTR(a.x64, a.hb64), a.g.sstride, j, z);
-    Spinor<TV> bv, zv;
-    convert(b, bv);
-    zero(zv);
-    SpinorIO<VF>::store(PAR_PTR(a.rs, a.hbv), a.g.sstride, j, bv);
-    SpinorIO<VF>::store(PAR_PTR(a.xs, a.hbv), a.g.sstride, j, zv);
-    Spinor<TS> bs;
-    convert(b, bs);
-    SpinorIO<SF>::store(PAR_PTR(a.p, a.hbs), a.g.sstride, j, bs);
-    red = site_norm2(b);
-  }
+  if (vec_site(a, parity, j, first))
+    red = init_site<VF, SF>(a.g, j, PAR_PTR(a.b64, a.hb64), PAR_PTR(a.r64, a.hb64), PAR_PTR(a.x64, a.hb64),
+                            PAR_PTR(a.rs, a.hbv), PAR_PTR(a.xs, a.hbv), PAR_PTR(a.p, a.hbs));
   block_reduce_finalize<BLAS_BLOCK>(red, first, a.red);
 }
 
 // x_s += alpha p; r_s -= alpha Ap; |r_s|^2 -> beta or pause
 template <int VF, int SF>
 __global__ void __launch_bounds__(BLAS_BLOCK) k_update(VecArgs a) {
-  using TV = typename PrecTraits<VF>::real;
-  using TS = typename PrecTraits<SF>::real;
   if (gate_closed(a.gate)) return;
   int parity;
   int64_t j, first;
   double red = 0.0;
-  if (vec_site(a, parity, j, first)) {
-    const TV alpha = (TV)a.sys[sys_of(j, a.red.nsys)].alpha;
-    Spinor<TS> p, ap;
-    SpinorIO<SF>::load(PAR_PTR(a.p, a.hbs), a.g.sstride, j, p);
-    SpinorIO<SF>::load(PAR_PTR(a.ap, a.hbs), a.g.sstride, j, ap);
-    Spinor<TV> x, r;
-    void* xs = PAR_PTR(a.xs, a.hbv);
-    void* rs = PAR_PTR(a.rs, a.hbv);
-    SpinorIO<VF>::load(xs, a.g.sstride, j, x);
-    SpinorIO<VF>::load(rs, a.g.sstride, j, r);
-#pragma unroll
-    for (int k = 0; k < 12; k++) {
-      x.v[k] = mk(fma(alpha, (TV)p.v[k].r, x.v[k].r), fma(alpha, (TV)p.v[k].i, x.v[k].i));
-      r.v[k] = mk(fma(-alpha, (TV)ap.v[k].r, r.v[k].r), fma(-alpha, (TV)ap.v[k].i, r.v[k].i));
-    }
-    SpinorIO<VF>::store(xs, a.g.sstride, j, x);
-    SpinorIO<VF>::store(rs, a.g.sstride, j, r);
-    red = site_norm2(r);
-  }
+  if (vec_site(a, parity, j, first))
+    red = update_site<VF, SF>(a.g, j, a.sys[sys_of(j, a.red.nsys)].alpha, PAR_PTR(a.p, a.hbs),
+                              PAR_PTR(a.ap, a.hbs), PAR_PTR(a.xs, a.hbv), PAR_PTR(a.rs, a.hbv));
   block_reduce_finalize<BLAS_BLOCK>(red, first, a.red);
 }
 
 // p = r_s + beta p
 template <int VF, int SF>
 __global__ void __launch_bounds__(BLAS_BLOCK) k_pupdate(VecArgs a) {
-  using TV = typename PrecTraits<VF>::real;
-  using TS = typename PrecTraits<SF>::real;
   if (gate_closed(a.gate)) return;
   int parity;
   int64_t j, first;
   if (!vec_site(a, parity, j, first)) return;
-  const TS beta = (TS)a.sys[sys_of(j, a.red.nsys)].beta;
-  Spinor<TV> r;
-  SpinorIO<VF>::load(PAR_PTR(a.rs, a.hbv), a.g.sstride, j, r);
-  void* pp = PAR_PTR(a.p, a.hbs);
-  Spinor<TS> p;
-  SpinorIO<SF>::load(pp, a.g.sstride, j, p);
-#pragma unroll
-  for (int k = 0; k < 12; k++) p.v[k] = mk(fma(beta, p.v[k].r, (TS)r.v[k].r), fma(beta, p.v[k].i, (TS)r.v[k].i));
-  SpinorIO<SF>::store(pp, a.g.sstride, j, p);
+  pupdate_site<VF, SF>(a.g, j, a.sys[sys_of(j, a.red.nsys)].beta, PAR_PTR(a.rs, a.hbv), PAR_PTR(a.p, a.hbs));
 }
 
 // x += x_s (FP64); x_s = 0
 template <int VF>
 __global__ void __launch_bounds__(BLAS_BLOCK) k_accumulate(VecArgs a) {
-  using TV = typename PrecTraits<VF>::real;
   int parity;
   int64_t j, first;
   if (!vec_site(a, parity, j, first)) return;
-  Spinor<double> x;
-  double* xp = PAR_PTR(a.x64, a.hb64);
-  SpinorIO<LQCD_F64>::load(xp, a.g.sstride, j, x);
-  Spinor<TV> xs, z;
-  void* xsp = PAR_PTR(a.xs, a.hbv);
-  SpinorIO<VF>::load(xsp, a.g.sstride, j, xs);
-#pragma unroll
-  for (int k = 0; k < 12; k++) x.v[k] = mk(x.v[k].r + (double)xs.v[k].r, x.v[k].i + (double)xs.v[k].i);
-  zero(z);
-  SpinorIO<LQCD_F64>::store(xp, a.g.sstride, j, x);
-  SpinorIO<VF>::store(xsp, a.g.sstride, j, z);
+  accumulate_site<VF>(a.g, j, PAR_PTR(a.x64, a.hb64), PAR_PTR(a.xs, a.hbv));
 }
 
 // r = b - A x (FP64), r_s = r; |r|^2 -> done flags, beta, resume
 template <int VF>
 __global__ void __launch_bounds__(BLAS_BLOCK) k_residual(VecArgs a) {
-  using TV = typename PrecTraits<VF>::real;
   int parity;
   int64_t j, first;
   double red = 0.0;
-  if (vec_site(a, parity, j, first)) {
-    Spinor<double> b, ax;
-    SpinorIO<LQCD_F64>::load(PAR_PTR(a.b64, a.hb64), a.g.sstride, j, b);
-    SpinorIO<LQCD_F64>::load(PAR_PTR(a.ax64, a.hb64), a.g.sstride, j, ax);
-#pragma unroll
-    for (int k = 0; k < 12; k++) b.v[k] = b.v[k] - ax.v[k];
-    SpinorIO<LQCD_F64>::store(PAR_PTR(a.r64, a.hb64), a.g.sstride, j, b);
-    Spinor<TV> rv;
-    convert(b, rv);
-    SpinorIO<VF>::store(PAR_PTR(a.rs, a.hbv), a.g.sstride, j, rv);
-    double s = 0.0;
-#pragma unroll
-    for (int k = 0; k < 12; k++) s = fma(b.v[k].r, b.v[k].r, fma(b.v[k].i, b.v[k].i, s));
-    red = s;
-  }
+  if (vec_site(a, parity, j, first))
+    red = residual_site<VF>(a.g, j, PAR_PTR(a.b64, a.hb64), PAR_PTR(a.ax64, a.hb64), PAR_PTR(a.r64, a.hb64),
+                            PAR_PTR(a.rs, a.hbv));
   block_reduce_finalize<BLAS_BLOCK>(red, first, a.red);
 }
 #undef PAR_PTR

@@ -1,0 +1,116 @@
+// Per-site bodies of the conjugate-gradient vector kernels, shared by the
+// single-lattice solver (cg.cu) and the batched solver (batch.cu). VF is the
+// format of the iterated vectors x_s, r_s (FP64 or FP32); SF the format of the
+// vectors the Dslash reads and writes, p and Ap (FP64, FP32 or FP16). Each
+// returning function gives the site's contribution to the next reduction.
+#pragma once
+
+#include "lqcd_common.cuh"
+
+namespace lqcd {
+
+template <typename T> __device__ __forceinline__ double site_norm2(const Spinor<T>& s) {
+  T acc = T(0);
+#pragma unroll
+  for (int k = 0; k < 12; k++) acc = fma(s.v[k].r, s.v[k].r, fma(s.v[k].i, s.v[k].i, acc));
+  return (double)acc;
+}
+
+template <typename TD, typename TS> __device__ __forceinline__ void convert(const Spinor<TS>& a, Spinor<TD>& b) {
+#pragma unroll
+  for (int k = 0; k < 12; k++) b.v[k] = mk((TD)a.v[k].r, (TD)a.v[k].i);
+}
+
+// r = b, r_s = b, p = b, x_s = 0, x = 0; returns |b|^2
+template <int VF, int SF>
+__device__ __forceinline__ double init_site(const Geom& g, int64_t j, const double* b64, double* r64, double* x64,
+                                            void* rs, void* xs, void* p) {
+  using TV = typename PrecTraits<VF>::real;
+  using TS = typename PrecTraits<SF>::real;
+  Spinor<double> b, z;
+  SpinorIO<LQCD_F64>::load(b64, g.sstride, j, b);
+  SpinorIO<LQCD_F64>::store(r64, g.sstride, j, b);
+  zero(z);
+  SpinorIO<LQCD_F64>::store(x64, g.sstride, j, z);
+  Spinor<TV> bv, zv;
+  convert(b, bv);
+  zero(zv);
+  SpinorIO<VF>::store(rs, g.sstride, j, bv);
+  SpinorIO<VF>::store(xs, g.sstride, j, zv);
+  Spinor<TS> bs;
+  convert(b, bs);
+  SpinorIO<SF>::store(p, g.sstride, j, bs);
+  return site_norm2(b);
+}
+
+// x_s += alpha p; r_s -= alpha Ap; returns |r_s|^2
+template <int VF, int SF>
+__device__ __forceinline__ double update_site(const Geom& g, int64_t j, double alpha_d, const void* p_,
+                                              const void* ap_, void* xs, void* rs) {
+  using TV = typename PrecTraits<VF>::real;
+  using TS = typename PrecTraits<SF>::real;
+  const TV alpha = (TV)alpha_d;
+  Spinor<TS> p, ap;
+  SpinorIO<SF>::load(p_, g.sstride, j, p);
+  SpinorIO<SF>::load(ap_, g.sstride, j, ap);
+  Spinor<TV> x, r;
+  SpinorIO<VF>::load(xs, g.sstride, j, x);
+  SpinorIO<VF>::load(rs, g.sstride, j, r);
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    x.v[k] = mk(fma(alpha, (TV)p.v[k].r, x.v[k].r), fma(alpha, (TV)p.v[k].i, x.v[k].i));
+    r.v[k] = mk(fma(-alpha, (TV)ap.v[k].r, r.v[k].r), fma(-alpha, (TV)ap.v[k].i, r.v[k].i));
+  }
+  SpinorIO<VF>::store(xs, g.sstride, j, x);
+  SpinorIO<VF>::store(rs, g.sstride, j, r);
+  return site_norm2(r);
+}
+
+// p = r_s + beta p
+template <int VF, int SF>
+__device__ __forceinline__ void pupdate_site(const Geom& g, int64_t j, double beta_d, const void* rs, void* pp) {
+  using TV = typename PrecTraits<VF>::real;
+  using TS = typename PrecTraits<SF>::real;
+  const TS beta = (TS)beta_d;
+  Spinor<TV> r;
+  SpinorIO<VF>::load(rs, g.sstride, j, r);
+  Spinor<TS> p;
+  SpinorIO<SF>::load(pp, g.sstride, j, p);
+#pragma unroll
+  for (int k = 0; k < 12; k++) p.v[k] = mk(fma(beta, p.v[k].r, (TS)r.v[k].r), fma(beta, p.v[k].i, (TS)r.v[k].i));
+  SpinorIO<SF>::store(pp, g.sstride, j, p);
+}
+
+// x += x_s (FP64); x_s = 0
+template <int VF>
+__device__ __forceinline__ void accumulate_site(const Geom& g, int64_t j, double* x64, void* xs) {
+  using TV = typename PrecTraits<VF>::real;
+  Spinor<double> x;
+  SpinorIO<LQCD_F64>::load(x64, g.sstride, j, x);
+  Spinor<TV> d, z;
+  SpinorIO<VF>::load(xs, g.sstride, j, d);
+#pragma unroll
+  for (int k = 0; k < 12; k++) x.v[k] = mk(x.v[k].r + (double)d.v[k].r, x.v[k].i + (double)d.v[k].i);
+  zero(z);
+  SpinorIO<LQCD_F64>::store(x64, g.sstride, j, x);
+  SpinorIO<VF>::store(xs, g.sstride, j, z);
+}
+
+// r = b - A x (FP64), r_s = r; returns |r|^2 in FP64
+template <int VF>
+__device__ __forceinline__ double residual_site(const Geom& g, int64_t j, const double* b64, const double* ax64,
+                                                double* r64, void* rs) {
+  using TV = typename PrecTraits<VF>::real;
+  Spinor<double> b, ax;
+  SpinorIO<LQCD_F64>::load(b64, g.sstride, j, b);
+  SpinorIO<LQCD_F64>::load(ax64, g.sstride, j, ax);
+#pragma unroll
+  for (int k = 0; k < 12; k++) b.v[k] = b.v[k] - ax.v[k];
+  SpinorIO<LQCD_F64>::store(r64, g.sstride, j, b);
+  Spinor<TV> rv;
+  convert(b, rv);
+  SpinorIO<VF>::store(rs, g.sstride, j, rv);
+  return site_norm2(b);
+}
+
+}  // namespace lqcd

@@ -121,44 +121,44 @@ template <> __device__ __forceinline__ double bc_phase<double>(const Geom& g, in
 template <> __device__ __forceinline__ float bc_phase<float>(const Geom& g, int mu) { return g.bcf[mu]; }
 
 template <int MU, int P, int R, bool DAG>
-__device__ __forceinline__ void hop_dir(Spinor<typename PrecTraits<P>::real>& acc, const HopArgs& A,
-                                        const Coord& x, int64_t cb, int64_t i5, int parity,
-                                        const void* in) {
+__device__ __forceinline__ void hop_dir(Spinor<typename PrecTraits<P>::real>& acc, const Geom& g,
+                                        const void* gauge, const Coord& x, int64_t cb, int64_t i5,
+                                        int parity, const void* in) {
   using T = typename PrecTraits<P>::real;
   constexpr int SF = DAG ? +1 : -1;  // forward hop carries (1 + SF gamma_mu)
-  const int64_t n5 = A.g.n5;
+  const int64_t n5 = g.n5;
   {
     bool wrap;
-    const int64_t nb = neighbour_cb<MU>(A.g, x, +1, wrap);
+    const int64_t nb = neighbour_cb<MU>(g, x, +1, wrap);
     Spinor<T> s;
-    SpinorIO<P>::load(in, A.g.sstride, nb * n5 + i5, s);
+    SpinorIO<P>::load(in, g.sstride, nb * n5 + i5, s);
     Half<T> h;
     project<MU, SF>(s, h);
     if (wrap) {
-      const T ph = bc_phase<T>(A.g, MU);
+      const T ph = bc_phase<T>(g, MU);
 #pragma unroll
       for (int k = 0; k < 6; k++) h.v[k] = ph * h.v[k];
     }
     Link<T> u;
-    LinkIO<P, R>::load(A.gauge, A.g.gstride, parity * 4 + MU, cb, u);
+    LinkIO<P, R>::load(gauge, g.gstride, parity * 4 + MU, cb, u);
     Half<T> w;
     link_mul(u, h, w);
     accumulate<MU, SF>(acc, w);
   }
   {
     bool wrap;
-    const int64_t nb = neighbour_cb<MU>(A.g, x, -1, wrap);
+    const int64_t nb = neighbour_cb<MU>(g, x, -1, wrap);
     Spinor<T> s;
-    SpinorIO<P>::load(in, A.g.sstride, nb * n5 + i5, s);
+    SpinorIO<P>::load(in, g.sstride, nb * n5 + i5, s);
     Half<T> h;
     project<MU, -SF>(s, h);
     if (wrap) {
-      const T ph = bc_phase<T>(A.g, MU);
+      const T ph = bc_phase<T>(g, MU);
 #pragma unroll
       for (int k = 0; k < 6; k++) h.v[k] = ph * h.v[k];
     }
     Link<T> u;
-    LinkIO<P, R>::load(A.gauge, A.g.gstride, (1 - parity) * 4 + MU, nb, u);
+    LinkIO<P, R>::load(gauge, g.gstride, (1 - parity) * 4 + MU, nb, u);
     Half<T> w;
     link_mul_dag(u, h, w);
     accumulate<MU, -SF>(acc, w);
@@ -175,10 +175,74 @@ __device__ __forceinline__ void add_chiral(Spinor<T>& out, const Spinor<T>& xs, 
   }
 }
 
+// Epilogue coefficients: PLAIN out = b H in; XPAY out = a x + b H in;
+// M5 out = M5op(x) + b H in with M5op diagonal m5d and corner mf.
+struct EpiCoef {
+  double a, b, m5d, mf;
+};
+
+// The result at output site j (= cb * n5 + i5) of checkerboard `parity`.
+template <int P, int R, bool DAG, int EPI>
+__device__ __forceinline__ void hop_site(const Geom& g, const void* gauge, const void* in, const void* xb,
+                                         int parity, int64_t j, const EpiCoef& c,
+                                         Spinor<typename PrecTraits<P>::real>& res) {
+  using T = typename PrecTraits<P>::real;
+  using IO = SpinorIO<P>;
+  const int64_t n5 = g.n5;
+  int64_t cb, i5;
+  if (n5 == 1) { cb = j; i5 = 0; } else { cb = j / n5; i5 = j - cb * n5; }
+  const Coord x = cb_to_coord(g, cb, parity);
+  Spinor<T> acc;
+  zero(acc);
+  hop_dir<0, P, R, DAG>(acc, g, gauge, x, cb, i5, parity, in);
+  hop_dir<1, P, R, DAG>(acc, g, gauge, x, cb, i5, parity, in);
+  hop_dir<2, P, R, DAG>(acc, g, gauge, x, cb, i5, parity, in);
+  hop_dir<3, P, R, DAG>(acc, g, gauge, x, cb, i5, parity, in);
+  const T b = (T)c.b;
+  if (EPI == EPI_PLAIN) {
+#pragma unroll
+    for (int k = 0; k < 12; k++) res.v[k] = b * acc.v[k];
+  } else if (EPI == EPI_XPAY) {
+    Spinor<T> xv;
+    IO::load(xb, g.sstride, j, xv);
+    const T a = (T)c.a;
+#pragma unroll
+    for (int k = 0; k < 12; k++) res.v[k] = mk(fma(a, xv.v[k].r, b * acc.v[k].r), fma(a, xv.v[k].i, b * acc.v[k].i));
+  } else {
+    // M5op(x)(s) = d x(s) - P_- x(s+1) - P_+ x(s-1), mf corners (dagger swaps directions)
+    Spinor<T> xv;
+    IO::load(xb, g.sstride, j, xv);
+    const T d = (T)c.m5d;
+#pragma unroll
+    for (int k = 0; k < 12; k++) res.v[k] = mk(fma(d, xv.v[k].r, b * acc.v[k].r), fma(d, xv.v[k].i, b * acc.v[k].i));
+    const bool top = i5 + 1 == n5, bottom = i5 == 0;
+    const int64_t jp = top ? j - (n5 - 1) : j + 1;
+    const int64_t jm = bottom ? j + (n5 - 1) : j - 1;
+    const T cp = top ? (T)c.mf : T(-1);
+    const T cm = bottom ? (T)c.mf : T(-1);
+    Spinor<T> xp, xm;
+    IO::load(xb, g.sstride, jp, xp);
+    IO::load(xb, g.sstride, jm, xm);
+    if (!DAG) {
+      add_chiral(res, xp, cp, false);
+      add_chiral(res, xm, cm, true);
+    } else {
+      add_chiral(res, xm, cm, false);
+      add_chiral(res, xp, cp, true);
+    }
+  }
+}
+
+template <typename T> __device__ __forceinline__ double norm2_site(const Spinor<T>& res) {
+  T s = T(0);
+#pragma unroll
+  for (int k = 0; k < 12; k++) s = fma(res.v[k].r, res.v[k].r, fma(res.v[k].i, res.v[k].i, s));
+  return (double)s;
+}
+
 template <int P, int R, bool DAG, int EPI, bool RED, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) hop_kernel(const HopArgs A) {
   using T = typename PrecTraits<P>::real;
-  using IO = SpinorIO<P>;
   if (gate_closed(A.gate)) return;
   int parity = A.out_parity;
   int blk = blockIdx.x;
@@ -192,57 +256,11 @@ __global__ void __launch_bounds__(BLOCK) hop_kernel(const HopArgs A) {
   const int64_t j = (int64_t)blk * BLOCK + threadIdx.x;
   double red = 0.0;
   if (j < A.g.nsites) {
-    const int64_t n5 = A.g.n5;
-    int64_t cb, i5;
-    if (n5 == 1) { cb = j; i5 = 0; } else { cb = j / n5; i5 = j - cb * n5; }
-    const Coord x = cb_to_coord(A.g, cb, parity);
-    Spinor<T> acc;
-    zero(acc);
-    hop_dir<0, P, R, DAG>(acc, A, x, cb, i5, parity, in);
-    hop_dir<1, P, R, DAG>(acc, A, x, cb, i5, parity, in);
-    hop_dir<2, P, R, DAG>(acc, A, x, cb, i5, parity, in);
-    hop_dir<3, P, R, DAG>(acc, A, x, cb, i5, parity, in);
-    const T b = (T)A.b;
     Spinor<T> res;
-    if (EPI == EPI_PLAIN) {
-#pragma unroll
-      for (int k = 0; k < 12; k++) res.v[k] = b * acc.v[k];
-    } else if (EPI == EPI_XPAY) {
-      Spinor<T> xv;
-      IO::load(xb, A.g.sstride, j, xv);
-      const T a = (T)A.a;
-#pragma unroll
-      for (int k = 0; k < 12; k++) res.v[k] = mk(fma(a, xv.v[k].r, b * acc.v[k].r), fma(a, xv.v[k].i, b * acc.v[k].i));
-    } else {
-      // M5op(x)(s) = d x(s) - P_- x(s+1) - P_+ x(s-1), mf corners (dagger swaps directions)
-      Spinor<T> xv;
-      IO::load(xb, A.g.sstride, j, xv);
-      const T d = (T)A.m5d;
-#pragma unroll
-      for (int k = 0; k < 12; k++) res.v[k] = mk(fma(d, xv.v[k].r, b * acc.v[k].r), fma(d, xv.v[k].i, b * acc.v[k].i));
-      const bool top = i5 + 1 == n5, bottom = i5 == 0;
-      const int64_t jp = top ? j - (n5 - 1) : j + 1;
-      const int64_t jm = bottom ? j + (n5 - 1) : j - 1;
-      const T cp = top ? (T)A.mf : T(-1);
-      const T cm = bottom ? (T)A.mf : T(-1);
-      Spinor<T> xp, xm;
-      IO::load(xb, A.g.sstride, jp, xp);
-      IO::load(xb, A.g.sstride, jm, xm);
-      if (!DAG) {
-        add_chiral(res, xp, cp, false);
-        add_chiral(res, xm, cm, true);
-      } else {
-        add_chiral(res, xm, cm, false);
-        add_chiral(res, xp, cp, true);
-      }
-    }
-    IO::store(out, A.g.sstride, j, res);
-    if (RED) {
-      T s = T(0);
-#pragma unroll
-      for (int k = 0; k < 12; k++) s = fma(res.v[k].r, res.v[k].r, fma(res.v[k].i, res.v[k].i, s));
-      red = (double)s;
-    }
+    const EpiCoef c{A.a, A.b, A.m5d, A.mf};
+    hop_site<P, R, DAG, EPI>(A.g, A.gauge, in, xb, parity, j, c, res);
+    SpinorIO<P>::store(out, A.g.sstride, j, res);
+    if (RED) red = norm2_site(res);
   }
   if (RED) block_reduce_finalize<BLOCK>(red, (int64_t)blk * BLOCK, A.red);
 }

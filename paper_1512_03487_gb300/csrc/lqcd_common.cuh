@@ -448,6 +448,44 @@ __device__ inline void finalize_totals(const ReduceCtx& rc, const double* totals
   }
 }
 
+// After every block has written its partials rc.partials[s * gridDim.x +
+// blockIdx.x] (s < nsys), the block that finishes last (atomic ticket; no
+// block ever waits for another) sums them per system in a fixed order and
+// runs the finaliser. `sh` is BLOCK doubles of shared scratch. Every thread of
+// the block must call it.
+template <int BLOCK>
+__device__ __forceinline__ void last_block_finalize(const ReduceCtx& rc, double* sh) {
+  __shared__ double totals[64];
+  __shared__ int is_last;
+  const int tid = threadIdx.x;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    unsigned int ticket = atomicAdd(rc.counter, 1u);
+    is_last = ticket == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  for (int s = 0; s < rc.nsys; s++) {
+    double acc = 0.0;
+    const double* part = rc.partials + (int64_t)s * gridDim.x;
+    for (int b = tid; b < (int)gridDim.x; b += BLOCK) acc += __ldcg(part + b);
+    sh[tid] = acc;
+    __syncthreads();
+    for (int w = BLOCK / 2; w > 0; w >>= 1) {
+      if (tid < w) sh[tid] += sh[tid + w];
+      __syncthreads();
+    }
+    if (tid == 0) totals[s] = sh[0];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    finalize_totals(rc, totals);
+    *rc.counter = 0u;
+  }
+}
+
 // Deterministic two-level reduction of one double per thread, grouped by
 // system (thread's system = global index mod nsys when nsys > 1). Per-block
 // partials go to rc.partials; the last block to finish (atomic ticket, no
@@ -456,8 +494,6 @@ __device__ inline void finalize_totals(const ReduceCtx& rc, const double* totals
 template <int BLOCK>
 __device__ __forceinline__ void block_reduce_finalize(double v, int64_t block_first_gid, const ReduceCtx& rc) {
   __shared__ double sh[BLOCK];
-  __shared__ double totals[64];
-  __shared__ int is_last;
   const int tid = threadIdx.x;
   const int nsys = rc.nsys;
   if (nsys == 1) {
@@ -481,32 +517,7 @@ __device__ __forceinline__ void block_reduce_finalize(double v, int64_t block_fi
       rc.partials[(int64_t)tid * gridDim.x + blockIdx.x] = s;
     }
   }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) {
-    unsigned int ticket = atomicAdd(rc.counter, 1u);
-    is_last = ticket == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  for (int s = 0; s < nsys; s++) {
-    double acc = 0.0;
-    const double* part = rc.partials + (int64_t)s * gridDim.x;
-    for (int b = tid; b < (int)gridDim.x; b += BLOCK) acc += __ldcg(part + b);
-    sh[tid] = acc;
-    __syncthreads();
-    for (int w = BLOCK / 2; w > 0; w >>= 1) {
-      if (tid < w) sh[tid] += sh[tid + w];
-      __syncthreads();
-    }
-    if (tid == 0) totals[s] = sh[0];
-    __syncthreads();
-  }
-  if (tid == 0) {
-    finalize_totals(rc, totals);
-    *rc.counter = 0u;
-  }
+  last_block_finalize<BLOCK>(rc, sh);
 }
 
 // System index of a site index j = cb * n5 + i5.
