@@ -237,6 +237,38 @@ int lqcd_cg_solve(void* x_dev, const void* b_dev, const void* gauge_dev,
                   lqcd_solve_info* info, void* workspace_dev, size_t workspace_bytes,
                   void* stream);
 
+/* ---------------------------------------------------------------- no-allocation operator */
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: code running inside a host callback
+ * (cudaLaunchHostFunc), where CUDA calls that allocate are not allowed; code
+ * on a latency-critical path, where cudaMalloc's implicit device
+ * synchronisation is unacceptable; or a plugin whose host framework owns the
+ * whole device memory pool.
+ *
+ * lqcd_M_noalloc computes exactly what lqcd_M computes (same kernels, same
+ * arguments minus tmp_dev): the caller still passes in_dev and out_dev, but
+ * the operator's odd-checkerboard temporaries live in one fixed device array
+ * of LQCD_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU
+ * that loads the library holds until the process exits. The call allocates
+ * nothing (no cudaMalloc, cudaFree or allocating library routine).
+ *  - Limit: the temporaries (one odd checkerboard field, two for domain wall,
+ *    none for subset LQCD_FULL) must fit in the array, e.g. a 24^3 x 48
+ *    FP32 or FP16 Wilson Schur operator fits, its FP64 form does not;
+ *    larger requests return LQCD_ERR_ARG with a message saying so.
+ *  - Set-up: the first call on each device, made with that device current,
+ *    looks up the array's device address (cudaGetSymbolAddress) once; make
+ *    that first call before any stream capture.
+ *  - Sharing: every call on a device uses the same array and the array keeps
+ *    the last call's contents. The operator writes its temporaries before
+ *    reading them, so nothing has to start at zero, but calls whose work
+ *    overlaps on the GPU (different streams, or host threads without
+ *    ordering) race on the array: order them on one stream. */
+#define LQCD_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+int lqcd_M_noalloc(void* out_dev, const void* in_dev, const void* gauge_dev,
+                   const lqcd_lattice* lat, const lqcd_operator* op, int subset, int dagger,
+                   void* stream);
+
 /* ---------------------------------------------------------------- force */
 
 /* Pseudofermion force for S = phi^dag (M^dag M)^-1 phi with M = D_W (Grid

@@ -79,6 +79,7 @@ SIGNATURES = {
     "lqcd_cg_workspace_bytes": (_SZ, [_LAT, _OP, _PRM, _I]),
     "lqcd_cg_solve": (_I, [_P, _P, _P, _P, _LAT, _OP, _PRM, _I, _INFO, _P, _SZ, _P]),
     "lqcd_force": (_I, [_P, _P, _P, _P, _LAT, _OP, _I, _P]),
+    "lqcd_M_noalloc": (_I, [_P, _P, _P, _LAT, _OP, _I, _I, _P]),
 }
 
 

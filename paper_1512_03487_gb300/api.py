@@ -155,6 +155,13 @@ def lqcd_M(out, inp, gauge, lat, op, subset, dagger, tmp, stream=None):
                       _ptr(tmp), _stream(stream)))
 
 
+def lqcd_M_noalloc(out, inp, gauge, lat, op, subset, dagger, stream=None):
+    """lqcd_M without a workspace argument, for callers that cannot allocate
+    device memory; the temporaries live in a fixed array inside the library."""
+    _check(lib.lqcd_M_noalloc(_ptr(out), _ptr(inp), _ptr(gauge), C.byref(lat), C.byref(op), subset,
+                              int(dagger), _stream(stream)))
+
+
 def lqcd_MdagM(out, inp, gauge, lat, op, subset, tmp, stream=None):
     _check(lib.lqcd_MdagM(_ptr(out), _ptr(inp), _ptr(gauge), C.byref(lat), C.byref(op), subset, _ptr(tmp),
                           _stream(stream)))
