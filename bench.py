@@ -34,6 +34,7 @@ METRIC = "Dslash GFLOP/s & HBM-roofline %; mixed vs FP64 CG time to 1e-10 residu
 FLOP_PER_SITE = 1320
 BC = (1.0, 1.0, 1.0, -1.0)
 WORKLOAD = "wilson_eo_cg_24x24x24x48_m0.01_exp0.3_tol1e-10"
+DELTA = 0.003
 PROFILE_JSON = os.path.join(ROOT, "profiles", "hop_f16r12_24x24x24x48.json")
 DSLASH_SOURCES = ["dslash_kernels.cuh", "lqcd_common.cuh", "dslash_launch.cuh", "dslash_f16.cu"]
 
@@ -48,6 +49,8 @@ def parse_args():
     ap.add_argument("--mass", type=float, default=0.01)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the domain-wall, multi-RHS, batch and force measurements")
     ap.add_argument("--mode", choices=["full", "step", "hop"], default="full",
                     help="step: only the timed solves; hop: only the dominant kernel's roofline loop")
     return ap.parse_args()
@@ -184,8 +187,10 @@ def run_lqcd(args, world, rank, local):
     src = F.empty(L.lqcd_spinor_bytes(lat, L.LQCD_F64, L.LQCD_EVEN))
     x = F.empty(L.lqcd_spinor_bytes(lat, L.LQCD_F64, L.LQCD_FULL))
     tmp = F.empty(L.lqcd_operator_workspace_bytes(lat, op64, L.LQCD_EVEN))
+    # delta = 0.003: the reliable-update threshold that minimised the FP16 solve time in a sweep
+    # over 0.1 ... 0.001 on this workload (4 FP64 residual recomputations instead of 10 at 0.1)
     prms = {p: L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=p, sloppy_recon=12 if p else 18,
-                               delta=0.1, check_interval=32) for p in (0, 1, 2)}
+                               delta=DELTA, check_interval=64) for p in (0, 1, 2)}
     ws = F.empty(max(L.lqcd_cg_workspace_bytes(lat, op64, prms[p], L.LQCD_EVEN) for p in (0, 1, 2)))
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
@@ -275,6 +280,13 @@ def run_lqcd(args, world, rank, local):
         e2e = run_e2e(L, F, lat, op64, U, b, prms[2], ws, tmp, x, gs[2], g64, bfull, bhat, src, flush,
                       stream, vh, args, world)
 
+    # ---- the other hot-path workloads (domain wall, multi-RHS, uneven batch, force)
+    extras = None
+    if not args.no_extras:
+        del U_dev, g64, gs, ws, tmp, x, bfull, bhat, src
+        torch.cuda.empty_cache()
+        extras = run_extras(L, F, flush, stream)
+
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "GFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 3),
@@ -282,7 +294,7 @@ def run_lqcd(args, world, rank, local):
         "dtype": "f32 arithmetic on f16 storage, f64 reliable updates",
         "data": "synthetic (seeded exp(0.3 i H) links, Gaussian source)",
         "config": {"workload": WORKLOAD, "lattice": list(dims), "mass": mass, "bc": list(BC),
-                   "solver": "even-odd CG on M_hat^dag M_hat, FP16+norm / 12-real inner, delta 0.1",
+                   "solver": f"even-odd CG on M_hat^dag M_hat, FP16+norm / 12-real inner, delta {DELTA}",
                    "tol": 1e-10, "l2": "flushed (512 MB write) before every timed step",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "full_system_rel_residual": res,
@@ -294,6 +306,8 @@ def run_lqcd(args, world, rank, local):
     }
     if e2e is not None:
         line["e2e"] = e2e
+    if extras is not None:
+        line["extras"] = extras
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         gf, dt = oracle_gflops(U, b, mass, 1)
         line["cpu_baseline"] = {"value": round(gf, 4), "unit": "GFLOP/s", "cores": threads_used(),
@@ -396,6 +410,196 @@ def run_e2e(L, F, lat, op64, U, b, prm, ws, tmp, x, g16, g64, bfull, bhat, src, 
     return {"value": round(flops / total / 1e9, 1), "unit": "GFLOP/s",
             "h2d_bytes_per_step": int(U_h.numel() * 8 + b_h.numel() * 8),
             "d2h_bytes_per_step": int(x_h.numel() * 8), "ms_per_step": round(total / args.steps * 1e3, 3)}
+
+
+# ------------------------------------------------------------------ other workloads
+
+def _events_time(fn, stream, flush=None, reps=1):
+    import torch
+    best = None
+    out = None
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None else min(best, t)
+    return best, out
+
+
+def _hop_gbs(L, F, lat, prec, recon, bytes_per_site, flush, stream, kind=0, n=10):
+    """Cold-L2 time of one hop launch (one checkerboard) and its algorithmic GB/s."""
+    import torch
+    op = L.operator(kind=kind, prec=prec, recon=recon)
+    nsites = lat.dims[0] * lat.dims[1] * lat.dims[2] * lat.dims[3] // 2 * lat.n5
+    g = F.empty(L.lqcd_gauge_bytes(lat, prec, recon))
+    g.zero_()
+    fin = F.empty(L.lqcd_spinor_bytes(lat, prec, L.LQCD_ODD))
+    fin.zero_()
+    out = F.empty(L.lqcd_spinor_bytes(lat, prec, L.LQCD_EVEN))
+    for _ in range(2):
+        L.lqcd_dslash(out, fin, g, lat, op, L.LQCD_EVEN, 0)
+    ts = []
+    for _ in range(n):
+        t, _ = _events_time(lambda: L.lqcd_dslash(out, fin, g, lat, op, L.LQCD_EVEN, 0), stream, flush)
+        ts.append(t)
+    t = float(np.mean(ts)) * 1e-3
+    peak, _ = measured_peak()
+    gbs = bytes_per_site * nsites / t / 1e9
+    return {"launch_us": round(t * 1e6, 2), "algorithmic_bytes_per_site": bytes_per_site, "achieved_gbs": round(gbs, 1),
+            "frac_of_measured_hbm": round(gbs / peak, 4), "gflops": round(FLOP_PER_SITE * nsites / t / 1e9, 1)}
+
+
+def run_extras(L, F, flush, stream):
+    """Domain-wall, multi-RHS, uneven-batch and force workloads, one timed run each."""
+    import torch
+    from synthetic import config_seed, gauge_field, gaussian_spinor
+    out = {}
+
+    # 16^4 x L_s = 16 domain wall, M5 = 1.8, mf = 0.02, Haar links, FP32-inner mixed CG to 1e-10
+    dims, Ls = (16, 16, 16, 16), 16
+    U = gauge_field(dims, "haar", config_seed(2, 0))
+    b = gaussian_spinor(dims, config_seed(2, 1), lead=(Ls,))
+    lat = L.lattice(dims, n5=Ls, bc=BC)
+    op = L.operator(kind=L.LQCD_DWF, M5=1.8, mf=0.02)
+    g64 = F.gauge_to_device(U, lat, 0, 18)
+    g32 = F.gauge_to_device(U, lat, 1, 12)
+    bd = F.spinor_to_device(b, lat, 0, 2)
+    del b
+    tmp = F.empty(L.lqcd_operator_workspace_bytes(lat, op, 0))
+    bhat = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
+    src = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
+    x = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
+    prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=12, delta=DELTA, check_interval=64)
+    ws = F.empty(L.lqcd_cg_workspace_bytes(lat, op, prm, 0))
+
+    def dwf_solve():
+        L.lqcd_eo_prepare(bhat, bd, g64, lat, op, tmp)
+        L.lqcd_M(src, bhat, g64, lat, op, L.LQCD_EVEN, 1, tmp)
+        info = L.lqcd_cg_solve(x, src, g64, g32, lat, op, prm, L.LQCD_EVEN, ws)
+        L.lqcd_eo_reconstruct(x, bd, g64, lat, op, tmp)
+        return info
+
+    dwf_solve()
+    ms, info = _events_time(dwf_solve, stream, flush)
+    dx = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
+    L.lqcd_M(dx, x, g64, lat, op, L.LQCD_FULL, 0, None)
+    n = 2 * 16 ** 4 * Ls * 24
+    a = torch.empty(n, dtype=torch.float64, device="cuda")
+    bb = torch.empty(n, dtype=torch.float64, device="cuda")
+    L.lqcd_spinor_unpack(a, dx, 0, 2, lat)
+    L.lqcd_spinor_unpack(bb, bd, 0, 2, lat)
+    res = float(torch.linalg.vector_norm(a - bb) / torch.linalg.vector_norm(bb))
+    hops = 1 + 2 + 4 * (info.iterations + info.reliable_updates) + 1
+    out["dwf_16x4_ls16_mixed_fp32"] = {
+        "ms": round(ms, 3), "iterations": info.iterations, "reliable_updates": info.reliable_updates,
+        "full_system_rel_residual": res,
+        "dslash_gflops_in_solve": round(hops * FLOP_PER_SITE * 16 ** 4 // 2 * Ls / (ms * 1e-3) / 1e9, 1),
+        "hop_f32r12_ls16": _hop_gbs(L, F, lat, 1, 12, 8 * 48 / Ls + 96 + 96, flush, stream, kind=L.LQCD_DWF)}
+    del g64, g32, bd, tmp, bhat, src, x, ws, dx, a, bb
+    torch.cuda.empty_cache()
+
+    # 32^4 with 12 right-hand sides sharing the links, m = 0.01, FP16-inner mixed CG per RHS to 1e-10
+    dims, nr = (32, 32, 32, 32), 12
+    U = gauge_field(dims, "haar", config_seed(3, 0))
+    lat = L.lattice(dims, n5=nr, bc=BC)
+    op = L.operator(mass=0.01)
+    g64 = F.gauge_to_device(U, lat, 0, 18)
+    g16 = F.gauge_to_device(U, lat, 2, 12)
+    del U
+    rhs = gaussian_spinor(dims, config_seed(3, 1), lead=(nr,))
+    be = F.spinor_to_device(F.checkerboard(rhs, 0), lat, 0, 0)
+    del rhs
+    x = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
+    prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=2, sloppy_recon=12, delta=DELTA, check_interval=64)
+    ws = F.empty(L.lqcd_cg_workspace_bytes(lat, op, prm, 0))
+    L.lqcd_cg_solve(x, be, g64, g16, lat, op, prm, 0, ws)
+    ms, info = _events_time(lambda: L.lqcd_cg_solve(x, be, g64, g16, lat, op, prm, 0, ws), stream, flush)
+    vh = 32 ** 4 // 2
+    out["multi_rhs_32x4_12rhs_mixed_fp16"] = {
+        "ms": round(ms, 3), "iterations": info.iterations, "reliable_updates": info.reliable_updates,
+        "max_true_rel_residual_normal_eq": info.true_rel_residual,
+        "dslash_gflops_in_solve": round(4 * (info.iterations + info.reliable_updates) * FLOP_PER_SITE * vh * nr
+                                        / (ms * 1e-3) / 1e9, 1),
+        "hop_f16r12_12rhs": _hop_gbs(L, F, lat, 2, 12, 8 * 24 / nr + 52 + 52, flush, stream),
+        "hop_f16r12_1rhs": _hop_gbs(L, F, L.lattice(dims, n5=1, bc=BC), 2, 12, 8 * 24 + 52 + 52, flush, stream)}
+    del g64, g16, be, x, ws
+    torch.cuda.empty_cache()
+
+    # uneven batch: 4 each of 8^4, 12^4, 16^4, 20^4, Haar links, m = 0.05, FP32-inner, one persistent launch per phase
+    shapes = [(n_, n_, n_, n_) for n_ in (8, 12, 16, 20) for _ in range(4)]
+    entries = []
+    for k, dims in enumerate(shapes):
+        lat = L.lattice(dims, bc=BC)
+        U = gauge_field(dims, "haar", config_seed(30 + k, 0))
+        bsrc = F.checkerboard(gaussian_spinor(dims, config_seed(30 + k, 1), lead=(1,)), 0)
+        entries.append(dict(lat=lat, mass=0.05, gauge=F.gauge_to_device(U, lat, 0, 18),
+                            gauge_sloppy=F.gauge_to_device(U, lat, 1, 12),
+                            x=F.empty(L.lqcd_spinor_bytes(lat, 0, 0)), b=F.spinor_to_device(bsrc, lat, 0, 0)))
+    items = L.batch_items(entries)
+    prm = L.solver_params(tol=1e-10, maxiter=5000, sloppy_prec=1, sloppy_recon=12, delta=DELTA, check_interval=64)
+    wsb = F.empty(L.lqcd_batch_cg_workspace_bytes(len(entries), items, 18, prm))
+    L.lqcd_batch_cg_solve(len(entries), items, 18, prm, wsb)  # tunes the grid, captures the graph
+    ms_b, infos = _events_time(lambda: L.lqcd_batch_cg_solve(len(entries), items, 18, prm, wsb), stream, flush)
+    op = L.operator(mass=0.05)
+    wss = [F.empty(L.lqcd_cg_workspace_bytes(e["lat"], op, prm, 0)) for e in entries]
+
+    def sequential():
+        its = []
+        for e, w in zip(entries, wss):
+            its.append(L.lqcd_cg_solve(e["x"], e["b"], e["gauge"], e["gauge_sloppy"], e["lat"], op, prm, 0, w))
+        return its
+
+    sequential()
+    ms_s, seq = _events_time(sequential, stream, flush)
+    out["uneven_batch_4x_8_12_16_20"] = {
+        "ms_persistent_batch": round(ms_b, 3), "ms_16_sequential_solves": round(ms_s, 3),
+        "speedup": round(ms_s / ms_b, 2), "iterations": infos[0].iterations,
+        "reliable_updates": infos[0].reliable_updates,
+        "max_true_rel_residual_normal_eq": max(i.true_rel_residual for i in infos),
+        "tuned_shapes": L.lqcd_tune_entries()}
+    del entries, items, wsb, wss
+    torch.cuda.empty_cache()
+
+    # force on 16^4: X = (M^dag M)^-1 phi (FP32-inner mixed, FP64 reliable updates), Y = M X, force kernel
+    dims = (16, 16, 16, 16)
+    U = gauge_field(dims, "haar", config_seed(4, 0))
+    phi = gaussian_spinor(dims, config_seed(4, 1), lead=(1,))
+    lat = L.lattice(dims, bc=BC)
+    op = L.operator(mass=0.05)
+    g64 = F.gauge_to_device(U, lat, 0, 18)
+    g32 = F.gauge_to_device(U, lat, 1, 18)
+    phid = F.spinor_to_device(phi, lat, 0, 2)
+    X = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
+    Y = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
+    Fo = F.empty(L.lqcd_gauge_bytes(lat, 0, 18))
+    prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=18, delta=DELTA, check_interval=64)
+    ws = F.empty(L.lqcd_cg_workspace_bytes(lat, op, prm, 2))
+
+    def force_step():
+        info = L.lqcd_cg_solve(X, phid, g64, g32, lat, op, prm, L.LQCD_FULL, ws)
+        L.lqcd_M(Y, X, g64, lat, op, L.LQCD_FULL, 0, None)
+        L.lqcd_force(Fo, g64, X, Y, lat, op, L.LQCD_FORCE_TA)
+        return info
+
+    force_step()
+    ms, info = _events_time(force_step, stream, flush)
+    tk, _ = _events_time(lambda: L.lqcd_force(Fo, g64, X, Y, lat, op, L.LQCD_FORCE_TA), stream, flush, reps=5)
+    V = 16 ** 4
+    fbytes = V * (2 * 192 + 4 * 144 + 4 * 144)  # X, Y once per site, 4 links in, 4 force matrices out
+    peak, _ = measured_peak()
+    out["force_16x4"] = {"ms_solve_and_force": round(ms, 3), "iterations": info.iterations,
+                         "reliable_updates": info.reliable_updates,
+                         "force_kernel_us": round(tk * 1e3, 2),
+                         "force_kernel_algorithmic_gbs": round(fbytes / (tk * 1e-3) / 1e9, 1),
+                         "force_kernel_frac_of_measured_hbm": round(fbytes / (tk * 1e-3) / 1e9 / peak, 4)}
+    return out
 
 
 # ------------------------------------------------------------------ reference arm

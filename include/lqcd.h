@@ -237,6 +237,41 @@ int lqcd_cg_solve(void* x_dev, const void* b_dev, const void* gauge_dev,
                   lqcd_solve_info* info, void* workspace_dev, size_t workspace_bytes,
                   void* stream);
 
+/* ---------------------------------------------------------------- batched solves */
+
+/* One lattice of a batched solve: independent Wilson systems of different
+ * sizes solved together (the paper's Grid objects of different geometry
+ * active at once, Sec. 2.4, with CG of Sec. 4 on each). */
+typedef struct {
+    lqcd_lattice lat;          /* this instance's geometry; n5 must be 1 */
+    double mass;               /* this instance's Wilson bare mass m */
+    const void* gauge;         /* FP64 links, device layout, recon as passed to the call */
+    const void* gauge_sloppy;  /* links in (sloppy_prec, sloppy_recon); NULL if sloppy_prec is LQCD_F64 */
+    void* x;                   /* FP64 even-checkerboard solution (written) */
+    const void* b;             /* FP64 even-checkerboard source */
+} lqcd_batch_item;
+
+/* Solves M_hat_i^dag M_hat_i x_i = b_i (Wilson, even-odd) for n <= 64
+ * instances at once with the CG of lqcd_cg_solve (FP64 or mixed precision,
+ * per-instance alpha, beta, reliable updates and convergence). Every phase of
+ * an iteration is one persistent launch over a work list of (instance, tile)
+ * pairs; the number of resident blocks per SM is chosen by timing candidates
+ * on the first solve of each batch shape (see lqcd_tune_save). infos: n
+ * entries (iterations and reliable updates are shared, true residuals are per
+ * instance). Synchronises the stream. workspace: lqcd_batch_cg_workspace_bytes()
+ * bytes, 256-byte aligned. */
+size_t lqcd_batch_cg_workspace_bytes(int n, const lqcd_batch_item* items, int recon,
+                                     const lqcd_solver_params* params);
+int lqcd_batch_cg_solve(int n, const lqcd_batch_item* items, int recon, const lqcd_solver_params* params,
+                        lqcd_solve_info* infos, void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* The autotuner's table (batch shape -> resident blocks per SM): write it to
+ * a text file, read it back (entries found in the file replace the current
+ * ones), and count its entries. */
+int lqcd_tune_save(const char* path);
+int lqcd_tune_load(const char* path);
+int lqcd_tune_entries(void);
+
 /* ---------------------------------------------------------------- no-allocation operator */
 
 /* The paper has no counterpart to this entry point; it exists for callers

@@ -47,6 +47,11 @@ class lqcd_solve_info(C.Structure):
                 ("time_ms", C.c_double), ("status", C.c_int)]
 
 
+class lqcd_batch_item(C.Structure):
+    _fields_ = [("lat", lqcd_lattice), ("mass", C.c_double), ("gauge", C.c_void_p), ("gauge_sloppy", C.c_void_p),
+                ("x", C.c_void_p), ("b", C.c_void_p)]
+
+
 _P = C.c_void_p
 _LAT = C.POINTER(lqcd_lattice)
 _OP = C.POINTER(lqcd_operator)
@@ -80,6 +85,11 @@ SIGNATURES = {
     "lqcd_cg_solve": (_I, [_P, _P, _P, _P, _LAT, _OP, _PRM, _I, _INFO, _P, _SZ, _P]),
     "lqcd_force": (_I, [_P, _P, _P, _P, _LAT, _OP, _I, _P]),
     "lqcd_M_noalloc": (_I, [_P, _P, _P, _LAT, _OP, _I, _I, _P]),
+    "lqcd_batch_cg_workspace_bytes": (_SZ, [_I, C.c_void_p, _I, _PRM]),
+    "lqcd_batch_cg_solve": (_I, [_I, C.c_void_p, _I, _PRM, C.c_void_p, _P, _SZ, _P]),
+    "lqcd_tune_save": (_I, [C.c_char_p]),
+    "lqcd_tune_load": (_I, [C.c_char_p]),
+    "lqcd_tune_entries": (_I, []),
 }
 
 

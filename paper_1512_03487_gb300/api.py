@@ -188,6 +188,46 @@ def lqcd_cg_solve(x, b, gauge, gauge_sloppy, lat, op, params, subset, workspace,
     return info
 
 
+def batch_items(entries):
+    """Array of lqcd_batch_item from dicts with keys lat, mass, gauge,
+    gauge_sloppy (may be None), x, b (tensors or device pointers)."""
+    arr = (_lib.lqcd_batch_item * len(entries))()
+    for i, e in enumerate(entries):
+        arr[i].lat = e["lat"]
+        arr[i].mass = float(e["mass"])
+        arr[i].gauge = _ptr(e["gauge"])
+        arr[i].gauge_sloppy = _ptr(e.get("gauge_sloppy"))
+        arr[i].x = _ptr(e["x"])
+        arr[i].b = _ptr(e["b"])
+    return arr
+
+
+def lqcd_batch_cg_workspace_bytes(n, items, recon, params) -> int:
+    return int(lib.lqcd_batch_cg_workspace_bytes(n, C.cast(items, C.c_void_p), recon, C.byref(params)))
+
+
+def lqcd_batch_cg_solve(n, items, recon, params, workspace, stream=None, raise_on_error=True):
+    infos = (lqcd_solve_info * n)()
+    nbytes = workspace.numel() * workspace.element_size()
+    st = lib.lqcd_batch_cg_solve(n, C.cast(items, C.c_void_p), recon, C.byref(params), C.cast(infos, C.c_void_p),
+                                 _ptr(workspace), nbytes, _stream(stream))
+    if raise_on_error:
+        _check(st)
+    return list(infos)
+
+
+def lqcd_tune_save(path: str) -> None:
+    _check(lib.lqcd_tune_save(path.encode()))
+
+
+def lqcd_tune_load(path: str) -> None:
+    _check(lib.lqcd_tune_load(path.encode()))
+
+
+def lqcd_tune_entries() -> int:
+    return int(lib.lqcd_tune_entries())
+
+
 def lqcd_force(out, gauge, X, Y, lat, op, kind, stream=None):
     _check(lib.lqcd_force(_ptr(out), _ptr(gauge), _ptr(X), _ptr(Y), C.byref(lat), C.byref(op), kind,
                           _stream(stream)))

@@ -13,6 +13,7 @@ static std::atomic<uint64_t> g_launches{0};
 // Set while a thread captures a CUDA graph: captured launches are counted when
 // the graph is replayed, not when they are recorded.
 thread_local bool g_count_suspended = false;
+thread_local uint64_t g_captured_launches = 0;
 
 int fail(int code, const char* fmt, ...) {
   va_list ap;
@@ -27,7 +28,8 @@ int cuda_fail(cudaError_t e, const char* what) {
 }
 
 void count_launches(uint64_t n) {
-  if (!g_count_suspended) g_launches.fetch_add(n, std::memory_order_relaxed);
+  if (g_count_suspended) g_captured_launches += n;
+  else g_launches.fetch_add(n, std::memory_order_relaxed);
 }
 
 int after_launch(const char* what) {
@@ -51,7 +53,8 @@ int make_geom(const lqcd_lattice* lat, Geom* g) {
       return fail(LQCD_ERR_ARG, "extent %d in direction %d must be even for checkerboarding", lat->dims[mu], mu);
   if (lat->n5 < 1) return fail(LQCD_ERR_ARG, "n5 = %d < 1", lat->n5);
   const int64_t V = (int64_t)lat->dims[0] * lat->dims[1] * lat->dims[2] * lat->dims[3];
-  if (V / 2 * lat->n5 > (int64_t)1 << 31) return fail(LQCD_ERR_ARG, "lattice too large");
+  if (V >= ((int64_t)1 << 31) || V / 2 * lat->n5 >= ((int64_t)1 << 31))
+    return fail(LQCD_ERR_ARG, "lattice too large: the 4D volume and V/2 * n5 must stay below 2^31");
   g->X = lat->dims[0];
   g->Y = lat->dims[1];
   g->Z = lat->dims[2];
@@ -66,6 +69,14 @@ int make_geom(const lqcd_lattice* lat, Geom* g) {
     g->bcd[mu] = lat->bc[mu];
     g->bcf[mu] = (float)lat->bc[mu];
   }
+  g->fXh = make_fastdiv((uint32_t)g->Xh);
+  g->fY = make_fastdiv((uint32_t)g->Y);
+  g->fZ = make_fastdiv((uint32_t)g->Z);
+  g->fn5 = make_fastdiv((uint32_t)g->n5);
+  g->st[0] = 1;
+  g->st[1] = g->X;
+  g->st[2] = g->X * g->Y;
+  g->st[3] = g->X * g->Y * g->Z;
   return LQCD_OK;
 }
 

@@ -23,11 +23,10 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <vector>
 
+#include "cg_engine.h"
 #include "cg_site.cuh"
-#include "lqcd_internal.h"
 
 namespace lqcd {
 
@@ -224,35 +223,45 @@ static int launch_vec(VecKernel k, int sloppy, const VecArgs& a, cudaStream_t s)
   return after_launch("cg vector kernel");
 }
 
-// Kernel launches are counted when they run: a thread capturing a graph
-// suspends counting and the replay adds the graph's node count.
-extern thread_local bool g_count_suspended;
-
-struct Solver {
+struct Solver : CgEngine {
   Geom g;
   lqcd_operator op64, ops;
   lqcd_solver_params prm;
-  int subset, nsys;
+  int subset;
   Workspace w;
   const void* gauge64;
   const void* gauge_s;
   VecArgs va;
-  ReduceCtx rc_alpha, rc_update, rc_reliable;
+  ReduceCtx rc_init, rc_alpha, rc_update, rc_reliable;
 
-  int inner_iteration(cudaStream_t s) {
+  int init(cudaStream_t s) override {
+    cudaError_t e = cudaMemsetAsync(w.counter, 0, 64, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cg: memset");
+    VecArgs a = va;
+    a.red = rc_init;
+    return launch_vec(VK_INIT, prm.sloppy_prec, a, s);
+  }
+
+  int head(cudaStream_t s, int cond, cudaGraphConditionalHandle h_rel) override {
     OpCtx cs{g, ops, gauge_s};
     int st = op_apply(cs, w.mp, w.p, subset, 0, w.t1_s, w.t2_s, &rc_alpha, w.ctrl, s);
     if (st) return st;
     if ((st = op_apply(cs, w.ap, w.mp, subset, 1, w.t1_s, w.t2_s, nullptr, w.ctrl, s))) return st;
     VecArgs a = va;
     a.red = rc_update;
+    a.red.cond = cond;
+    a.red.h_rel = h_rel;
     a.gate = w.ctrl;
-    if ((st = launch_vec(VK_UPDATE, prm.sloppy_prec, a, s))) return st;
+    return launch_vec(VK_UPDATE, prm.sloppy_prec, a, s);
+  }
+
+  int tail(cudaStream_t s) override {
+    VecArgs a = va;
     a.gate = w.ctrl;
     return launch_vec(VK_PUPDATE, prm.sloppy_prec, a, s);
   }
 
-  int reliable_update(cudaStream_t s) {
+  int reliable(cudaStream_t s) override {
     VecArgs a = va;
     int st = launch_vec(VK_ACCUM, prm.sloppy_prec, a, s);
     if (st) return st;
@@ -260,93 +269,9 @@ struct Solver {
     if ((st = op_apply(c64, w.mid64, a.x64, subset, 0, w.t1_64, w.t2_64, nullptr, nullptr, s))) return st;
     if ((st = op_apply(c64, w.ax64, w.mid64, subset, 1, w.t1_64, w.t2_64, nullptr, nullptr, s))) return st;
     a.red = rc_reliable;
-    if ((st = launch_vec(VK_RESIDUAL, prm.sloppy_prec, a, s))) return st;
-    a.gate = w.ctrl;
-    return launch_vec(VK_PUPDATE, prm.sloppy_prec, a, s);
+    return launch_vec(VK_RESIDUAL, prm.sloppy_prec, a, s);
   }
 };
-
-
-// ------------------------------------------------------------------ chunk-graph cache
-// Everything a captured chunk bakes into its launches (pointers, geometry,
-// operator, sloppy format, chunk length, iteration cap).
-struct GraphKey {
-  int device;
-  const void* x;
-  const void* b;
-  const void* gauge_s;
-  const void* ws;
-  lqcd_lattice lat;
-  lqcd_operator op;
-  int sloppy_prec, sloppy_recon, chunk, maxiter, subset;
-};
-
-struct GraphEntry {
-  GraphKey key;
-  cudaGraphExec_t exec;
-  uint64_t nodes;
-  uint64_t last_use;
-};
-
-static std::mutex g_graph_mutex;
-static std::vector<GraphEntry> g_graphs;
-static uint64_t g_graph_clock = 0;
-constexpr size_t MAX_GRAPHS = 16;
-
-static int chunk_graph(Solver& S, const GraphKey& key, cudaGraphExec_t* exec, uint64_t* nodes) {
-  std::lock_guard<std::mutex> lock(g_graph_mutex);
-  for (auto& e : g_graphs) {
-    if (memcmp(&e.key, &key, sizeof(GraphKey)) == 0) {
-      e.last_use = ++g_graph_clock;
-      *exec = e.exec;
-      *nodes = e.nodes;
-      return LQCD_OK;
-    }
-  }
-  cudaStream_t cap;
-  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-  if (e != cudaSuccess) return cuda_fail(e, "cg: stream create");
-  cudaGraph_t graph = nullptr;
-  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) {
-    cudaStreamDestroy(cap);
-    return cuda_fail(e, "cg: begin capture");
-  }
-  int st = LQCD_OK;
-  g_count_suspended = true;
-  for (int i = 0; i < key.chunk && st == LQCD_OK; i++) st = S.inner_iteration(cap);
-  g_count_suspended = false;
-  e = cudaStreamEndCapture(cap, &graph);
-  cudaStreamDestroy(cap);
-  if (st) {
-    if (graph) cudaGraphDestroy(graph);
-    return st;
-  }
-  if (e != cudaSuccess) return cuda_fail(e, "cg: end capture");
-  size_t n = 0;
-  cudaGraphGetNodes(graph, nullptr, &n);
-  cudaGraphExec_t ex = nullptr;
-  e = cudaGraphInstantiate(&ex, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return cuda_fail(e, "cg: graph instantiate");
-  if (g_graphs.size() >= MAX_GRAPHS) {
-    size_t lru = 0;
-    for (size_t i = 1; i < g_graphs.size(); i++)
-      if (g_graphs[i].last_use < g_graphs[lru].last_use) lru = i;
-    cudaGraphExecDestroy(g_graphs[lru].exec);
-    g_graphs.erase(g_graphs.begin() + lru);
-  }
-  g_graphs.push_back(GraphEntry{key, ex, (uint64_t)n, ++g_graph_clock});
-  *exec = ex;
-  *nodes = n;
-  return LQCD_OK;
-}
-
-void release_graph_cache() {
-  std::lock_guard<std::mutex> lock(g_graph_mutex);
-  for (auto& e : g_graphs) cudaGraphExecDestroy(e.exec);
-  g_graphs.clear();
-}
 
 }  // namespace lqcd
 
@@ -369,7 +294,6 @@ int lqcd_cg_solve(void* x, const void* b, const void* gauge, const void* gauge_s
                   void* workspace, size_t workspace_bytes, void* stream) {
   const auto t0 = std::chrono::steady_clock::now();
   lqcd_solve_info local;
-  memset(&local, 0, sizeof(local));
   lqcd_solve_info* inf = info ? info : &local;
   memset(inf, 0, sizeof(*inf));
   auto finish = [&](int status) {
@@ -394,6 +318,8 @@ int lqcd_cg_solve(void* x, const void* b, const void* gauge, const void* gauge_s
   S.w = carve(workspace, S.g, *op, *prm, subset, S.nsys);
   if (workspace_bytes < S.w.total)
     return finish(fail(LQCD_ERR_WORKSPACE, "cg: workspace %zu < %zu bytes", workspace_bytes, S.w.total));
+  S.ctrl = S.w.ctrl;
+  S.sys = S.w.sys;
   S.op64 = *op;
   S.ops = *op;
   S.ops.prec = prm->sloppy_prec;
@@ -427,10 +353,11 @@ int lqcd_cg_solve(void* x, const void* b, const void* gauge, const void* gauge_s
   base.sys = S.w.sys;
   base.ctrl = S.w.ctrl;
   base.nsys = S.nsys;
-  ReduceCtx rc_init = base;
-  rc_init.fin = FIN_INIT;
-  rc_init.tol2_rel = prm->tol * prm->tol;
-  rc_init.delta2 = prm->sloppy_prec == LQCD_F64 ? 0.0 : prm->delta * prm->delta;
+  a.red = base;
+  S.rc_init = base;
+  S.rc_init.fin = FIN_INIT;
+  S.rc_init.tol2_rel = prm->tol * prm->tol;
+  S.rc_init.delta2 = prm->sloppy_prec == LQCD_F64 ? 0.0 : prm->delta * prm->delta;
   S.rc_alpha = base;
   S.rc_alpha.fin = FIN_ALPHA;
   S.rc_update = base;
@@ -438,90 +365,52 @@ int lqcd_cg_solve(void* x, const void* b, const void* gauge, const void* gauge_s
   S.rc_update.maxiter = prm->maxiter;
   S.rc_reliable = base;
   S.rc_reliable.fin = FIN_RELIABLE;
-  a.red = base;
 
-  cudaError_t e = cudaMemsetAsync(S.w.counter, 0, 64, s);
-  if (e != cudaSuccess) return finish(cuda_fail(e, "cg: memset"));
-  {
-    VecArgs ai = a;
-    ai.red = rc_init;
-    if ((st = launch_vec(VK_INIT, prm->sloppy_prec, ai, s))) return finish(st);
+  // what the captured graph bakes in (tol and delta live in device state, not in the graph)
+  std::vector<unsigned char> key;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  key_append(key, 1);  // single-lattice solver
+  key_append(key, dev);
+  key_append(key, x);
+  key_append(key, b);
+  key_append(key, gauge);
+  key_append(key, gauge_sloppy);
+  key_append(key, workspace);
+  for (int mu = 0; mu < 4; mu++) {
+    key_append(key, lat->dims[mu]);
+    key_append(key, lat->bc[mu]);
   }
+  key_append(key, lat->n5);
+  key_append(key, op->kind);
+  key_append(key, op->mass);
+  key_append(key, op->M5);
+  key_append(key, op->mf);
+  key_append(key, op->recon);
+  key_append(key, prm->sloppy_prec);
+  key_append(key, prm->sloppy_recon);
+  key_append(key, S.prm.check_interval);
+  key_append(key, prm->maxiter);
+  key_append(key, subset);
 
-  // The chunk: check_interval inner iterations, captured once as a graph and
-  // cached across solves with the same buffers and parameters.
-  const int chunk = S.prm.check_interval;
-  cudaGraphExec_t exec = nullptr;
-  uint64_t nodes_per_chunk = 0;
-  if (prm->use_graph) {
-    GraphKey key;
-    memset(&key, 0, sizeof(key));
-    cudaGetDevice(&key.device);
-    key.x = x;
-    key.b = b;
-    key.gauge_s = gauge_sloppy;
-    key.ws = workspace;
-    key.lat = *lat;
-    key.op = *op;
-    key.sloppy_prec = prm->sloppy_prec;
-    key.sloppy_recon = prm->sloppy_recon;
-    key.chunk = chunk;
-    key.maxiter = prm->maxiter;
-    key.subset = subset;
-    if ((st = chunk_graph(S, key, &exec, &nodes_per_chunk))) return finish(st);
-  }
   Control ctrl;
-  int reliable = 0;
-  int status = LQCD_OK;
-  for (;;) {
-    e = cudaMemcpyAsync(&ctrl, S.w.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) { status = cuda_fail(e, "cg: control readback"); break; }
-    if (ctrl.reason & REASON_NAN) { status = fail(LQCD_ERR_NAN, "cg: NaN/Inf or non-positive p^dag A p"); break; }
-    if (ctrl.n_done == ctrl.nsys) break;
-    if (ctrl.iter >= prm->maxiter) {
-      // final FP64 check of where the iteration stands
-      reliable++;
-      if ((st = S.reliable_update(s))) { status = st; break; }
-      e = cudaMemcpyAsync(&ctrl, S.w.ctrl, sizeof(Control), cudaMemcpyDeviceToHost, s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-      if (e != cudaSuccess) { status = cuda_fail(e, "cg: control readback"); break; }
-      if (ctrl.n_done != ctrl.nsys) status = fail(LQCD_ERR_NOT_CONVERGED, "cg: maxiter %d reached", prm->maxiter);
-      break;
-    }
-    if (ctrl.active == 0) {
-      // paused: convergence candidate or reliable update due
-      reliable++;
-      if ((st = S.reliable_update(s))) { status = st; break; }
-      continue;
-    }
-    if (prm->timeout_ms > 0) {
-      double el = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-      if (el > prm->timeout_ms) { status = fail(LQCD_ERR_TIMEOUT, "cg: timeout after %.1f ms", el); break; }
-    }
-    if (exec) {
-      e = cudaGraphLaunch(exec, s);
-      if (e != cudaSuccess) { status = cuda_fail(e, "cg: graph launch"); break; }
-      count_launches(nodes_per_chunk);
-    } else {
-      for (int i = 0; i < chunk && st == LQCD_OK; i++) st = S.inner_iteration(s);
-      if (st) { status = st; break; }
-    }
-  }
+  memset(&ctrl, 0, sizeof(ctrl));
+  const int status = run_cg(S, S.prm, key, s, t0, &ctrl);
   // report
   std::vector<SysState> sys(S.nsys);
-  e = cudaMemcpyAsync(sys.data(), S.w.sys, sizeof(SysState) * S.nsys, cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaMemcpyAsync(sys.data(), S.w.sys, sizeof(SysState) * S.nsys, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess && status == LQCD_OK) status = cuda_fail(e, "cg: state readback");
+  int out_status = status;
+  if (e != cudaSuccess && out_status == LQCD_OK) out_status = cuda_fail(e, "cg: state readback");
   double worst = 0.0;
   for (int i = 0; i < S.nsys; i++) {
     double rel = sys[i].rr0 > 0 ? std::sqrt(sys[i].rr_true / sys[i].rr0) : 0.0;
     if (rel > worst || std::isnan(rel)) worst = rel;
   }
   inf->iterations = ctrl.iter;
-  inf->reliable_updates = reliable;
+  inf->reliable_updates = ctrl.n_reliable;
   inf->true_rel_residual = worst;
-  return finish(status);
+  return finish(out_status);
 }
 
 }  // extern "C"

@@ -120,6 +120,32 @@ template <typename T> __device__ __forceinline__ T bc_phase(const Geom& g, int m
 template <> __device__ __forceinline__ double bc_phase<double>(const Geom& g, int mu) { return g.bcd[mu]; }
 template <> __device__ __forceinline__ float bc_phase<float>(const Geom& g, int mu) { return g.bcf[mu]; }
 
+// Load the neighbour spinor and spin-project it with (1 + S gamma_mu); the
+// boundary phase of a wrapping hop and, for FP16 storage, the site norm are
+// applied to the 12 reals of the half spinor instead of the 24 of the spinor.
+template <int P, int MU, int S>
+__device__ __forceinline__ void load_project(const void* in, const Geom& g, int64_t idx, bool wrap,
+                                             Half<typename PrecTraits<P>::real>& h) {
+  using T = typename PrecTraits<P>::real;
+  Spinor<T> s;
+  if constexpr (P == LQCD_F16) {
+    float nrm;
+    SpinorIO<P>::load_unscaled(in, g.sstride, idx, s, nrm);
+    project<MU, S>(s, h);
+    const T f = wrap ? bc_phase<T>(g, MU) * nrm : nrm;
+#pragma unroll
+    for (int k = 0; k < 6; k++) h.v[k] = f * h.v[k];
+  } else {
+    SpinorIO<P>::load(in, g.sstride, idx, s);
+    project<MU, S>(s, h);
+    if (wrap) {
+      const T ph = bc_phase<T>(g, MU);
+#pragma unroll
+      for (int k = 0; k < 6; k++) h.v[k] = ph * h.v[k];
+    }
+  }
+}
+
 template <int MU, int P, int R, bool DAG>
 __device__ __forceinline__ void hop_dir(Spinor<typename PrecTraits<P>::real>& acc, const Geom& g,
                                         const void* gauge, const Coord& x, int64_t cb, int64_t i5,
@@ -130,15 +156,8 @@ __device__ __forceinline__ void hop_dir(Spinor<typename PrecTraits<P>::real>& ac
   {
     bool wrap;
     const int64_t nb = neighbour_cb<MU>(g, x, +1, wrap);
-    Spinor<T> s;
-    SpinorIO<P>::load(in, g.sstride, nb * n5 + i5, s);
     Half<T> h;
-    project<MU, SF>(s, h);
-    if (wrap) {
-      const T ph = bc_phase<T>(g, MU);
-#pragma unroll
-      for (int k = 0; k < 6; k++) h.v[k] = ph * h.v[k];
-    }
+    load_project<P, MU, SF>(in, g, nb * n5 + i5, wrap, h);
     Link<T> u;
     LinkIO<P, R>::load(gauge, g.gstride, parity * 4 + MU, cb, u);
     Half<T> w;
@@ -148,15 +167,8 @@ __device__ __forceinline__ void hop_dir(Spinor<typename PrecTraits<P>::real>& ac
   {
     bool wrap;
     const int64_t nb = neighbour_cb<MU>(g, x, -1, wrap);
-    Spinor<T> s;
-    SpinorIO<P>::load(in, g.sstride, nb * n5 + i5, s);
     Half<T> h;
-    project<MU, -SF>(s, h);
-    if (wrap) {
-      const T ph = bc_phase<T>(g, MU);
-#pragma unroll
-      for (int k = 0; k < 6; k++) h.v[k] = ph * h.v[k];
-    }
+    load_project<P, MU, -SF>(in, g, nb * n5 + i5, wrap, h);
     Link<T> u;
     LinkIO<P, R>::load(gauge, g.gstride, (1 - parity) * 4 + MU, nb, u);
     Half<T> w;
@@ -190,7 +202,13 @@ __device__ __forceinline__ void hop_site(const Geom& g, const void* gauge, const
   using IO = SpinorIO<P>;
   const int64_t n5 = g.n5;
   int64_t cb, i5;
-  if (n5 == 1) { cb = j; i5 = 0; } else { cb = j / n5; i5 = j - cb * n5; }
+  if (n5 == 1) {
+    cb = j;
+    i5 = 0;
+  } else {
+    cb = fdiv((uint32_t)j, g.fn5);
+    i5 = j - cb * n5;
+  }
   const Coord x = cb_to_coord(g, cb, parity);
   Spinor<T> acc;
   zero(acc);

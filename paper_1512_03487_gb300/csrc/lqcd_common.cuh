@@ -27,14 +27,34 @@ int after_launch(const char* what);
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
 // ------------------------------------------------------------------ geometry
+// Division of n < 2^31 by a runtime constant d >= 1 with one multiply-high,
+// an add and a shift (Granlund and Montgomery, "Division by invariant
+// integers using multiplication", PLDI 1994, the round-up multiplier for
+// unsigned N-bit operands): s = ceil(log2 d), m = floor(2^32 (2^s - d) / d) + 1,
+// q = (mulhi(n, m) + n) >> s. n < 2^31 keeps the sum within 32 bits.
+struct FastDiv {
+  uint32_t d, m, s;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  f.s = 0;
+  while ((1ull << f.s) < d) f.s++;
+  f.m = (uint32_t)(((1ull << 32) * ((1ull << f.s) - d)) / d + 1);
+  return f;
+}
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) { return (__umulhi(n, f.m) + n) >> f.s; }
+
 struct Geom {
   int X, Y, Z, T;
   int Xh;           // X / 2
   int Vh;           // half 4D volume
   int n5;           // inner extent (L_s or number of RHS)
-  int64_t nsites;   // Vh * n5: sites of one checkerboard field
+  int64_t nsites;   // Vh * n5: sites of one checkerboard field (< 2^31)
   int64_t sstride;  // chunk stride of a spinor checkerboard field (sites)
   int64_t gstride;  // chunk stride of a gauge (parity, mu) block (cb sites)
+  FastDiv fXh, fY, fZ, fn5;
+  int st[4];        // lexicographic strides 1, X, X Y, X Y Z (4D volume < 2^31)
   float bcf[4];
   double bcd[4];
 };
@@ -165,6 +185,23 @@ template <> struct SpinorIO<LQCD_F16> {
       }
     }
   }
+  // Components without the site norm (returned separately), so that a caller
+  // can apply the norm after a linear map that shrinks the data (spin projection).
+  static __device__ __forceinline__ void load_unscaled(const void* base, int64_t stride, int64_t j, Spinor<T>& s,
+                                                       float& nrm) {
+    const uint4* b = reinterpret_cast<const uint4*>(base);
+    nrm = __ldg(norm_ptr(base, stride) + j);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      uint4 w = __ldg(b + c * stride + j);
+      unsigned int words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        float2 f = __half22float2(*reinterpret_cast<__half2*>(&words[q]));
+        s.v[4 * c + q] = mk(f.x, f.y);
+      }
+    }
+  }
   static __device__ __forceinline__ void store(void* base, int64_t stride, int64_t j, const Spinor<T>& s) {
     float m = 0.f;
 #pragma unroll
@@ -270,22 +307,25 @@ template <> struct LinkIO<LQCD_F16, 12> {
 };
 
 // ------------------------------------------------------------------ site coordinates
+// 32-bit index arithmetic throughout: the 4D volume is below 2^31 (checked
+// when the geometry is made), so lexicographic and checkerboard indices fit.
 struct Coord {
-  int c[4];     // x, y, z, t
-  int64_t lex;  // x + X (y + Y (z + Z t))
+  int c[4];      // x, y, z, t
+  uint32_t lex;  // x + X (y + Y (z + Z t))
 };
 
-__device__ __forceinline__ Coord cb_to_coord(const Geom& g, int64_t cb, int parity) {
+__device__ __forceinline__ Coord cb_to_coord(const Geom& g, int64_t cb64, int parity) {
   Coord r;
-  int64_t q = cb / g.Xh;
-  int xh = (int)(cb - q * g.Xh);
-  int64_t q2 = q / g.Y;
-  r.c[1] = (int)(q - q2 * g.Y);
-  int64_t q3 = q2 / g.Z;
-  r.c[2] = (int)(q2 - q3 * g.Z);
+  const uint32_t cb = (uint32_t)cb64;
+  const uint32_t q = fdiv(cb, g.fXh);
+  const uint32_t xh = cb - q * (uint32_t)g.Xh;
+  const uint32_t q2 = fdiv(q, g.fY);
+  r.c[1] = (int)(q - q2 * (uint32_t)g.Y);
+  const uint32_t q3 = fdiv(q2, g.fZ);
+  r.c[2] = (int)(q2 - q3 * (uint32_t)g.Z);
   r.c[3] = (int)q3;
-  r.c[0] = 2 * xh + ((parity + r.c[1] + r.c[2] + r.c[3]) & 1);
-  r.lex = r.c[0] + (int64_t)g.X * (r.c[1] + (int64_t)g.Y * (r.c[2] + (int64_t)g.Z * r.c[3]));
+  r.c[0] = (int)(2 * xh) + ((parity + r.c[1] + r.c[2] + r.c[3]) & 1);
+  r.lex = (uint32_t)r.c[0] + 2 * q * (uint32_t)g.Xh;  // x + X (y + Y (z + Z t))
   return r;
 }
 
@@ -293,16 +333,16 @@ __device__ __forceinline__ Coord cb_to_coord(const Geom& g, int64_t cb, int pari
 template <int MU>
 __device__ __forceinline__ int64_t neighbour_cb(const Geom& g, const Coord& x, int sign, bool& wrap) {
   const int L = MU == 0 ? g.X : MU == 1 ? g.Y : MU == 2 ? g.Z : g.T;
-  const int64_t st = MU == 0 ? 1 : MU == 1 ? (int64_t)g.X : MU == 2 ? (int64_t)g.X * g.Y : (int64_t)g.X * g.Y * g.Z;
-  int64_t lex;
+  const uint32_t st = (uint32_t)g.st[MU];
+  uint32_t lex;
   if (sign > 0) {
     wrap = x.c[MU] == L - 1;
-    lex = wrap ? x.lex - (int64_t)(L - 1) * st : x.lex + st;
+    lex = wrap ? x.lex - (uint32_t)(L - 1) * st : x.lex + st;
   } else {
     wrap = x.c[MU] == 0;
-    lex = wrap ? x.lex + (int64_t)(L - 1) * st : x.lex - st;
+    lex = wrap ? x.lex + (uint32_t)(L - 1) * st : x.lex - st;
   }
-  return lex >> 1;
+  return (int64_t)(lex >> 1);
 }
 
 // ------------------------------------------------------------------ CG control
@@ -324,12 +364,14 @@ struct SysState {
 enum { REASON_CONVERGED = 1, REASON_RELIABLE = 2, REASON_NAN = 4 };
 
 struct Control {
-  int active;   // 1 while inner iterations run; kernels of a chunk return early when 0
-  int reason;   // REASON_* bits explaining a pause
-  int iter;     // inner iterations completed
+  int active;      // 1 while inner iterations run; gated kernels return at once when 0
+  int reason;      // REASON_* bits explaining a pause / a pending reliable update
+  int iter;        // inner iterations completed
   int nsys;
   int n_done;
-  int pad[3];
+  int n_reliable;  // FP64 residual recomputations done
+  int chunk_left;  // device-driven loop: iterations left in the current graph launch
+  int pad;
 };
 
 // What the last block of a reducing kernel does with the per-system totals.
@@ -351,7 +393,9 @@ struct ReduceCtx {
   int fin;
   double tol2_rel;        // FIN_INIT: tol^2
   double delta2;          // FIN_INIT: delta^2
-  int maxiter;            // FIN_UPDATE: pause once this many iterations ran
+  int maxiter;            // FIN_UPDATE: request a final FP64 residual once this many iterations ran
+  int cond;               // FIN_UPDATE: 1 = set h_rel (device-driven graph), 0 = pause for the host
+  cudaGraphConditionalHandle h_rel;  // IF node running the reliable update (when cond)
 };
 
 __device__ __forceinline__ bool gate_closed(const Control* ctrl) {
@@ -388,9 +432,17 @@ __device__ inline void finalize_totals(const ReduceCtx& rc, const double* totals
         else if (totals[s] <= st.tol2) reason |= REASON_CONVERGED;
         else if (totals[s] <= st.delta2 * st.maxrr) reason |= REASON_RELIABLE;
       }
-      if (reason) {
-        rc.ctrl->reason |= reason;
+      rc.ctrl->iter += 1;
+      const bool at_cap = rc.maxiter > 0 && rc.ctrl->iter >= rc.maxiter;
+      if (reason & REASON_NAN) {
+        rc.ctrl->reason |= REASON_NAN;
         rc.ctrl->active = 0;
+      } else if (reason || at_cap) {
+        // An FP64 residual recomputation is due (or the iteration cap is
+        // reached and the true residual must be known): beta waits for it.
+        rc.ctrl->reason |= reason;
+        if (rc.cond) cudaGraphSetConditional(rc.h_rel, 1);  // run the reliable-update branch now
+        else rc.ctrl->active = 0;                           // pause for the host
       } else {
         for (int s = 0; s < nsys; s++) {
           SysState& st = rc.sys[s];
@@ -400,8 +452,6 @@ __device__ inline void finalize_totals(const ReduceCtx& rc, const double* totals
           st.maxrr = fmax(st.maxrr, totals[s]);
         }
       }
-      rc.ctrl->iter += 1;
-      if (rc.maxiter > 0 && rc.ctrl->iter >= rc.maxiter) rc.ctrl->active = 0;
     } break;
     case FIN_INIT: {
       int n_done = 0;
@@ -420,6 +470,8 @@ __device__ inline void finalize_totals(const ReduceCtx& rc, const double* totals
       rc.ctrl->nsys = nsys;
       rc.ctrl->n_done = n_done;
       rc.ctrl->iter = 0;
+      rc.ctrl->n_reliable = 0;
+      rc.ctrl->chunk_left = 0;
       rc.ctrl->reason = bad ? REASON_NAN : 0;
       rc.ctrl->active = (!bad && n_done < nsys) ? 1 : 0;
     } break;
@@ -442,6 +494,7 @@ __device__ inline void finalize_totals(const ReduceCtx& rc, const double* totals
         n_done += st.done;
       }
       rc.ctrl->n_done = n_done;
+      rc.ctrl->n_reliable += 1;
       rc.ctrl->reason = bad ? REASON_NAN : 0;
       rc.ctrl->active = (!bad && n_done < nsys) ? 1 : 0;
     } break;
