@@ -51,8 +51,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the domain-wall, multi-RHS, batch and force measurements")
-    ap.add_argument("--mode", choices=["full", "step", "hop"], default="full",
-                    help="step: only the timed solves; hop: only the dominant kernel's roofline loop")
+    ap.add_argument("--mode", choices=["full", "step", "hop", "hops"], default="full",
+                    help="step: only the timed solves; hop: only the dominant kernel's roofline loop; "
+                         "hops: the three hop shapes (profiling)")
     return ap.parse_args()
 
 
@@ -168,6 +169,21 @@ def run_lqcd(args, world, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    if args.mode == "hops":
+        # profiling mode: the three hop shapes of the hot path on zero-filled fields
+        # (the kernels do the same work whatever the values), args.steps launches each
+        flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+        res = {
+            "f16r12_24x24x24x48": _hop_gbs(L, F, L.lattice((24, 24, 24, 48), bc=BC), 2, 12, 296, flush, stream,
+                                           n=args.steps),
+            "dwf_f32r12_16x4_ls16": _hop_gbs(L, F, L.lattice((16, 16, 16, 16), n5=16, bc=BC), 1, 12,
+                                             8 * 48 / 16 + 192, flush, stream, kind=L.LQCD_DWF, n=args.steps),
+            "f16r12_32x4_12rhs": _hop_gbs(L, F, L.lattice((32, 32, 32, 32), n5=12, bc=BC), 2, 12, 8 * 24 / 12 + 104,
+                                          flush, stream, n=args.steps)}
+        if rank == 0:
+            print(json.dumps({"mode": "hops", "hops": res}), flush=True)
+        return
     dims = tuple(args.dims)
     mass = args.mass
     U, b = make_inputs(dims)

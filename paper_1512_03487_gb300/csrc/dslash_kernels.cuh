@@ -88,6 +88,40 @@ __device__ __forceinline__ void accumulate(Spinor<T>& acc, const Half<T>& w) {
   }
 }
 
+// acc + f a and acc + f (i a), one fused multiply-add per real component
+template <typename T> __device__ __forceinline__ cpx<T> fmacc(cpx<T> acc, T f, cpx<T> a) {
+  return mk(fma(f, a.r, acc.r), fma(f, a.i, acc.i));
+}
+template <typename T> __device__ __forceinline__ cpx<T> fmacc_i(cpx<T> acc, T f, cpx<T> a) {
+  return mk(fma(-f, a.i, acc.r), fma(f, a.r, acc.i));
+}
+
+// acc += f (upper = w, lower = S B_mu^dag w): the factor f (boundary phase and,
+// for FP16 storage, the neighbour's site norm) rides on the accumulation FMAs.
+template <int MU, int S, typename T>
+__device__ __forceinline__ void accumulate_scaled(Spinor<T>& acc, const Half<T>& w, T f) {
+  const T fs = S > 0 ? f : -f;
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const cpx<T> w0 = w.v[c], w1 = w.v[3 + c];
+    acc.v[c] = fmacc(acc.v[c], f, w0);
+    acc.v[3 + c] = fmacc(acc.v[3 + c], f, w1);
+    if (MU == 0) {         // lower2 = S i w1, lower3 = S i w0
+      acc.v[6 + c] = fmacc_i(acc.v[6 + c], fs, w1);
+      acc.v[9 + c] = fmacc_i(acc.v[9 + c], fs, w0);
+    } else if (MU == 1) {  // lower2 = S w1, lower3 = -S w0
+      acc.v[6 + c] = fmacc(acc.v[6 + c], fs, w1);
+      acc.v[9 + c] = fmacc(acc.v[9 + c], -fs, w0);
+    } else if (MU == 2) {  // lower2 = S i w0, lower3 = -S i w1
+      acc.v[6 + c] = fmacc_i(acc.v[6 + c], fs, w0);
+      acc.v[9 + c] = fmacc_i(acc.v[9 + c], -fs, w1);
+    } else {               // lower2 = S w0, lower3 = S w1
+      acc.v[6 + c] = fmacc(acc.v[6 + c], fs, w0);
+      acc.v[9 + c] = fmacc(acc.v[9 + c], fs, w1);
+    }
+  }
+}
+
 // w_a = U h_a
 template <typename T>
 __device__ __forceinline__ void link_mul(const Link<T>& u, const Half<T>& h, Half<T>& w) {
@@ -120,30 +154,26 @@ template <typename T> __device__ __forceinline__ T bc_phase(const Geom& g, int m
 template <> __device__ __forceinline__ double bc_phase<double>(const Geom& g, int mu) { return g.bcd[mu]; }
 template <> __device__ __forceinline__ float bc_phase<float>(const Geom& g, int mu) { return g.bcf[mu]; }
 
-// Load the neighbour spinor and spin-project it with (1 + S gamma_mu); the
-// boundary phase of a wrapping hop and, for FP16 storage, the site norm are
-// applied to the 12 reals of the half spinor instead of the 24 of the spinor.
+// Load the neighbour spinor and spin-project it with (1 + S gamma_mu). The
+// linear factor the half spinor still needs -- the boundary phase of a
+// wrapping hop and, for FP16 storage, the neighbour's site norm -- is returned
+// instead of applied; accumulate_scaled folds it into its FMAs.
 template <int P, int MU, int S>
-__device__ __forceinline__ void load_project(const void* in, const Geom& g, int64_t idx, bool wrap,
-                                             Half<typename PrecTraits<P>::real>& h) {
+__device__ __forceinline__ typename PrecTraits<P>::real load_project(const void* in, const Geom& g, int64_t idx,
+                                                                     bool wrap, Half<typename PrecTraits<P>::real>& h) {
   using T = typename PrecTraits<P>::real;
   Spinor<T> s;
+  T f;
   if constexpr (P == LQCD_F16) {
     float nrm;
     SpinorIO<P>::load_unscaled(in, g.sstride, idx, s, nrm);
-    project<MU, S>(s, h);
-    const T f = wrap ? bc_phase<T>(g, MU) * nrm : nrm;
-#pragma unroll
-    for (int k = 0; k < 6; k++) h.v[k] = f * h.v[k];
+    f = nrm;
   } else {
     SpinorIO<P>::load(in, g.sstride, idx, s);
-    project<MU, S>(s, h);
-    if (wrap) {
-      const T ph = bc_phase<T>(g, MU);
-#pragma unroll
-      for (int k = 0; k < 6; k++) h.v[k] = ph * h.v[k];
-    }
+    f = T(1);
   }
+  project<MU, S>(s, h);
+  return wrap ? bc_phase<T>(g, MU) * f : f;
 }
 
 template <int MU, int P, int R, bool DAG>
@@ -157,23 +187,23 @@ __device__ __forceinline__ void hop_dir(Spinor<typename PrecTraits<P>::real>& ac
     bool wrap;
     const int64_t nb = neighbour_cb<MU>(g, x, +1, wrap);
     Half<T> h;
-    load_project<P, MU, SF>(in, g, nb * n5 + i5, wrap, h);
+    const T f = load_project<P, MU, SF>(in, g, nb * n5 + i5, wrap, h);
     Link<T> u;
     LinkIO<P, R>::load(gauge, g.gstride, parity * 4 + MU, cb, u);
     Half<T> w;
     link_mul(u, h, w);
-    accumulate<MU, SF>(acc, w);
+    accumulate_scaled<MU, SF>(acc, w, f);
   }
   {
     bool wrap;
     const int64_t nb = neighbour_cb<MU>(g, x, -1, wrap);
     Half<T> h;
-    load_project<P, MU, -SF>(in, g, nb * n5 + i5, wrap, h);
+    const T f = load_project<P, MU, -SF>(in, g, nb * n5 + i5, wrap, h);
     Link<T> u;
     LinkIO<P, R>::load(gauge, g.gstride, (1 - parity) * 4 + MU, nb, u);
     Half<T> w;
     link_mul_dag(u, h, w);
-    accumulate<MU, -SF>(acc, w);
+    accumulate_scaled<MU, -SF>(acc, w, f);
   }
 }
 
