@@ -49,6 +49,11 @@ def parse_args():
     ap.add_argument("--mass", type=float, default=0.01)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the solver's kernels directly instead of replaying its CUDA graph "
+                         "(profilers list kernels inside conditional graph bodies only this way)")
+    ap.add_argument("--check-interval", type=int, default=64,
+                    help="iterations per graph launch / host check of the solver")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the domain-wall, multi-RHS, batch and force measurements")
     ap.add_argument("--mode", choices=["full", "step", "hop", "hops"], default="full",
@@ -206,7 +211,9 @@ def run_lqcd(args, world, rank, local):
     # delta = 0.003: the reliable-update threshold that minimised the FP16 solve time in a sweep
     # over 0.1 ... 0.001 on this workload (4 FP64 residual recomputations instead of 10 at 0.1)
     prms = {p: L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=p, sloppy_recon=12 if p else 18,
-                               delta=DELTA, check_interval=64) for p in (0, 1, 2)}
+                               delta=DELTA, check_interval=args.check_interval,
+                               use_graph=0 if args.no_graph else 1)
+            for p in (0, 1, 2)}
     ws = F.empty(max(L.lqcd_cg_workspace_bytes(lat, op64, prms[p], L.LQCD_EVEN) for p in (0, 1, 2)))
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
