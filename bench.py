@@ -552,7 +552,13 @@ def run_extras(L, F, flush, stream):
                                         / (ms * 1e-3) / 1e9, 1),
         "hop_f16r12_12rhs": _hop_gbs(L, F, lat, 2, 12, 8 * 24 / nr + 52 + 52, flush, stream),
         "hop_f16r12_1rhs": _hop_gbs(L, F, L.lattice(dims, n5=1, bc=BC), 2, 12, 8 * 24 + 52 + 52, flush, stream)}
-    del g64, g16, be, x, ws
+    wsb = F.empty(L.lqcd_block_cg_workspace_bytes(lat, op, prm))
+    L.lqcd_block_cg_solve(x, be, g64, g16, lat, op, prm, wsb)
+    msb, infb = _events_time(lambda: L.lqcd_block_cg_solve(x, be, g64, g16, lat, op, prm, wsb), stream, flush)
+    out["multi_rhs_32x4_12rhs_mixed_fp16"]["block_cg"] = {
+        "ms": round(msb, 3), "iterations": infb.iterations, "reliable_updates": infb.reliable_updates,
+        "max_true_rel_residual_normal_eq": infb.true_rel_residual}
+    del g64, g16, be, x, ws, wsb
     torch.cuda.empty_cache()
 
     # uneven batch: 4 each of 8^4, 12^4, 16^4, 20^4, Haar links, m = 0.05, FP32-inner, one persistent launch per phase

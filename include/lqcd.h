@@ -220,8 +220,9 @@ int lqcd_eo_reconstruct(void* x_full_dev, const void* b_full_dev, const void* ga
  * A = M^dag M (subset LQCD_FULL) or M_hat^dag M_hat (subset LQCD_EVEN), x0 = 0.
  * x_dev, b_dev: FP64 fields (op->prec == LQCD_F64) of that subset.
  * gauge_dev: FP64 gauge in op->recon. gauge_sloppy_dev: gauge in
- * (params->sloppy_prec, params->sloppy_recon), used by the inner iteration;
- * may equal gauge_dev when sloppy_prec is LQCD_F64. With a Wilson operator
+ * (params->sloppy_prec, params->sloppy_recon), used by the inner iteration.
+ * When sloppy_prec is LQCD_F64 it is ignored (may be NULL): the inner
+ * iteration then runs on gauge_dev in op->recon, whatever sloppy_recon says. With a Wilson operator
  * and n5 > 1 every i5 is an independent system (multi-RHS, own scalars,
  * shared link loads); with a domain-wall operator n5 = L_s is one system.
  * Mixed precision: the iteration runs in the sloppy format; x accumulates
@@ -237,6 +238,20 @@ int lqcd_cg_solve(void* x_dev, const void* b_dev, const void* gauge_dev,
                   lqcd_solve_info* info, void* workspace_dev, size_t workspace_bytes,
                   void* stream);
 
+/* Block CG (O'Leary 1980) for the n5 <= 16 right-hand sides of a Wilson
+ * multi-RHS field (subset LQCD_EVEN: M_hat^dag M_hat X = B): one block Krylov
+ * space shared by all columns, N x N Gram matrices accumulated in FP64,
+ * alpha and beta from Cholesky factorisations on the device, the same
+ * sloppy-operator / FP64-reliable-update scheme as lqcd_cg_solve. Converged
+ * columns are frozen; a breakdown falls back to per-column steps. Exit when
+ * every column's FP64 true residual is <= tol. Arguments as lqcd_cg_solve
+ * (no subset argument). */
+size_t lqcd_block_cg_workspace_bytes(const lqcd_lattice* lat, const lqcd_operator* op,
+                                     const lqcd_solver_params* params);
+int lqcd_block_cg_solve(void* x_dev, const void* b_dev, const void* gauge_dev, const void* gauge_sloppy_dev,
+                        const lqcd_lattice* lat, const lqcd_operator* op, const lqcd_solver_params* params,
+                        lqcd_solve_info* info, void* workspace_dev, size_t workspace_bytes, void* stream);
+
 /* ---------------------------------------------------------------- batched solves */
 
 /* One lattice of a batched solve: independent Wilson systems of different
@@ -246,7 +261,7 @@ typedef struct {
     lqcd_lattice lat;          /* this instance's geometry; n5 must be 1 */
     double mass;               /* this instance's Wilson bare mass m */
     const void* gauge;         /* FP64 links, device layout, recon as passed to the call */
-    const void* gauge_sloppy;  /* links in (sloppy_prec, sloppy_recon); NULL if sloppy_prec is LQCD_F64 */
+    const void* gauge_sloppy;  /* links in (sloppy_prec, sloppy_recon); ignored if sloppy_prec is LQCD_F64 */
     void* x;                   /* FP64 even-checkerboard solution (written) */
     const void* b;             /* FP64 even-checkerboard source */
 } lqcd_batch_item;

@@ -85,6 +85,8 @@ SIGNATURES = {
     "lqcd_cg_solve": (_I, [_P, _P, _P, _P, _LAT, _OP, _PRM, _I, _INFO, _P, _SZ, _P]),
     "lqcd_force": (_I, [_P, _P, _P, _P, _LAT, _OP, _I, _P]),
     "lqcd_M_noalloc": (_I, [_P, _P, _P, _LAT, _OP, _I, _I, _P]),
+    "lqcd_block_cg_workspace_bytes": (_SZ, [_LAT, _OP, _PRM]),
+    "lqcd_block_cg_solve": (_I, [_P, _P, _P, _P, _LAT, _OP, _PRM, _INFO, _P, _SZ, _P]),
     "lqcd_batch_cg_workspace_bytes": (_SZ, [_I, C.c_void_p, _I, _PRM]),
     "lqcd_batch_cg_solve": (_I, [_I, C.c_void_p, _I, _PRM, C.c_void_p, _P, _SZ, _P]),
     "lqcd_tune_save": (_I, [C.c_char_p]),

@@ -188,6 +188,21 @@ def lqcd_cg_solve(x, b, gauge, gauge_sloppy, lat, op, params, subset, workspace,
     return info
 
 
+def lqcd_block_cg_workspace_bytes(lat, op, params) -> int:
+    return int(lib.lqcd_block_cg_workspace_bytes(C.byref(lat), C.byref(op), C.byref(params)))
+
+
+def lqcd_block_cg_solve(x, b, gauge, gauge_sloppy, lat, op, params, workspace, stream=None,
+                        raise_on_error=True) -> lqcd_solve_info:
+    info = lqcd_solve_info()
+    nbytes = workspace.numel() * workspace.element_size()
+    st = lib.lqcd_block_cg_solve(_ptr(x), _ptr(b), _ptr(gauge), _ptr(gauge_sloppy), C.byref(lat), C.byref(op),
+                                 C.byref(params), C.byref(info), _ptr(workspace), nbytes, _stream(stream))
+    if raise_on_error:
+        _check(st)
+    return info
+
+
 def batch_items(entries):
     """Array of lqcd_batch_item from dicts with keys lat, mass, gauge,
     gauge_sloppy (may be None), x, b (tensors or device pointers)."""

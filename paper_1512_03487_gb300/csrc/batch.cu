@@ -448,7 +448,7 @@ int lqcd_batch_cg_solve(int n, const lqcd_batch_item* items, int recon, const lq
     memset(&I, 0, sizeof(I));
     I.g = g;
     I.gauge64 = items[i].gauge;
-    I.gauge_s = items[i].gauge_sloppy ? items[i].gauge_sloppy : items[i].gauge;
+    I.gauge_s = (prm->sloppy_prec == LQCD_F64 || !items[i].gauge_sloppy) ? items[i].gauge : items[i].gauge_sloppy;
     I.c = 4.0 + items[i].mass;
     I.tile0 = tiles;
     tiles += (g.nsites + TILE - 1) / TILE;
@@ -481,7 +481,8 @@ int lqcd_batch_cg_solve(int n, const lqcd_batch_item* items, int recon, const lq
   S.ctrl = lay.ctrl;
   S.sys = lay.sys;
   S.sloppy = prm->sloppy_prec;
-  S.sloppy_recon = prm->sloppy_recon;
+  // the FP64 inner operator runs on the FP64 fields themselves, in their format
+  S.sloppy_recon = prm->sloppy_prec == LQCD_F64 ? recon : prm->sloppy_recon;
   S.recon = recon;
   S.total_tiles = tiles;
   memset(&S.base, 0, sizeof(S.base));

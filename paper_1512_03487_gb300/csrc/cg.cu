@@ -307,10 +307,8 @@ int lqcd_cg_solve(void* x, const void* b, const void* gauge, const void* gauge_s
   if (!x || !b || !gauge || !workspace || ((uintptr_t)workspace & 255) || ((uintptr_t)x & 15) ||
       ((uintptr_t)b & 15))
     return finish(fail(LQCD_ERR_ARG, "cg: null or misaligned pointer (workspace needs 256-byte alignment)"));
-  if (!gauge_sloppy) {
-    if (prm->sloppy_prec != LQCD_F64) return finish(fail(LQCD_ERR_ARG, "cg: gauge_sloppy required"));
-    gauge_sloppy = gauge;
-  }
+  if (prm->sloppy_prec == LQCD_F64) gauge_sloppy = gauge;  // the FP64 field serves both
+  if (!gauge_sloppy) return finish(fail(LQCD_ERR_ARG, "cg: gauge_sloppy required"));
   S.prm = *prm;
   if (S.prm.check_interval <= 0) S.prm.check_interval = 16;
   S.subset = subset;
@@ -323,7 +321,8 @@ int lqcd_cg_solve(void* x, const void* b, const void* gauge, const void* gauge_s
   S.op64 = *op;
   S.ops = *op;
   S.ops.prec = prm->sloppy_prec;
-  S.ops.recon = prm->sloppy_recon;
+  // the FP64 inner operator runs on the FP64 field itself, in that field's format
+  S.ops.recon = prm->sloppy_prec == LQCD_F64 ? op->recon : prm->sloppy_recon;
   S.gauge64 = gauge;
   S.gauge_s = gauge_sloppy;
   cudaStream_t s = (cudaStream_t)stream;
