@@ -1,15 +1,15 @@
 #!/usr/bin/env python
 """Benchmark: even-odd preconditioned Wilson CG to a 1e-10 FP64 true residual
-on a 24^3 x 48 lattice (links exp(0.3 i H), m = 0.01), FP16-storage inner
-Dslash with FP64 reliable updates, on one GB300.
+on a 24^3 x 48 lattice (links exp(0.3 i H), m = 0.01), FP32 inner Dslash
+(12-real links) with FP64 reliable updates, on one GB300.
 
 One step = one full solve of D_W x = b from resident FP64 inputs: link
 preparation (FP64 and FP16 / 12-real device layouts), source preparation
 b_hat = b_e + H_eo b_o / 2c, CG on M_hat^dag M_hat with source M_hat^dag b_hat,
 reconstruction of x_o. The headline value is the Dslash throughput sustained
 inside the step: (hops in the step) x 1320 flop x Vh / step time. The JSON
-line also carries the FP64 and FP32-inner solve times (the mixed vs FP64
-comparison), the roofline of the dominant kernel (the FP16 hop), the oracle
+line also carries the FP64 and FP16-inner solve times (the mixed vs FP64
+comparison), the roofline of the dominant kernel (the FP32 hop), the oracle
 CPU baseline and the end-to-end number through host buffers.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lqcd|reference]
@@ -34,9 +34,16 @@ METRIC = "Dslash GFLOP/s & HBM-roofline %; mixed vs FP64 CG time to 1e-10 residu
 FLOP_PER_SITE = 1320
 BC = (1.0, 1.0, 1.0, -1.0)
 WORKLOAD = "wilson_eo_cg_24x24x24x48_m0.01_exp0.3_tol1e-10"
-DELTA = 0.003
-PROFILE_JSON = os.path.join(ROOT, "profiles", "hop_f16r12_24x24x24x48.json")
-DSLASH_SOURCES = ["dslash_kernels.cuh", "lqcd_common.cuh", "dslash_launch.cuh", "dslash_f16.cu"]
+# Inner (sloppy) precision of the headline solve and the reliable-update threshold per inner
+# precision. A reliable update recomputes r = b - A x with the FP64 operator, which on GB300 is
+# bound by the FP64 pipe and costs as much as ~10 FP32 iterations, so the largest drop per
+# update that the inner precision sustains wins: sweeps on this workload gave delta = 1e-5 for
+# FP32 storage (2 updates, 61 iterations) and 0.003 for FP16 storage (4 updates, 63
+# iterations; smaller deltas add iterations), and FP32 inner is the faster of the two.
+HEADLINE = 1
+DELTA = {0: 0.1, 1: 1e-5, 2: 0.003}
+PROFILE_JSON = os.path.join(ROOT, "profiles", "hop_f32r12_24x24x24x48.json")
+DSLASH_SOURCES = ["dslash_kernels.cuh", "lqcd_common.cuh", "cg_site.cuh", "dslash_launch.cuh", "dslash_f32.cu"]
 
 
 def parse_args():
@@ -136,6 +143,26 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------------ L2 flush
+
+class L2Flush:
+    """Leaves L2 cold and clean before a timed region: writes a 512 MB buffer (4x the
+    129 MB L2), then reads a separate 256 MB buffer, so that the dirty lines of the
+    write are written back inside the flush and not during the timed kernel (a
+    write-only flush leaves up to an L2 of dirty lines whose write-back lands on
+    whatever runs next)."""
+
+    def __init__(self, device):
+        import torch
+        self.w = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=device)
+        self.r = torch.ones(64 * 1024 * 1024, dtype=torch.float32, device=device)
+
+    def __call__(self):
+        import torch
+        self.w.zero_()
+        torch.sum(self.r)
+
+
 # ------------------------------------------------------------------ oracle timing
 
 def oracle_gflops(U, b, mass, napply=1):
@@ -178,13 +205,15 @@ def run_lqcd(args, world, rank, local):
     if args.mode == "hops":
         # profiling mode: the three hop shapes of the hot path on zero-filled fields
         # (the kernels do the same work whatever the values), args.steps launches each
-        flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+        flush = L2Flush(dev)
         res = {
+            "f32r12_24x24x24x48": _hop_gbs(L, F, L.lattice((24, 24, 24, 48), bc=BC), 1, 12, 576, flush, stream,
+                                           n=args.steps),
             "f16r12_24x24x24x48": _hop_gbs(L, F, L.lattice((24, 24, 24, 48), bc=BC), 2, 12, 296, flush, stream,
                                            n=args.steps),
             "dwf_f32r12_16x4_ls16": _hop_gbs(L, F, L.lattice((16, 16, 16, 16), n5=16, bc=BC), 1, 12,
                                              8 * 48 / 16 + 192, flush, stream, kind=L.LQCD_DWF, n=args.steps),
-            "f16r12_32x4_12rhs": _hop_gbs(L, F, L.lattice((32, 32, 32, 32), n5=12, bc=BC), 2, 12, 8 * 24 / 12 + 104,
+            "f32r12_32x4_12rhs": _hop_gbs(L, F, L.lattice((32, 32, 32, 32), n5=12, bc=BC), 1, 12, 8 * 48 / 12 + 192,
                                           flush, stream, n=args.steps)}
         if rank == 0:
             print(json.dumps({"mode": "hops", "hops": res}), flush=True)
@@ -208,14 +237,12 @@ def run_lqcd(args, world, rank, local):
     src = F.empty(L.lqcd_spinor_bytes(lat, L.LQCD_F64, L.LQCD_EVEN))
     x = F.empty(L.lqcd_spinor_bytes(lat, L.LQCD_F64, L.LQCD_FULL))
     tmp = F.empty(L.lqcd_operator_workspace_bytes(lat, op64, L.LQCD_EVEN))
-    # delta = 0.003: the reliable-update threshold that minimised the FP16 solve time in a sweep
-    # over 0.1 ... 0.001 on this workload (4 FP64 residual recomputations instead of 10 at 0.1)
     prms = {p: L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=p, sloppy_recon=12 if p else 18,
-                               delta=DELTA, check_interval=args.check_interval,
+                               delta=DELTA[p], check_interval=args.check_interval,
                                use_graph=0 if args.no_graph else 1)
             for p in (0, 1, 2)}
     ws = F.empty(max(L.lqcd_cg_workspace_bytes(lat, op64, prms[p], L.LQCD_EVEN) for p in (0, 1, 2)))
-    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    flush = L2Flush(dev)
 
     def step(sloppy):
         """One solve of D_W x = b from the resident FP64 inputs; returns hops executed."""
@@ -232,7 +259,7 @@ def run_lqcd(args, world, rank, local):
         return 1 + 2 + 4 * (info.iterations + info.reliable_updates) + 1, info
 
     def timed(fn, *a):
-        flush.zero_()
+        flush()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -244,15 +271,15 @@ def run_lqcd(args, world, rank, local):
 
     if args.mode == "hop":
         # profiling mode: only the dominant kernel's roofline loop
-        L.lqcd_gauge_pack(gs[2], L.LQCD_F16, 12, U_dev, lat)
-        roof = hop_roofline(L, F, lat, gs[2], flush, stream, vh, launches=args.steps)
+        L.lqcd_gauge_pack(gs[HEADLINE], HEADLINE, 12, U_dev, lat)
+        roof = hop_roofline(L, F, lat, gs[HEADLINE], flush, stream, vh, launches=args.steps)
         if rank == 0:
             print(json.dumps({"mode": "hop", "roofline": roof}), flush=True)
         return
 
-    # ---- headline: FP16-inner mixed precision solve
+    # ---- headline: FP32-inner mixed precision solve
     for _ in range(args.warmup):
-        step(2)
+        step(HEADLINE)
     barrier(world)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
@@ -260,7 +287,7 @@ def run_lqcd(args, world, rank, local):
     launches0 = L.lqcd_launch_count()
     total_ms, total_hops, infos = 0.0, 0, []
     for _ in range(args.steps):
-        ms, (hops, info) = timed(step, 2)
+        ms, (hops, info) = timed(step, HEADLINE)
         total_ms += ms
         total_hops += hops
         infos.append(info)
@@ -284,24 +311,26 @@ def run_lqcd(args, world, rank, local):
     # ---- mixed vs FP64 comparison (one timed solve each after one warm-up)
     cgcmp = {}
     for name, p in (("fp64", 0), ("mixed_fp32", 1), ("mixed_fp16", 2)):
-        if p != 2:
+        if p != HEADLINE:
             step(p)
         ms, (hops, info) = timed(step, p)
         cgcmp[name] = {"ms": round(ms, 3), "iterations": info.iterations,
-                       "reliable_updates": info.reliable_updates,
+                       "reliable_updates": info.reliable_updates, "delta": DELTA[p],
                        "true_rel_residual_normal_eq": info.true_rel_residual,
                        "dslash_gflops": round(hops * FLOP_PER_SITE * vh / (ms * 1e-3) / 1e9, 1)}
     cgcmp["speedup_fp16_vs_fp64"] = round(cgcmp["fp64"]["ms"] / cgcmp["mixed_fp16"]["ms"], 2)
     cgcmp["speedup_fp32_vs_fp64"] = round(cgcmp["fp64"]["ms"] / cgcmp["mixed_fp32"]["ms"], 2)
 
-    # ---- roofline of the dominant kernel: FP16 hop, 12-real links, one checkerboard
-    roof = hop_roofline(L, F, lat, gs[2], flush, stream, vh)
+    # ---- roofline of the dominant kernel: the inner hop (FP32, 12-real links), one checkerboard;
+    # and of the FP64 hop of the reliable updates, bound by the FP64 pipe
+    roof = hop_roofline(L, F, lat, gs[HEADLINE], flush, stream, vh)
+    roof64 = fp64_hop_roofline(L, F, lat, g64, flush, stream, vh)
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(L, F, lat, op64, U, b, prms[2], ws, tmp, x, gs[2], g64, bfull, bhat, src, flush,
-                      stream, vh, args, world)
+        e2e = run_e2e(L, F, lat, op64, U, b, prms[HEADLINE], ws, tmp, x, gs[HEADLINE], g64, bfull, bhat, src,
+                      flush, stream, vh, args, world)
 
     # ---- the other hot-path workloads (domain wall, multi-RHS, uneven batch, force)
     extras = None
@@ -314,16 +343,17 @@ def run_lqcd(args, world, rank, local):
         "metric": METRIC, "value": round(value, 1), "unit": "GFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 arithmetic on f16 storage, f64 reliable updates",
+        "dtype": "f32 inner iteration (f32 storage, 12-real links), f64 reliable updates",
         "data": "synthetic (seeded exp(0.3 i H) links, Gaussian source)",
         "config": {"workload": WORKLOAD, "lattice": list(dims), "mass": mass, "bc": list(BC),
-                   "solver": f"even-odd CG on M_hat^dag M_hat, FP16+norm / 12-real inner, delta {DELTA}",
-                   "tol": 1e-10, "l2": "flushed (512 MB write) before every timed step",
+                   "solver": f"even-odd CG on M_hat^dag M_hat, FP32 / 12-real inner, delta {DELTA[HEADLINE]}",
+                   "tol": 1e-10, "l2": "flushed before every timed step (512 MB write, then 256 MB read)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "full_system_rel_residual": res,
         "iterations_per_step": infos[-1].iterations, "reliable_updates_per_step": infos[-1].reliable_updates,
         "cg": cgcmp,
         "roofline": roof,
+        "roofline_fp64_hop": roof64,
         "gpu_launches": int(launches),
         "clocks": clk,
     }
@@ -352,28 +382,34 @@ def full_residual(L, F, lat, op64, g64, x, b_dev, tmp):
     return float(torch.linalg.vector_norm(a - b_dev) / torch.linalg.vector_norm(b_dev))
 
 
-def hop_roofline(L, F, lat, g16, flush, stream, vh, launches=20):
+def _cold_hop_seconds(L, F, lat, g, prec, recon, flush, stream, launches):
+    """Mean event-timed duration of one checkerboard hop launch, L2 flushed before each."""
     import torch
-    op = L.operator(prec=L.LQCD_F16, recon=12)
+    op = L.operator(prec=prec, recon=recon)
     rng = np.random.default_rng(5)
     shape = F.host_spinor_shape(lat, L.LQCD_ODD)
     host = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
-    fin = F.spinor_to_device(host, lat, L.LQCD_F16, L.LQCD_ODD)
-    out = F.empty(L.lqcd_spinor_bytes(lat, L.LQCD_F16, L.LQCD_EVEN))
+    fin = F.spinor_to_device(host, lat, prec, L.LQCD_ODD)
+    out = F.empty(L.lqcd_spinor_bytes(lat, prec, L.LQCD_EVEN))
     for _ in range(3):
-        L.lqcd_dslash(out, fin, g16, lat, op, L.LQCD_EVEN, 0)
+        L.lqcd_dslash(out, fin, g, lat, op, L.LQCD_EVEN, 0)
     times = []
     for _ in range(launches):
-        flush.zero_()
+        flush()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        L.lqcd_dslash(out, fin, g16, lat, op, L.LQCD_EVEN, 0)
+        L.lqcd_dslash(out, fin, g, lat, op, L.LQCD_EVEN, 0)
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
-    t = float(np.mean(times)) * 1e-3
-    bytes_per_site = 8 * 24 + 52 + 52  # 8 links (12 halves) + input and output FP16 spinor with norm
+    return float(np.mean(times)) * 1e-3
+
+
+def hop_roofline(L, F, lat, gsl, flush, stream, vh, launches=20):
+    t = _cold_hop_seconds(L, F, lat, gsl, HEADLINE, 12, flush, stream, launches)
+    # 8 links of 12 reals + input and output spinor, in the inner precision
+    bytes_per_site = {1: 8 * 48 + 96 + 96, 2: 8 * 24 + 52 + 52}[HEADLINE]
     achieved = bytes_per_site * vh / t / 1e9
     peak, peak_src = measured_peak()
     traffic = None
@@ -384,10 +420,22 @@ def hop_roofline(L, F, lat, g16, flush, stream, vh, launches=20):
             traffic = prof.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
-    return {"bound": "hbm", "kernel": "hop_kernel<F16, recon 12> (one checkerboard, cold L2)",
+    name = {1: "F32", 2: "F16"}[HEADLINE]
+    return {"bound": "hbm", "kernel": f"hop_kernel<{name}, recon 12> (one checkerboard, cold L2)",
             "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
             "peak_source": peak_src, "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_site * vh,
             "launch_us": round(t * 1e6, 2), "gflops": round(FLOP_PER_SITE * vh / t / 1e9, 1)}
+
+
+def fp64_hop_roofline(L, F, lat, g64, flush, stream, vh, launches=5):
+    """The FP64 hop of the reliable updates against the FP64 pipe: 1320 flop per site over the
+    nominal 1.25 TFLOP/s FP64 rate of GB300 (no measured FP64 peak is available)."""
+    t = _cold_hop_seconds(L, F, lat, g64, L.LQCD_F64, 18, flush, stream, launches)
+    tf = FLOP_PER_SITE * vh / t / 1e12
+    return {"bound": "alu", "kernel": "hop_kernel<F64, recon 18> (one checkerboard, cold L2)",
+            "achieved": round(tf, 4), "peak": 1.25, "unit": "TFLOP/s", "frac": round(tf / 1.25, 4),
+            "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)", "launch_us": round(t * 1e6, 2),
+            "hbm_gbs": round((8 * 144 + 192 + 192) * vh / t / 1e9, 1)}
 
 
 def measured_peak():
@@ -398,7 +446,7 @@ def measured_peak():
         return 6800.0, "fallback 6.8 TB/s (of fallback)"
 
 
-def run_e2e(L, F, lat, op64, U, b, prm, ws, tmp, x, g16, g64, bfull, bhat, src, flush, stream, vh, args, world):
+def run_e2e(L, F, lat, op64, U, b, prm, ws, tmp, x, gsl, g64, bfull, bhat, src, flush, stream, vh, args, world):
     """Same solve through the C ABI from pinned host buffers: H2D of the FP64
     gauge field and source, pack, solve, reconstruct, D2H of the solution."""
     import torch
@@ -409,11 +457,11 @@ def run_e2e(L, F, lat, op64, U, b, prm, ws, tmp, x, g16, g64, bfull, bhat, src, 
 
     def e2e_step():
         L.lqcd_gauge_upload(g64, L.LQCD_F64, 18, U_h, staging, lat)
-        L.lqcd_gauge_pack(g16, L.LQCD_F16, 12, staging, lat)
+        L.lqcd_gauge_pack(gsl, HEADLINE, 12, staging, lat)
         L.lqcd_spinor_upload(bfull, L.LQCD_F64, L.LQCD_FULL, b_h, staging, lat)
         L.lqcd_eo_prepare(bhat, bfull, g64, lat, op64, tmp)
         L.lqcd_M(src, bhat, g64, lat, op64, L.LQCD_EVEN, 1, tmp)
-        info = L.lqcd_cg_solve(x, src, g64, g16, lat, op64, prm, L.LQCD_EVEN, ws)
+        info = L.lqcd_cg_solve(x, src, g64, gsl, lat, op64, prm, L.LQCD_EVEN, ws)
         L.lqcd_eo_reconstruct(x, bfull, g64, lat, op64, tmp)
         L.lqcd_spinor_download(x_h, x, L.LQCD_F64, L.LQCD_FULL, staging, lat)
         return 1 + 2 + 4 * (info.iterations + info.reliable_updates) + 1
@@ -422,7 +470,7 @@ def run_e2e(L, F, lat, op64, U, b, prm, ws, tmp, x, g16, g64, bfull, bhat, src, 
         e2e_step()
     total, hops = 0.0, 0
     for _ in range(args.steps):
-        flush.zero_()
+        flush()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         hops += e2e_step()
@@ -443,7 +491,7 @@ def _events_time(fn, stream, flush=None, reps=1):
     out = None
     for _ in range(reps):
         if flush is not None:
-            flush.zero_()
+            flush()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -499,7 +547,8 @@ def run_extras(L, F, flush, stream):
     bhat = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
     src = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
     x = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
-    prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=12, delta=DELTA, check_interval=64)
+    prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=12, delta=DELTA[1],
+                          check_interval=64)
     ws = F.empty(L.lqcd_cg_workspace_bytes(lat, op, prm, 0))
 
     def dwf_solve():
@@ -528,37 +577,43 @@ def run_extras(L, F, flush, stream):
     del g64, g32, bd, tmp, bhat, src, x, ws, dx, a, bb
     torch.cuda.empty_cache()
 
-    # 32^4 with 12 right-hand sides sharing the links, m = 0.01, FP16-inner mixed CG per RHS to 1e-10
+    # 32^4 with 12 right-hand sides sharing the links, m = 0.01, mixed CG per RHS to 1e-10:
+    # FP32 inner (delta 1e-5, the faster), FP16 inner (delta 0.003), and block CG with FP32 inner
     dims, nr = (32, 32, 32, 32), 12
     U = gauge_field(dims, "haar", config_seed(3, 0))
     lat = L.lattice(dims, n5=nr, bc=BC)
     op = L.operator(mass=0.01)
     g64 = F.gauge_to_device(U, lat, 0, 18)
-    g16 = F.gauge_to_device(U, lat, 2, 12)
+    gsl = {1: F.gauge_to_device(U, lat, 1, 12), 2: F.gauge_to_device(U, lat, 2, 12)}
     del U
     rhs = gaussian_spinor(dims, config_seed(3, 1), lead=(nr,))
     be = F.spinor_to_device(F.checkerboard(rhs, 0), lat, 0, 0)
     del rhs
     x = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
-    prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=2, sloppy_recon=12, delta=DELTA, check_interval=64)
-    ws = F.empty(L.lqcd_cg_workspace_bytes(lat, op, prm, 0))
-    L.lqcd_cg_solve(x, be, g64, g16, lat, op, prm, 0, ws)
-    ms, info = _events_time(lambda: L.lqcd_cg_solve(x, be, g64, g16, lat, op, prm, 0, ws), stream, flush)
+    prm = {q: L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=q, sloppy_recon=12, delta=DELTA[q],
+                              check_interval=64) for q in (1, 2)}
+    ws = F.empty(max(L.lqcd_cg_workspace_bytes(lat, op, prm[q], 0) for q in (1, 2)))
     vh = 32 ** 4 // 2
-    out["multi_rhs_32x4_12rhs_mixed_fp16"] = {
-        "ms": round(ms, 3), "iterations": info.iterations, "reliable_updates": info.reliable_updates,
-        "max_true_rel_residual_normal_eq": info.true_rel_residual,
-        "dslash_gflops_in_solve": round(4 * (info.iterations + info.reliable_updates) * FLOP_PER_SITE * vh * nr
-                                        / (ms * 1e-3) / 1e9, 1),
-        "hop_f16r12_12rhs": _hop_gbs(L, F, lat, 2, 12, 8 * 24 / nr + 52 + 52, flush, stream),
-        "hop_f16r12_1rhs": _hop_gbs(L, F, L.lattice(dims, n5=1, bc=BC), 2, 12, 8 * 24 + 52 + 52, flush, stream)}
-    wsb = F.empty(L.lqcd_block_cg_workspace_bytes(lat, op, prm))
-    L.lqcd_block_cg_solve(x, be, g64, g16, lat, op, prm, wsb)
-    msb, infb = _events_time(lambda: L.lqcd_block_cg_solve(x, be, g64, g16, lat, op, prm, wsb), stream, flush)
-    out["multi_rhs_32x4_12rhs_mixed_fp16"]["block_cg"] = {
+    mr = {}
+    for q, name in ((1, "fp32_inner"), (2, "fp16_inner")):
+        L.lqcd_cg_solve(x, be, g64, gsl[q], lat, op, prm[q], 0, ws)
+        ms, info = _events_time(lambda: L.lqcd_cg_solve(x, be, g64, gsl[q], lat, op, prm[q], 0, ws), stream, flush)
+        mr[name] = {
+            "ms": round(ms, 3), "iterations": info.iterations, "reliable_updates": info.reliable_updates,
+            "delta": DELTA[q], "max_true_rel_residual_normal_eq": info.true_rel_residual,
+            "dslash_gflops_in_solve": round(4 * (info.iterations + info.reliable_updates) * FLOP_PER_SITE * vh * nr
+                                            / (ms * 1e-3) / 1e9, 1)}
+    wsb = F.empty(L.lqcd_block_cg_workspace_bytes(lat, op, prm[1]))
+    L.lqcd_block_cg_solve(x, be, g64, gsl[1], lat, op, prm[1], wsb)
+    msb, infb = _events_time(lambda: L.lqcd_block_cg_solve(x, be, g64, gsl[1], lat, op, prm[1], wsb), stream, flush)
+    mr["block_cg_fp32_inner"] = {
         "ms": round(msb, 3), "iterations": infb.iterations, "reliable_updates": infb.reliable_updates,
         "max_true_rel_residual_normal_eq": infb.true_rel_residual}
-    del g64, g16, be, x, ws, wsb
+    mr["hop_f32r12_12rhs"] = _hop_gbs(L, F, lat, 1, 12, 8 * 48 / nr + 96 + 96, flush, stream)
+    mr["hop_f16r12_12rhs"] = _hop_gbs(L, F, lat, 2, 12, 8 * 24 / nr + 52 + 52, flush, stream)
+    mr["hop_f32r12_1rhs"] = _hop_gbs(L, F, L.lattice(dims, n5=1, bc=BC), 1, 12, 8 * 48 + 96 + 96, flush, stream)
+    out["multi_rhs_32x4_12rhs_mixed"] = mr
+    del g64, gsl, be, x, ws, wsb
     torch.cuda.empty_cache()
 
     # uneven batch: 4 each of 8^4, 12^4, 16^4, 20^4, Haar links, m = 0.05, FP32-inner, one persistent launch per phase
@@ -572,7 +627,7 @@ def run_extras(L, F, flush, stream):
                             gauge_sloppy=F.gauge_to_device(U, lat, 1, 12),
                             x=F.empty(L.lqcd_spinor_bytes(lat, 0, 0)), b=F.spinor_to_device(bsrc, lat, 0, 0)))
     items = L.batch_items(entries)
-    prm = L.solver_params(tol=1e-10, maxiter=5000, sloppy_prec=1, sloppy_recon=12, delta=DELTA, check_interval=64)
+    prm = L.solver_params(tol=1e-10, maxiter=5000, sloppy_prec=1, sloppy_recon=12, delta=DELTA[1], check_interval=64)
     wsb = F.empty(L.lqcd_batch_cg_workspace_bytes(len(entries), items, 18, prm))
     L.lqcd_batch_cg_solve(len(entries), items, 18, prm, wsb)  # tunes the grid, captures the graph
     ms_b, infos = _events_time(lambda: L.lqcd_batch_cg_solve(len(entries), items, 18, prm, wsb), stream, flush)
@@ -608,7 +663,8 @@ def run_extras(L, F, flush, stream):
     X = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
     Y = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
     Fo = F.empty(L.lqcd_gauge_bytes(lat, 0, 18))
-    prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=18, delta=DELTA, check_interval=64)
+    prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=18, delta=DELTA[1],
+                          check_interval=64)
     ws = F.empty(L.lqcd_cg_workspace_bytes(lat, op, prm, 2))
 
     def force_step():

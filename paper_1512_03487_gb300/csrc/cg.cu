@@ -41,7 +41,6 @@ struct VecArgs {
   void* xs;           // sloppy-vector solution increment (VF)
   void* rs;           // sloppy-vector residual (VF)
   void* p;            // search direction (SF)
-  const void* ap;     // A p (SF)
   int64_t hb64, hbv, hbs;  // bytes of one checkerboard per format
   SysState* sys;
   ReduceCtx red;
@@ -71,19 +70,6 @@ __global__ void __launch_bounds__(BLAS_BLOCK) k_init(VecArgs a) {
   if (vec_site(a, parity, j, first))
     red = init_site<VF, SF>(a.g, j, PAR_PTR(a.b64, a.hb64), PAR_PTR(a.r64, a.hb64), PAR_PTR(a.x64, a.hb64),
                             PAR_PTR(a.rs, a.hbv), PAR_PTR(a.xs, a.hbv), PAR_PTR(a.p, a.hbs));
-  block_reduce_finalize<BLAS_BLOCK>(red, first, a.red);
-}
-
-// x_s += alpha p; r_s -= alpha Ap; |r_s|^2 -> beta or pause
-template <int VF, int SF>
-__global__ void __launch_bounds__(BLAS_BLOCK) k_update(VecArgs a) {
-  if (gate_closed(a.gate)) return;
-  int parity;
-  int64_t j, first;
-  double red = 0.0;
-  if (vec_site(a, parity, j, first))
-    red = update_site<VF, SF>(a.g, j, a.sys[sys_of(j, a.red.nsys)].alpha, PAR_PTR(a.p, a.hbs),
-                              PAR_PTR(a.ap, a.hbs), PAR_PTR(a.xs, a.hbv), PAR_PTR(a.rs, a.hbv));
   block_reduce_finalize<BLAS_BLOCK>(red, first, a.red);
 }
 
@@ -134,14 +120,12 @@ struct Workspace {
   void* rs;
   void* xs;
   void* p;
-  void* ap;
   void* mp;
   void* t1_s;
   void* t2_s;
   size_t total;
 };
 
-static int vec_prec(int sloppy) { return sloppy == LQCD_F64 ? LQCD_F64 : LQCD_F32; }
 
 static int64_t max_blocks(const Geom& g, int subset) {
   const int64_t per = (g.nsites + 63) / 64;  // smallest block size used by reducing kernels is >= 64
@@ -174,7 +158,6 @@ static Workspace carve(void* base, const Geom& g, const lqcd_operator& op, const
   w.rs = take(field_bytes(g, VF, subset));
   w.xs = take(field_bytes(g, VF, subset));
   w.p = take(field_bytes(g, SF, subset));
-  w.ap = take(field_bytes(g, SF, subset));
   w.mp = take(field_bytes(g, SF, subset));
   if (subset == LQCD_EVEN) {
     w.t1_s = take(cb_spinor_bytes(g, SF));
@@ -201,13 +184,12 @@ static int validate(const lqcd_lattice* lat, const lqcd_operator* op, const lqcd
 }
 
 // Launch helpers for the (VF, SF) instantiations.
-enum VecKernel { VK_INIT, VK_UPDATE, VK_PUPDATE, VK_ACCUM, VK_RESIDUAL };
+enum VecKernel { VK_INIT, VK_PUPDATE, VK_ACCUM, VK_RESIDUAL };
 
 template <int VF, int SF>
 static void launch_vec_t(VecKernel k, unsigned grid, const VecArgs& a, cudaStream_t s) {
   switch (k) {
     case VK_INIT: k_init<VF, SF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
-    case VK_UPDATE: k_update<VF, SF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
     case VK_PUPDATE: k_pupdate<VF, SF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
     case VK_ACCUM: k_accumulate<VF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
     case VK_RESIDUAL: k_residual<VF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
@@ -242,17 +224,18 @@ struct Solver : CgEngine {
     return launch_vec(VK_INIT, prm.sloppy_prec, a, s);
   }
 
+  // M_hat p with |M_hat p|^2 = p^dag A p -> alpha; then M_hat^dag (M_hat p) = A p,
+  // whose last hop applies x_s += alpha p, r_s -= alpha A p and reduces |r_s|^2
+  // (beta, or a reliable-update request) instead of storing A p.
   int head(cudaStream_t s, int cond, cudaGraphConditionalHandle h_rel) override {
     OpCtx cs{g, ops, gauge_s};
     int st = op_apply(cs, w.mp, w.p, subset, 0, w.t1_s, w.t2_s, &rc_alpha, w.ctrl, s);
     if (st) return st;
-    if ((st = op_apply(cs, w.ap, w.mp, subset, 1, w.t1_s, w.t2_s, nullptr, w.ctrl, s))) return st;
-    VecArgs a = va;
-    a.red = rc_update;
-    a.red.cond = cond;
-    a.red.h_rel = h_rel;
-    a.gate = w.ctrl;
-    return launch_vec(VK_UPDATE, prm.sloppy_prec, a, s);
+    ReduceCtx ru = rc_update;
+    ru.cond = cond;
+    ru.h_rel = h_rel;
+    const HopUpdate upd{w.p, w.xs, w.rs, va.hbv};
+    return op_apply(cs, nullptr, w.mp, subset, 1, w.t1_s, w.t2_s, &ru, w.ctrl, s, &upd);
   }
 
   int tail(cudaStream_t s) override {
@@ -340,7 +323,6 @@ int lqcd_cg_solve(void* x, const void* b, const void* gauge, const void* gauge_s
   a.xs = S.w.xs;
   a.rs = S.w.rs;
   a.p = S.w.p;
-  a.ap = S.w.ap;
   a.hb64 = (int64_t)cb_spinor_bytes(S.g, LQCD_F64);
   a.hbv = (int64_t)cb_spinor_bytes(S.g, VF);
   a.hbs = (int64_t)cb_spinor_bytes(S.g, SF);

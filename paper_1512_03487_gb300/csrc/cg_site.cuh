@@ -43,16 +43,15 @@ __device__ __forceinline__ double init_site(const Geom& g, int64_t j, const doub
   return site_norm2(b);
 }
 
-// x_s += alpha p; r_s -= alpha Ap; returns |r_s|^2
-template <int VF, int SF>
-__device__ __forceinline__ double update_site(const Geom& g, int64_t j, double alpha_d, const void* p_,
-                                              const void* ap_, void* xs, void* rs) {
+// x_s += alpha p; r_s -= alpha Ap with Ap given in registers; returns |r_s|^2
+template <int VF, int SF, typename TA>
+__device__ __forceinline__ double update_site_ap(const Geom& g, int64_t j, double alpha_d, const void* p_,
+                                                 const Spinor<TA>& ap, void* xs, void* rs) {
   using TV = typename PrecTraits<VF>::real;
   using TS = typename PrecTraits<SF>::real;
   const TV alpha = (TV)alpha_d;
-  Spinor<TS> p, ap;
+  Spinor<TS> p;
   SpinorIO<SF>::load(p_, g.sstride, j, p);
-  SpinorIO<SF>::load(ap_, g.sstride, j, ap);
   Spinor<TV> x, r;
   SpinorIO<VF>::load(xs, g.sstride, j, x);
   SpinorIO<VF>::load(rs, g.sstride, j, r);
@@ -64,6 +63,15 @@ __device__ __forceinline__ double update_site(const Geom& g, int64_t j, double a
   SpinorIO<VF>::store(xs, g.sstride, j, x);
   SpinorIO<VF>::store(rs, g.sstride, j, r);
   return site_norm2(r);
+}
+
+// x_s += alpha p; r_s -= alpha Ap; returns |r_s|^2
+template <int VF, int SF>
+__device__ __forceinline__ double update_site(const Geom& g, int64_t j, double alpha_d, const void* p_,
+                                              const void* ap_, void* xs, void* rs) {
+  Spinor<typename PrecTraits<SF>::real> ap;
+  SpinorIO<SF>::load(ap_, g.sstride, j, ap);
+  return update_site_ap<VF, SF>(g, j, alpha_d, p_, ap, xs, rs);
 }
 
 // p = r_s + beta p

@@ -2,7 +2,7 @@
 #include "dslash_launch.cuh"
 
 namespace lqcd {
-int launch_hop_f64(int recon, bool dagger, int epi, bool reduce, HopArgs a, cudaStream_t s) {
+int launch_hop_f64(int recon, bool dagger, int epi, int reduce, HopArgs a, cudaStream_t s) {
   return launch_hop_prec<LQCD_F64>(recon, dagger, epi, reduce, a, s);
 }
 }  // namespace lqcd

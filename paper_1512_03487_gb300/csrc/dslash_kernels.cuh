@@ -18,6 +18,7 @@
 // the lower half is S B^dag h, so only h is multiplied by the link.
 #pragma once
 
+#include "cg_site.cuh"
 #include "lqcd_common.cuh"
 
 namespace lqcd {
@@ -36,9 +37,19 @@ struct HopArgs {
   int64_t half_bytes;     // bytes of one checkerboard of a full field
   double a, b;            // EPI_PLAIN: out = b H in; EPI_XPAY: out = a x + b H in
   double m5d, mf;         // EPI_M5: out = M5op(x) + b H in, M5op diagonal m5d = 5 - M5
-  ReduceCtx red;          // |out|^2 per system when reducing
+  ReduceCtx red;          // |out|^2 per system (RED_NORM) or |r_s|^2 (RED_CG_UPDATE)
   const Control* gate;    // kernel returns at once when gate->active == 0
+  // RED_CG_UPDATE: out = A p is not stored; instead x_s += alpha p and
+  // r_s -= alpha A p, alpha = red.sys[system].alpha. p is in the format of
+  // out; x_s and r_s in vec_prec of it (upd_half_bytes: one checkerboard).
+  const void* upd_p;
+  void* upd_xs;
+  void* upd_rs;
+  int64_t upd_half_bytes;
 };
+
+// Reduction / epilogue modes of the hop kernel.
+enum HopReduce { RED_NONE = 0, RED_NORM = 1, RED_CG_UPDATE = 2 };
 
 template <int MU, int S, typename T>
 __device__ __forceinline__ void project(const Spinor<T>& s, Half<T>& h) {
@@ -288,7 +299,7 @@ template <typename T> __device__ __forceinline__ double norm2_site(const Spinor<
   return (double)s;
 }
 
-template <int P, int R, bool DAG, int EPI, bool RED, int BLOCK>
+template <int P, int R, bool DAG, int EPI, int RED, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) hop_kernel(const HopArgs A) {
   using T = typename PrecTraits<P>::real;
   if (gate_closed(A.gate)) return;
@@ -307,8 +318,15 @@ __global__ void __launch_bounds__(BLOCK) hop_kernel(const HopArgs A) {
     Spinor<T> res;
     const EpiCoef c{A.a, A.b, A.m5d, A.mf};
     hop_site<P, R, DAG, EPI>(A.g, A.gauge, in, xb, parity, j, c, res);
-    SpinorIO<P>::store(out, A.g.sstride, j, res);
-    if (RED) red = norm2_site(res);
+    if (RED == RED_CG_UPDATE) {
+      const int64_t ps = A.full ? parity * A.half_bytes : 0, vs = A.full ? parity * A.upd_half_bytes : 0;
+      red = update_site_ap<vec_prec(P), P>(A.g, j, A.red.sys[sys_of(j, A.red.nsys)].alpha,
+                                           static_cast<const char*>(A.upd_p) + ps,
+                                           res, static_cast<char*>(A.upd_xs) + vs, static_cast<char*>(A.upd_rs) + vs);
+    } else {
+      SpinorIO<P>::store(out, A.g.sstride, j, res);
+      if (RED == RED_NORM) red = norm2_site(res);
+    }
   }
   if (RED) block_reduce_finalize<BLOCK>(red, (int64_t)blk * BLOCK, A.red);
 }

@@ -6,7 +6,7 @@
 
 namespace lqcd {
 
-template <int P, int R, bool DAG, int EPI, bool RED>
+template <int P, int R, bool DAG, int EPI, int RED>
 static int launch_hop_inst(const HopArgs& a, cudaStream_t s) {
   const int64_t nb = (a.g.nsites + HOP_BLOCK - 1) / HOP_BLOCK;
   const int64_t grid = a.full ? 2 * nb : nb;
@@ -15,18 +15,25 @@ static int launch_hop_inst(const HopArgs& a, cudaStream_t s) {
   return after_launch("hop_kernel");
 }
 
+template <int P, int R, bool DAG, int EPI>
+static int launch_hop_red(int red, const HopArgs& a, cudaStream_t s) {
+  if (red == RED_NONE) return launch_hop_inst<P, R, DAG, EPI, RED_NONE>(a, s);
+  if (red == RED_NORM) return launch_hop_inst<P, R, DAG, EPI, RED_NORM>(a, s);
+  // the fused CG update follows the last hop of M^dag M, always a dagger hop
+  if (DAG && red == RED_CG_UPDATE) return launch_hop_inst<P, R, DAG, EPI, DAG ? RED_CG_UPDATE : RED_NONE>(a, s);
+  return fail(LQCD_ERR_UNSUPPORTED, "hop reduction mode %d (dagger %d)", red, (int)DAG);
+}
+
 template <int P, int R, bool DAG>
-static int launch_hop_epi(int epi, bool red, const HopArgs& a, cudaStream_t s) {
-  if (epi == EPI_PLAIN) return launch_hop_inst<P, R, DAG, EPI_PLAIN, false>(a, s);
-  if (epi == EPI_XPAY)
-    return red ? launch_hop_inst<P, R, DAG, EPI_XPAY, true>(a, s) : launch_hop_inst<P, R, DAG, EPI_XPAY, false>(a, s);
-  if (epi == EPI_M5)
-    return red ? launch_hop_inst<P, R, DAG, EPI_M5, true>(a, s) : launch_hop_inst<P, R, DAG, EPI_M5, false>(a, s);
+static int launch_hop_epi(int epi, int red, const HopArgs& a, cudaStream_t s) {
+  if (epi == EPI_PLAIN) return launch_hop_inst<P, R, DAG, EPI_PLAIN, RED_NONE>(a, s);
+  if (epi == EPI_XPAY) return launch_hop_red<P, R, DAG, EPI_XPAY>(red, a, s);
+  if (epi == EPI_M5) return launch_hop_red<P, R, DAG, EPI_M5>(red, a, s);
   return fail(LQCD_ERR_ARG, "bad epilogue %d", epi);
 }
 
 template <int P>
-static int launch_hop_prec(int recon, bool dagger, int epi, bool red, HopArgs a, cudaStream_t s) {
+static int launch_hop_prec(int recon, bool dagger, int epi, int red, HopArgs a, cudaStream_t s) {
   a.blocks_per_parity = (int)((a.g.nsites + HOP_BLOCK - 1) / HOP_BLOCK);
   if (epi == EPI_PLAIN && red) return fail(LQCD_ERR_UNSUPPORTED, "plain hop with reduction");
   if (recon == 18)

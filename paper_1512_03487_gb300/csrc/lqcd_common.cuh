@@ -66,6 +66,10 @@ template <> struct PrecTraits<LQCD_F64> { using real = double; static constexpr 
 template <> struct PrecTraits<LQCD_F32> { using real = float; static constexpr int site_bytes = 96; };
 template <> struct PrecTraits<LQCD_F16> { using real = float; static constexpr int site_bytes = 52; };
 
+// Format of the iterated CG vectors x_s, r_s for a given sloppy storage format:
+// FP64 stays FP64, FP32 and FP16 storage iterate in FP32.
+__host__ __device__ constexpr int vec_prec(int sloppy) { return sloppy == LQCD_F64 ? LQCD_F64 : LQCD_F32; }
+
 inline int spinor_site_bytes(int prec) {
   return prec == LQCD_F64 ? 192 : prec == LQCD_F32 ? 96 : prec == LQCD_F16 ? 52 : 0;
 }

@@ -7,10 +7,10 @@
 namespace lqcd {
 
 // ---- hop launchers (one translation unit per precision)
-int launch_hop(int prec, int recon, bool dagger, int epi, bool reduce, HopArgs a, cudaStream_t s);
-int launch_hop_f64(int recon, bool dagger, int epi, bool reduce, HopArgs a, cudaStream_t s);
-int launch_hop_f32(int recon, bool dagger, int epi, bool reduce, HopArgs a, cudaStream_t s);
-int launch_hop_f16(int recon, bool dagger, int epi, bool reduce, HopArgs a, cudaStream_t s);
+int launch_hop(int prec, int recon, bool dagger, int epi, int reduce, HopArgs a, cudaStream_t s);
+int launch_hop_f64(int recon, bool dagger, int epi, int reduce, HopArgs a, cudaStream_t s);
+int launch_hop_f32(int recon, bool dagger, int epi, int reduce, HopArgs a, cudaStream_t s);
+int launch_hop_f16(int recon, bool dagger, int epi, int reduce, HopArgs a, cudaStream_t s);
 
 // Blocks of the hop kernel per checkerboard (the reduction buffers are sized from it).
 constexpr int HOP_BLOCK = 128;
@@ -37,8 +37,17 @@ struct OpCtx {
 };
 // out = M in (subset LQCD_FULL) or M_hat in (LQCD_EVEN), dagger; optional |out|^2
 // reduction and gate. t1, t2: odd checkerboard temporaries (EVEN subset).
+// With upd (and red) the last hop does not store out but runs the fused CG
+// update of HopArgs::upd_* instead (dagger only).
+struct HopUpdate {
+  const void* p;
+  void* xs;
+  void* rs;
+  int64_t half_bytes;  // one checkerboard of x_s / r_s
+};
 int op_apply(const OpCtx& c, void* out, const void* in, int subset, int dagger,
-             void* t1, void* t2, const ReduceCtx* red, const Control* gate, cudaStream_t s);
+             void* t1, void* t2, const ReduceCtx* red, const Control* gate, cudaStream_t s,
+             const HopUpdate* upd = nullptr);
 // Bytes of the temporaries op_apply needs (t1 + t2) for a subset.
 size_t op_tmp_bytes(const Geom& g, int kind, int prec, int subset);
 // Bytes of a field of the given subset.

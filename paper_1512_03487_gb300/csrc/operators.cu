@@ -8,7 +8,7 @@
 
 namespace lqcd {
 
-int launch_hop(int prec, int recon, bool dagger, int epi, bool reduce, HopArgs a, cudaStream_t s) {
+int launch_hop(int prec, int recon, bool dagger, int epi, int reduce, HopArgs a, cudaStream_t s) {
   switch (prec) {
     case LQCD_F64: return launch_hop_f64(recon, dagger, epi, reduce, a, s);
     case LQCD_F32: return launch_hop_f32(recon, dagger, epi, reduce, a, s);
@@ -36,8 +36,17 @@ static HopArgs base_args(const OpCtx& c, const ReduceCtx* red, const Control* ga
 }
 
 int op_apply(const OpCtx& c, void* out, const void* in, int subset, int dagger, void* t1, void* t2,
-             const ReduceCtx* red, const Control* gate, cudaStream_t s) {
+             const ReduceCtx* red, const Control* gate, cudaStream_t s, const HopUpdate* upd) {
   const int P = c.op.prec, R = c.op.recon;
+  if (upd && (!red || !dagger)) return fail(LQCD_ERR_ARG, "fused CG update needs a reduction and dagger");
+  const int mode = upd ? RED_CG_UPDATE : red ? RED_NORM : RED_NONE;
+  auto set_upd = [&](HopArgs& a) {
+    if (!upd) return;
+    a.upd_p = upd->p;
+    a.upd_xs = upd->xs;
+    a.upd_rs = upd->rs;
+    a.upd_half_bytes = upd->half_bytes;
+  };
   const bool wilson = c.op.kind == LQCD_WILSON;
   const double cw = 4.0 + c.op.mass;
   if (subset == LQCD_FULL) {
@@ -49,7 +58,8 @@ int op_apply(const OpCtx& c, void* out, const void* in, int subset, int dagger, 
     a.x = in;
     a.a = cw;
     a.b = -0.5;
-    return launch_hop(P, R, dagger, wilson ? EPI_XPAY : EPI_M5, red != nullptr, a, s);
+    set_upd(a);
+    return launch_hop(P, R, dagger, wilson ? EPI_XPAY : EPI_M5, mode, a, s);
   }
   if (subset != LQCD_EVEN) return fail(LQCD_ERR_ARG, "operator subset must be LQCD_EVEN or LQCD_FULL");
   HopArgs h1 = base_args(c, nullptr, gate);
@@ -57,7 +67,7 @@ int op_apply(const OpCtx& c, void* out, const void* in, int subset, int dagger, 
   h1.out = t1;
   h1.in = in;
   h1.b = 1.0;
-  int st = launch_hop(P, R, dagger, EPI_PLAIN, false, h1, s);
+  int st = launch_hop(P, R, dagger, EPI_PLAIN, RED_NONE, h1, s);
   if (st) return st;
   const void* src = t1;
   if (!wilson) {
@@ -83,7 +93,8 @@ int op_apply(const OpCtx& c, void* out, const void* in, int subset, int dagger, 
   } else {
     h2.b = -0.25;
   }
-  return launch_hop(P, R, dagger, wilson ? EPI_XPAY : EPI_M5, red != nullptr, h2, s);
+  set_upd(h2);
+  return launch_hop(P, R, dagger, wilson ? EPI_XPAY : EPI_M5, mode, h2, s);
 }
 
 static bool misaligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) != 0; }
@@ -118,7 +129,7 @@ int lqcd_dslash(void* out, const void* in, const void* gauge, const lqcd_lattice
   a.full = out_subset == LQCD_FULL;
   a.out_parity = a.full ? 0 : out_subset;
   a.half_bytes = (int64_t)cb_spinor_bytes(g, op->prec);
-  return launch_hop(op->prec, op->recon, dagger != 0, EPI_PLAIN, false, a, (cudaStream_t)stream);
+  return launch_hop(op->prec, op->recon, dagger != 0, EPI_PLAIN, RED_NONE, a, (cudaStream_t)stream);
 }
 
 size_t lqcd_operator_workspace_bytes(const lqcd_lattice* lat, const lqcd_operator* op, int subset) {
@@ -187,7 +198,7 @@ int lqcd_eo_prepare(void* bhat, const void* b_full, const void* gauge, const lqc
     a.in = tmp;
     a.b = 0.5;
   }
-  return launch_hop(op->prec, op->recon, false, EPI_XPAY, false, a, s);
+  return launch_hop(op->prec, op->recon, false, EPI_XPAY, RED_NONE, a, s);
 }
 
 int lqcd_eo_reconstruct(void* x_full, const void* b_full, const void* gauge, const lqcd_lattice* lat,
@@ -210,12 +221,12 @@ int lqcd_eo_reconstruct(void* x_full, const void* b_full, const void* gauge, con
     a.out = off(x_full, cb);
     a.a = 1.0 / cw;
     a.b = 1.0 / (2.0 * cw);
-    return launch_hop(op->prec, op->recon, false, EPI_XPAY, false, a, s);
+    return launch_hop(op->prec, op->recon, false, EPI_XPAY, RED_NONE, a, s);
   }
   a.out = tmp;
   a.a = 1.0;
   a.b = 0.5;
-  if ((st = launch_hop(op->prec, op->recon, false, EPI_XPAY, false, a, s))) return st;
+  if ((st = launch_hop(op->prec, op->recon, false, EPI_XPAY, RED_NONE, a, s))) return st;
   M5Args m{off(x_full, cb), tmp, g, 5.0 - op->M5, op->mf, 0, nullptr};
   return launch_m5inv(op->prec, m, s);
 }
