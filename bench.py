@@ -63,6 +63,9 @@ def parse_args():
                     help="iterations per graph launch / host check of the solver")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the domain-wall, multi-RHS, batch and force measurements")
+    ap.add_argument("--hop-shape", default=None,
+                    help="hops mode: run only this shape (f32r12_24x24x24x48, f16r12_24x24x24x48, "
+                         "dwf_f32r12_16x4_ls16, f32r12_32x4_12rhs)")
     ap.add_argument("--mode", choices=["full", "step", "hop", "hops"], default="full",
                     help="step: only the timed solves; hop: only the dominant kernel's roofline loop; "
                          "hops: the three hop shapes (profiling)")
@@ -206,15 +209,17 @@ def run_lqcd(args, world, rank, local):
         # profiling mode: the three hop shapes of the hot path on zero-filled fields
         # (the kernels do the same work whatever the values), args.steps launches each
         flush = L2Flush(dev)
-        res = {
-            "f32r12_24x24x24x48": _hop_gbs(L, F, L.lattice((24, 24, 24, 48), bc=BC), 1, 12, 576, flush, stream,
-                                           n=args.steps),
-            "f16r12_24x24x24x48": _hop_gbs(L, F, L.lattice((24, 24, 24, 48), bc=BC), 2, 12, 296, flush, stream,
-                                           n=args.steps),
-            "dwf_f32r12_16x4_ls16": _hop_gbs(L, F, L.lattice((16, 16, 16, 16), n5=16, bc=BC), 1, 12,
-                                             8 * 48 / 16 + 192, flush, stream, kind=L.LQCD_DWF, n=args.steps),
-            "f32r12_32x4_12rhs": _hop_gbs(L, F, L.lattice((32, 32, 32, 32), n5=12, bc=BC), 1, 12, 8 * 48 / 12 + 192,
-                                          flush, stream, n=args.steps)}
+        shapes = {
+            "f32r12_24x24x24x48": lambda: _hop_gbs(L, F, L.lattice((24, 24, 24, 48), bc=BC), 1, 12, 576, flush,
+                                                   stream, n=args.steps),
+            "f16r12_24x24x24x48": lambda: _hop_gbs(L, F, L.lattice((24, 24, 24, 48), bc=BC), 2, 12, 296, flush,
+                                                   stream, n=args.steps),
+            "dwf_f32r12_16x4_ls16": lambda: _hop_gbs(L, F, L.lattice((16, 16, 16, 16), n5=16, bc=BC), 1, 12,
+                                                     8 * 48 / 16 + 192, flush, stream, kind=L.LQCD_DWF, n=args.steps),
+            "f32r12_32x4_12rhs": lambda: _hop_gbs(L, F, L.lattice((32, 32, 32, 32), n5=12, bc=BC), 1, 12,
+                                                  8 * 48 / 12 + 192, flush, stream, n=args.steps)}
+        names = [args.hop_shape] if args.hop_shape else list(shapes)
+        res = {name: shapes[name]() for name in names}
         if rank == 0:
             print(json.dumps({"mode": "hops", "hops": res}), flush=True)
         return
@@ -616,6 +621,8 @@ def run_extras(L, F, flush, stream):
     del g64, gsl, be, x, ws, wsb
     torch.cuda.empty_cache()
 
+    out["su3_mul_footprint"] = su3_sweep(L, F, flush, stream)
+
     # uneven batch: 4 each of 8^4, 12^4, 16^4, 20^4, Haar links, m = 0.05, FP32-inner, one persistent launch per phase
     shapes = [(n_, n_, n_, n_) for n_ in (8, 12, 16, 20) for _ in range(4)]
     entries = []
@@ -688,6 +695,62 @@ def run_extras(L, F, flush, stream):
 
 
 # ------------------------------------------------------------------ reference arm
+
+def su3_sweep(L, F, flush, stream):
+    """SU(3) x SU(3) field product z = x y against memory footprint (the paper's first
+    benchmark): FP32 L^4 fields from L2-resident to 3.6 GB, timed back to back (warm) and,
+    beyond L2, after an L2 flush (cold); FP64 at 48^4 cold. 216 B and 198 flop per FP32 site."""
+    import torch
+    peak, _ = measured_peak()
+    rows = []
+    for prec, sizes in ((1, (8, 12, 16, 24, 32, 48, 64)), (0, (48,))):
+        bps = 216 if prec == 1 else 432
+        for n_ in sizes:
+            lat = L.lattice((n_, n_, n_, n_))
+            nsites = n_ ** 4
+            f = [F.empty(L.lqcd_colour_matrix_bytes(lat, prec)) for _ in range(3)]
+            for t in f:
+                t.zero_()
+            # warm: 50 launches captured in one CUDA graph and replayed back to back, so that
+            # L2-resident sizes show the GPU's time rather than the host's launch rate
+            reps = 50
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                for _ in range(3):
+                    L.lqcd_su3_mul(f[2], f[0], f[1], lat, prec)
+            torch.cuda.current_stream().wait_stream(side)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                for _ in range(reps):
+                    L.lqcd_su3_mul(f[2], f[0], f[1], lat, prec)
+            graph.replay()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            warm = e0.elapsed_time(e1) / reps * 1e-3
+            del graph
+            row = {"prec": "f32" if prec == 1 else "f64", "lattice": [n_] * 4, "sites": nsites,
+                   "footprint_mb": round(bps * nsites / 1e6, 2), "warm_us": round(warm * 1e6, 2),
+                   "warm_gbs": round(bps * nsites / warm / 1e9, 1),
+                   "warm_gflops": round(198 * nsites / warm / 1e9, 1)}
+            if bps * nsites > 256e6:
+                cold, _ = _events_time(lambda: L.lqcd_su3_mul(f[2], f[0], f[1], lat, prec), stream, flush, reps=5)
+                cold *= 1e-3
+                row.update({"cold_us": round(cold * 1e6, 2), "cold_gbs": round(bps * nsites / cold / 1e9, 1),
+                            "frac_of_measured_hbm": round(bps * nsites / cold / 1e9 / peak, 4)})
+                if prec == 0:  # 198 FP64 flop per 432 B: bound by the FP64 pipe, not by HBM
+                    row.update({"bound": "alu", "cold_tflops": round(198 * nsites / cold / 1e12, 4),
+                                "frac_of_nominal_fp64": round(198 * nsites / cold / 1e12 / 1.25, 4)})
+            rows.append(row)
+            del f
+    torch.cuda.empty_cache()
+    return rows
+
 
 def run_reference(args, world, rank):
     """The FP64 numpy oracle, as it stands, timed on the host cores on the same

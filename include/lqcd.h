@@ -319,6 +319,30 @@ int lqcd_M_noalloc(void* out_dev, const void* in_dev, const void* gauge_dev,
                    const lqcd_lattice* lat, const lqcd_operator* op, int subset, int dagger,
                    void* stream);
 
+/* ---------------------------------------------------------------- colour-matrix fields */
+
+/* Fields of 3x3 complex matrices, one per site (the paper's
+ * LatticeColourMatrix), and their site-by-site product z = x * y, the first
+ * kernel of the paper's performance section (Sec. 5: SU(3) x SU(3) product of
+ * fields, performance against memory footprint).
+ *  Sites: every site of the lattice times n5 (no checkerboarding).
+ *  Host layout: M[i5][t][z][y][x][row][col], complex FP64 interleaved.
+ *  Device layout (produced by lqcd_colour_matrix_pack): structure of arrays,
+ *    site fastest, stride = sites rounded up to 32; FP64 9 chunks of double2
+ *    (entries row-major); FP32 4 chunks of float4 (entries 0-7) then one
+ *    chunk of float2 (entry 8). prec: LQCD_F64 or LQCD_F32 (else
+ *    LQCD_ERR_ARG). Pointers must be 16-byte aligned. */
+size_t lqcd_colour_matrix_bytes(const lqcd_lattice* lat, int prec);
+int lqcd_colour_matrix_pack(void* dst_dev, int prec, const double* src_dev, const lqcd_lattice* lat,
+                            void* stream);
+int lqcd_colour_matrix_unpack(double* dst_dev, const void* src_dev, int prec, const lqcd_lattice* lat,
+                              void* stream);
+/* z(s) = x(s) y(s) at every site s (z_ik = sum_j x_ij y_jk), computed in the
+ * field precision. z may be x or y (each site is read before it is written).
+ * Asynchronous on stream. 198 flop per site. */
+int lqcd_su3_mul(void* z_dev, const void* x_dev, const void* y_dev, const lqcd_lattice* lat, int prec,
+                 void* stream);
+
 /* ---------------------------------------------------------------- force */
 
 /* Pseudofermion force for S = phi^dag (M^dag M)^-1 phi with M = D_W (Grid

@@ -1,5 +1,6 @@
 """Plain, slow FP64 CPU oracle for the Wilson / domain-wall Dirac operators,
-the even-odd Schur complement, conjugate gradient and the fermion force.
+the even-odd Schur complement, conjugate gradient, the fermion force and the
+SU(3) x SU(3) field product.
 
 TEST INFRASTRUCTURE ONLY. Nothing in the library imports this package; only
 the test suite, the smoke check and the CPU-baseline / reference leg of the
@@ -16,4 +17,4 @@ convention chosen where the paper is silent, and each function is pinned by a
 test against a closed form, an identity or brute force; see the module
 headers. No function here is "parity unpinned".
 """
-from . import gamma, wilson, dwf, cg, force  # noqa: F401
+from . import gamma, wilson, dwf, cg, force, su3  # noqa: F401

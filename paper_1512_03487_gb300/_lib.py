@@ -84,6 +84,10 @@ SIGNATURES = {
     "lqcd_cg_workspace_bytes": (_SZ, [_LAT, _OP, _PRM, _I]),
     "lqcd_cg_solve": (_I, [_P, _P, _P, _P, _LAT, _OP, _PRM, _I, _INFO, _P, _SZ, _P]),
     "lqcd_force": (_I, [_P, _P, _P, _P, _LAT, _OP, _I, _P]),
+    "lqcd_colour_matrix_bytes": (_SZ, [_LAT, _I]),
+    "lqcd_colour_matrix_pack": (_I, [_P, _I, _P, _LAT, _P]),
+    "lqcd_colour_matrix_unpack": (_I, [_P, _P, _I, _LAT, _P]),
+    "lqcd_su3_mul": (_I, [_P, _P, _P, _LAT, _I, _P]),
     "lqcd_M_noalloc": (_I, [_P, _P, _P, _LAT, _OP, _I, _I, _P]),
     "lqcd_block_cg_workspace_bytes": (_SZ, [_LAT, _OP, _PRM]),
     "lqcd_block_cg_solve": (_I, [_P, _P, _P, _P, _LAT, _OP, _PRM, _INFO, _P, _SZ, _P]),

@@ -243,6 +243,22 @@ def lqcd_tune_entries() -> int:
     return int(lib.lqcd_tune_entries())
 
 
+def lqcd_colour_matrix_bytes(lat, prec) -> int:
+    return int(lib.lqcd_colour_matrix_bytes(C.byref(lat), prec))
+
+
+def lqcd_colour_matrix_pack(dst, prec, src, lat, stream=None):
+    _check(lib.lqcd_colour_matrix_pack(_ptr(dst), prec, _ptr(src), C.byref(lat), _stream(stream)))
+
+
+def lqcd_colour_matrix_unpack(dst, src, prec, lat, stream=None):
+    _check(lib.lqcd_colour_matrix_unpack(_ptr(dst), _ptr(src), prec, C.byref(lat), _stream(stream)))
+
+
+def lqcd_su3_mul(z, x, y, lat, prec, stream=None):
+    _check(lib.lqcd_su3_mul(_ptr(z), _ptr(x), _ptr(y), C.byref(lat), prec, _stream(stream)))
+
+
 def lqcd_force(out, gauge, X, Y, lat, op, kind, stream=None):
     _check(lib.lqcd_force(_ptr(out), _ptr(gauge), _ptr(X), _ptr(Y), C.byref(lat), C.byref(op), kind,
                           _stream(stream)))

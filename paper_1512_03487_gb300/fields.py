@@ -71,6 +71,25 @@ def gauge_to_host(field: torch.Tensor, lat, prec: int, recon: int, stream=None) 
     return staging.cpu().numpy().view(np.complex128).reshape(shape)
 
 
+def host_colour_matrix_shape(lat):
+    X, Y, Z, T = (int(lat.dims[k]) for k in range(4))
+    return (int(lat.n5), T, Z, Y, X, 3, 3)
+
+
+def colour_matrix_to_device(M, lat, prec: int, stream=None) -> torch.Tensor:
+    staging = _as_device_f64(M)
+    dst = empty(api.lqcd_colour_matrix_bytes(lat, prec))
+    api.lqcd_colour_matrix_pack(dst, prec, staging, lat, stream)
+    return dst
+
+
+def colour_matrix_to_host(field: torch.Tensor, lat, prec: int, stream=None) -> np.ndarray:
+    shape = host_colour_matrix_shape(lat)
+    staging = torch.empty(2 * int(np.prod(shape)), dtype=torch.float64, device="cuda")
+    api.lqcd_colour_matrix_unpack(staging, field, prec, lat, stream)
+    return staging.cpu().numpy().view(np.complex128).reshape(shape)
+
+
 def checkerboard(full: np.ndarray, parity: int) -> np.ndarray:
     """Sites of one parity of a full-lattice array ``[..., T, Z, Y, X, 4, 3]``
     in lexicographic order, shaped ``[..., T, Z, Y, X/2, 4, 3]``."""

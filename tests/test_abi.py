@@ -113,3 +113,17 @@ def test_cg_rejects_bad_arguments_on_host(api):
     st = api.lib.lqcd_cg_solve(4096, 8192, 12288, 12288, C.byref(lat), C.byref(op), C.byref(prm),
                                api.LQCD_EVEN, C.byref(info), 1 << 20, 16, None)
     assert st == -7  # workspace too small
+
+
+def test_colour_matrix_sizes_and_rejections(api):
+    lat = api.lattice((4, 4, 4, 6), n5=3)  # 1152 sites, padded to 1152
+    assert api.lqcd_colour_matrix_bytes(lat, api.LQCD_F64) == 1152 * 144
+    assert api.lqcd_colour_matrix_bytes(lat, api.LQCD_F32) == 1152 * 72
+    assert api.lqcd_colour_matrix_bytes(api.lattice((2, 2, 2, 6), n5=1), api.LQCD_F32) == 64 * 72  # 48 -> 64
+    assert api.lqcd_colour_matrix_bytes(lat, api.LQCD_F16) == 0
+    buf = 4096
+    for z, x, y, prec in ((buf, buf, buf, api.LQCD_F16), (0, buf, buf, api.LQCD_F32),
+                          (buf + 8, buf, buf, api.LQCD_F64)):
+        with pytest.raises(api.LqcdError) as ei:
+            api.lqcd_su3_mul(z, x, y, lat, prec, stream=0)
+        assert ei.value.status == -1
