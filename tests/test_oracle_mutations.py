@@ -103,3 +103,33 @@ def test_force_mutations_are_caught(monkeypatch, mutation):
 
     fd = (S(ex(T, eps) @ U) - S(ex(T, -eps) @ U)) / (2 * eps)
     assert abs(fd - analytic) > 1e-3 * abs(fd)
+
+
+def _gauge_fd_error(g_module):
+    from synthetic import make_rng, random_su3_algebra
+    dims = (2, 4, 2, 4)
+    U = gauge_field(dims, "exp", 1504, eps=0.5)
+    T = random_su3_algebra(make_rng(1505), U.size // 9).reshape(U.shape)
+    analytic = np.einsum("...ij,...ji->...", T, g_module.force(U, 5.6)).real.sum()
+    h = 1e-5
+    fd = (g_module.action(g_module.update_links(U, T, h), 5.6) -
+          g_module.action(g_module.update_links(U, T, -h), 5.6)) / (2 * h)
+    return abs(fd - analytic) / abs(fd)
+
+
+@pytest.mark.parametrize("mutation", ["lower_staple_unshifted", "staple_dagger", "force_sign", "half_coupling"])
+def test_gauge_force_mutations_are_caught(monkeypatch, mutation):
+    from oracle import gauge
+    assert _gauge_fd_error(gauge) < 1e-6
+    if mutation == "lower_staple_unshifted":
+        monkeypatch.setattr(gauge, "_bwd", lambda f, mu: f)
+    elif mutation == "staple_dagger":
+        orig = gauge.staple
+        monkeypatch.setattr(gauge, "staple", lambda U, mu: gauge.dag(orig(U, mu)))
+    elif mutation == "force_sign":
+        orig = gauge.force
+        monkeypatch.setattr(gauge, "force", lambda U, beta: -orig(U, beta))
+    elif mutation == "half_coupling":
+        orig = gauge.force
+        monkeypatch.setattr(gauge, "force", lambda U, beta: orig(U, beta / 2))
+    assert _gauge_fd_error(gauge) > 1e-3
