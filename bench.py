@@ -622,6 +622,7 @@ def run_extras(L, F, flush, stream):
     torch.cuda.empty_cache()
 
     out["su3_mul_footprint"] = su3_sweep(L, F, flush, stream)
+    out["hmc_16x4"] = hmc_bench(L, F, stream)
 
     # uneven batch: 4 each of 8^4, 12^4, 16^4, 20^4, Haar links, m = 0.05, FP32-inner, one persistent launch per phase
     shapes = [(n_, n_, n_, n_) for n_ in (8, 12, 16, 20) for _ in range(4)]
@@ -750,6 +751,41 @@ def su3_sweep(L, F, flush, stream):
             del f
     torch.cuda.empty_cache()
     return rows
+
+
+def hmc_bench(L, F, stream):
+    """One HMC trajectory on 16^4: Wilson gauge action (beta 5.6) plus one Wilson
+    pseudofermion (m = 0.2), minimum-norm integrator, tau = 1 in 10 steps (21 force
+    evaluations), FP32-inner CG to 1e-10 on the full lattice for every force."""
+    import torch
+    from synthetic import config_seed, gauge_field, gaussian_spinor, make_rng, random_su3_algebra
+    dims, beta, mass = (16, 16, 16, 16), 5.6, 0.2
+    lat = L.lattice(dims, bc=BC)
+    op = L.operator(mass=mass)
+    U = gauge_field(dims, "exp", config_seed(50, 0), eps=0.3)
+    P = random_su3_algebra(make_rng(config_seed(50, 1)), U.size // 9).reshape(U.shape)
+    eta = gaussian_spinor(dims, config_seed(50, 2)) / np.sqrt(2.0)
+    prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=12, delta=DELTA[1], check_interval=64)
+    hp = L.hmc_params(beta, 1.0, 10, L.LQCD_MINNORM2, 1)
+    U0 = F.gauge_to_device(U, lat, 0, 18)
+    P0 = F.gauge_to_device(P, lat, 0, 18)
+    phid = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
+    L.lqcd_M(phid, F.spinor_to_device(eta, lat, 0, 2), U0, lat, op, L.LQCD_FULL, 1, None)  # phi = M^dag eta
+    Ud, Pd = torch.empty_like(U0), torch.empty_like(P0)
+    ws = F.empty(L.lqcd_hmc_workspace_bytes(lat, op, prm))
+
+    def traj():
+        Ud.copy_(U0)
+        Pd.copy_(P0)
+        return L.lqcd_hmc_trajectory(Ud, Pd, phid, lat, op, hp, prm, ws)
+
+    traj()
+    ms, info = _events_time(traj, stream)
+    # the synthetic start (links exp(0.3 i H)) is far from equilibrium at beta 5.6, so dH measures
+    # the integrator on large forces, not an acceptance rate
+    return {"ms_per_trajectory": round(ms, 2), "dH": info.H1 - info.H0, "H0": info.H0,
+            "force_evaluations": info.force_evaluations, "cg_iterations": info.cg_iterations,
+            "plaquette_action_share": round(info.gauge0 / info.H0, 4)}
 
 
 def run_reference(args, world, rank):

@@ -343,6 +343,70 @@ int lqcd_colour_matrix_unpack(double* dst_dev, const void* src_dev, int prec, co
 int lqcd_su3_mul(void* z_dev, const void* x_dev, const void* y_dev, const lqcd_lattice* lat, int prec,
                  void* stream);
 
+/* ---------------------------------------------------------------- gauge action and HMC */
+
+/* Wilson gauge action, its force and hybrid Monte Carlo (the paper lists HMC,
+ * the Wilson gauge action and the leapfrog and minimum-norm integrators among
+ * its algorithms, Sec. 4; the formulas are the textbook ones):
+ *   S_g = beta sum_{x, mu<nu} (1 - Re tr U_munu(x) / 3), periodic in every direction;
+ *   F_g = (beta / 3) traceless[(W - W^dag) / (2 i)], W = U_mu(x) times its staple sum,
+ *   so that dS_g = eps tr(T F_g) under U -> exp(i eps T) U (the convention of lqcd_force).
+ * Gauge and momentum fields are FP64 in the device layout with recon 18
+ * (lqcd_gauge_pack / _unpack); a momentum field holds one traceless Hermitian
+ * matrix per link. Calls that return a number reduce through a workspace of
+ * lqcd_reduce_workspace_bytes() bytes (256-byte aligned) and synchronise. */
+size_t lqcd_reduce_workspace_bytes(const lqcd_lattice* lat);
+/* Mean plaquette: the average of Re tr U_munu(x) / 3 over sites and the six planes. */
+int lqcd_plaquette(double* plaquette_host, const void* gauge_dev, const lqcd_lattice* lat,
+                   void* workspace_dev, size_t workspace_bytes, void* stream);
+/* Kinetic energy sum over links of tr(P^2) / 2. */
+int lqcd_momentum_kinetic(double* kinetic_host, const void* mom_dev, const lqcd_lattice* lat,
+                          void* workspace_dev, size_t workspace_bytes, void* stream);
+/* out_dev = F_g (must not alias gauge_dev). Asynchronous. */
+int lqcd_gauge_force(void* out_dev, const void* gauge_dev, const lqcd_lattice* lat, double beta, void* stream);
+/* U <- exp(i eps P) U for every link (FP64 Taylor series with scaling and squaring). Asynchronous. */
+int lqcd_gauge_exp_update(void* gauge_dev, const void* mom_dev, double eps, const lqcd_lattice* lat,
+                          void* stream);
+
+#define LQCD_LEAPFROG 0  /* P(eps/2) U(eps) P(eps) ... U(eps) P(eps/2) */
+#define LQCD_MINNORM2 1  /* per step P(l eps) U(eps/2) P((1-2l) eps) U(eps/2) P(l eps), l = 0.1931833 */
+
+typedef struct {
+    double beta;     /* Wilson gauge coupling */
+    double tau;      /* trajectory length; eps = tau / nsteps */
+    int nsteps;      /* molecular-dynamics steps (>= 1) */
+    int integrator;  /* LQCD_LEAPFROG or LQCD_MINNORM2 */
+    int fermion;     /* 1: add one Wilson pseudofermion S_f = phi^dag (M^dag M)^-1 phi */
+} lqcd_hmc_params;
+
+typedef struct {
+    double H0, H1;              /* Hamiltonian K + S_g + S_f before and after the trajectory */
+    double kinetic0, kinetic1;
+    double gauge0, gauge1;
+    double fermion0, fermion1;
+    int force_evaluations;      /* momentum steps: nsteps + 1 (leapfrog), 2 nsteps + 1 (min. norm) */
+    int cg_iterations;          /* summed over every solve of the trajectory */
+    int status;
+} lqcd_hmc_info;
+
+/* One molecular-dynamics trajectory of hybrid Monte Carlo: integrates
+ * dU/dt = i P U, dP/dt = -(F_g + F_f) over tau, updating gauge_dev and
+ * mom_dev in place, and reports H before and after. The caller draws the
+ * momenta (density exp(-tr P^2 / 2) on traceless Hermitian matrices) and the
+ * pseudofermion phi = M^dag eta (eta of density exp(-eta^dag eta)), and makes
+ * the accept / reject decision with exp(H0 - H1), keeping a copy of the gauge
+ * field to restore on rejection. op: Wilson, LQCD_F64, recon 18, n5 = 1;
+ * phi_dev: FP64 LQCD_FULL spinor (ignored without fermion). Every fermion
+ * force solves M^dag M X = phi on the full lattice with lqcd_cg_solve and
+ * params (sloppy_prec LQCD_F64 or LQCD_F32; the sloppy links are repacked
+ * from the updated field before each solve). Synchronises. */
+size_t lqcd_hmc_workspace_bytes(const lqcd_lattice* lat, const lqcd_operator* op,
+                                const lqcd_solver_params* params);
+int lqcd_hmc_trajectory(void* gauge_dev, void* mom_dev, const void* phi_dev, const lqcd_lattice* lat,
+                        const lqcd_operator* op, const lqcd_hmc_params* hmc,
+                        const lqcd_solver_params* params, lqcd_hmc_info* info,
+                        void* workspace_dev, size_t workspace_bytes, void* stream);
+
 /* ---------------------------------------------------------------- force */
 
 /* Pseudofermion force for S = phi^dag (M^dag M)^-1 phi with M = D_W (Grid

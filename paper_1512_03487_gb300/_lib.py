@@ -25,6 +25,7 @@ LQCD_F64, LQCD_F32, LQCD_F16 = 0, 1, 2
 LQCD_EVEN, LQCD_ODD, LQCD_FULL = 0, 1, 2
 LQCD_WILSON, LQCD_DWF = 0, 1
 LQCD_FORCE_TA, LQCD_FORCE_GRAD = 0, 1
+LQCD_LEAPFROG, LQCD_MINNORM2 = 0, 1
 
 
 class lqcd_lattice(C.Structure):
@@ -50,6 +51,17 @@ class lqcd_solve_info(C.Structure):
 class lqcd_batch_item(C.Structure):
     _fields_ = [("lat", lqcd_lattice), ("mass", C.c_double), ("gauge", C.c_void_p), ("gauge_sloppy", C.c_void_p),
                 ("x", C.c_void_p), ("b", C.c_void_p)]
+
+
+class lqcd_hmc_params(C.Structure):
+    _fields_ = [("beta", C.c_double), ("tau", C.c_double), ("nsteps", C.c_int), ("integrator", C.c_int),
+                ("fermion", C.c_int)]
+
+
+class lqcd_hmc_info(C.Structure):
+    _fields_ = [("H0", C.c_double), ("H1", C.c_double), ("kinetic0", C.c_double), ("kinetic1", C.c_double),
+                ("gauge0", C.c_double), ("gauge1", C.c_double), ("fermion0", C.c_double), ("fermion1", C.c_double),
+                ("force_evaluations", C.c_int), ("cg_iterations", C.c_int), ("status", C.c_int)]
 
 
 _P = C.c_void_p
@@ -88,6 +100,14 @@ SIGNATURES = {
     "lqcd_colour_matrix_pack": (_I, [_P, _I, _P, _LAT, _P]),
     "lqcd_colour_matrix_unpack": (_I, [_P, _P, _I, _LAT, _P]),
     "lqcd_su3_mul": (_I, [_P, _P, _P, _LAT, _I, _P]),
+    "lqcd_reduce_workspace_bytes": (_SZ, [_LAT]),
+    "lqcd_plaquette": (_I, [C.POINTER(C.c_double), _P, _LAT, _P, _SZ, _P]),
+    "lqcd_momentum_kinetic": (_I, [C.POINTER(C.c_double), _P, _LAT, _P, _SZ, _P]),
+    "lqcd_gauge_force": (_I, [_P, _P, _LAT, C.c_double, _P]),
+    "lqcd_gauge_exp_update": (_I, [_P, _P, C.c_double, _LAT, _P]),
+    "lqcd_hmc_workspace_bytes": (_SZ, [_LAT, _OP, _PRM]),
+    "lqcd_hmc_trajectory": (_I, [_P, _P, _P, _LAT, _OP, C.POINTER(lqcd_hmc_params), _PRM,
+                                 C.POINTER(lqcd_hmc_info), _P, _SZ, _P]),
     "lqcd_M_noalloc": (_I, [_P, _P, _P, _LAT, _OP, _I, _I, _P]),
     "lqcd_block_cg_workspace_bytes": (_SZ, [_LAT, _OP, _PRM]),
     "lqcd_block_cg_solve": (_I, [_P, _P, _P, _P, _LAT, _OP, _PRM, _INFO, _P, _SZ, _P]),

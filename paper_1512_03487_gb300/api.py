@@ -16,7 +16,8 @@ import numpy as np
 from . import _lib
 from ._lib import (  # noqa: F401  (re-exported constants and structs)
     LQCD_DWF, LQCD_EVEN, LQCD_F16, LQCD_F32, LQCD_F64, LQCD_FORCE_GRAD, LQCD_FORCE_TA, LQCD_FULL,
-    LQCD_ODD, LQCD_WILSON, lqcd_lattice, lqcd_operator, lqcd_solve_info, lqcd_solver_params,
+    LQCD_LEAPFROG, LQCD_MINNORM2, LQCD_ODD, LQCD_WILSON, lqcd_hmc_info, lqcd_hmc_params, lqcd_lattice,
+    lqcd_operator, lqcd_solve_info, lqcd_solver_params,
 )
 
 lib = _lib.load()
@@ -257,6 +258,53 @@ def lqcd_colour_matrix_unpack(dst, src, prec, lat, stream=None):
 
 def lqcd_su3_mul(z, x, y, lat, prec, stream=None):
     _check(lib.lqcd_su3_mul(_ptr(z), _ptr(x), _ptr(y), C.byref(lat), prec, _stream(stream)))
+
+
+def hmc_params(beta: float, tau: float, nsteps: int, integrator: int = LQCD_MINNORM2,
+               fermion: int = 1) -> lqcd_hmc_params:
+    return lqcd_hmc_params(beta=beta, tau=tau, nsteps=nsteps, integrator=integrator, fermion=fermion)
+
+
+def lqcd_reduce_workspace_bytes(lat) -> int:
+    return int(lib.lqcd_reduce_workspace_bytes(C.byref(lat)))
+
+
+def lqcd_plaquette(gauge, lat, workspace, stream=None) -> float:
+    out = C.c_double()
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(lib.lqcd_plaquette(C.byref(out), _ptr(gauge), C.byref(lat), _ptr(workspace), nbytes, _stream(stream)))
+    return out.value
+
+
+def lqcd_momentum_kinetic(mom, lat, workspace, stream=None) -> float:
+    out = C.c_double()
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(lib.lqcd_momentum_kinetic(C.byref(out), _ptr(mom), C.byref(lat), _ptr(workspace), nbytes,
+                                     _stream(stream)))
+    return out.value
+
+
+def lqcd_gauge_force(out, gauge, lat, beta, stream=None):
+    _check(lib.lqcd_gauge_force(_ptr(out), _ptr(gauge), C.byref(lat), float(beta), _stream(stream)))
+
+
+def lqcd_gauge_exp_update(gauge, mom, eps, lat, stream=None):
+    _check(lib.lqcd_gauge_exp_update(_ptr(gauge), _ptr(mom), float(eps), C.byref(lat), _stream(stream)))
+
+
+def lqcd_hmc_workspace_bytes(lat, op, params) -> int:
+    return int(lib.lqcd_hmc_workspace_bytes(C.byref(lat), C.byref(op), C.byref(params)))
+
+
+def lqcd_hmc_trajectory(gauge, mom, phi, lat, op, hmc, params, workspace, stream=None,
+                        raise_on_error=True) -> lqcd_hmc_info:
+    info = lqcd_hmc_info()
+    nbytes = workspace.numel() * workspace.element_size()
+    st = lib.lqcd_hmc_trajectory(_ptr(gauge), _ptr(mom), _ptr(phi), C.byref(lat), C.byref(op), C.byref(hmc),
+                                 C.byref(params), C.byref(info), _ptr(workspace), nbytes, _stream(stream))
+    if raise_on_error:
+        _check(st)
+    return info
 
 
 def lqcd_force(out, gauge, X, Y, lat, op, kind, stream=None):

@@ -26,6 +26,8 @@ struct ForceArgs {
   Geom g;
   int64_t half_bytes;
   int kind;
+  int accumulate;  // 1: out -= coef * force (molecular-dynamics momentum update)
+  double coef;
 };
 
 // M = sum_a g_a h_a^dag (colour outer products of two half spinors)
@@ -94,8 +96,16 @@ __device__ __forceinline__ void force_dir(const ForceArgs& a, const Coord& x, in
     out[8].r -= tr;
   }
   double2* o = a.out + (int64_t)(parity * 4 + MU) * 9 * a.g.gstride + cb;
+  if (a.accumulate) {
 #pragma unroll
-  for (int k = 0; k < 9; k++) o[k * a.g.gstride] = make_double2(out[k].r, out[k].i);
+    for (int k = 0; k < 9; k++) {
+      const double2 w = o[k * a.g.gstride];
+      o[k * a.g.gstride] = make_double2(w.x - a.coef * out[k].r, w.y - a.coef * out[k].i);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 9; k++) o[k * a.g.gstride] = make_double2(out[k].r, out[k].i);
+  }
 }
 
 template <int R>
@@ -114,6 +124,19 @@ __global__ void __launch_bounds__(FORCE_BLOCK) force_kernel(const ForceArgs a) {
   force_dir<3, R>(a, x, cb, parity, xs, ys);
 }
 
+static int launch_force(const ForceArgs& a, int recon, cudaStream_t s) {
+  const unsigned grid = (unsigned)((2 * (int64_t)a.g.Vh + FORCE_BLOCK - 1) / FORCE_BLOCK);
+  if (recon == 18) force_kernel<18><<<grid, FORCE_BLOCK, 0, s>>>(a);
+  else force_kernel<12><<<grid, FORCE_BLOCK, 0, s>>>(a);
+  return after_launch("force_kernel");
+}
+
+int force_accumulate(double2* mom, const void* gauge, const void* X, const void* Y, const Geom& g, int recon,
+                     double coef, cudaStream_t s) {
+  ForceArgs a{mom, gauge, X, Y, g, (int64_t)cb_spinor_bytes(g, LQCD_F64), LQCD_FORCE_TA, 1, coef};
+  return launch_force(a, recon, s);
+}
+
 }  // namespace lqcd
 
 using namespace lqcd;
@@ -129,10 +152,6 @@ extern "C" int lqcd_force(void* out, const void* gauge, const void* X, const voi
   if (kind != LQCD_FORCE_TA && kind != LQCD_FORCE_GRAD) return fail(LQCD_ERR_ARG, "lqcd_force: bad kind %d", kind);
   if (!out || !gauge || !X || !Y || (((uintptr_t)out | (uintptr_t)gauge | (uintptr_t)X | (uintptr_t)Y) & 15))
     return fail(LQCD_ERR_ARG, "lqcd_force: null or misaligned pointer");
-  ForceArgs a{static_cast<double2*>(out), gauge, X, Y, g, (int64_t)cb_spinor_bytes(g, LQCD_F64), kind};
-  const unsigned grid = (unsigned)((2 * (int64_t)g.Vh + FORCE_BLOCK - 1) / FORCE_BLOCK);
-  cudaStream_t s = (cudaStream_t)stream;
-  if (op->recon == 18) force_kernel<18><<<grid, FORCE_BLOCK, 0, s>>>(a);
-  else force_kernel<12><<<grid, FORCE_BLOCK, 0, s>>>(a);
-  return after_launch("force_kernel");
+  ForceArgs a{static_cast<double2*>(out), gauge, X, Y, g, (int64_t)cb_spinor_bytes(g, LQCD_F64), kind, 0, 0.0};
+  return launch_force(a, op->recon, (cudaStream_t)stream);
 }

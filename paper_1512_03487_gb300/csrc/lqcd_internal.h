@@ -54,6 +54,11 @@ size_t op_tmp_bytes(const Geom& g, int kind, int prec, int subset);
 size_t field_bytes(const Geom& g, int prec, int subset);
 int check_operator(const lqcd_operator* op, const Geom& g);
 
+// ---- fermion force accumulated into a momentum field: mom -= coef * F (traceless
+// Hermitian force of lqcd_force, kind LQCD_FORCE_TA); FP64 fields, gauge in recon.
+int force_accumulate(double2* mom, const void* gauge, const void* X, const void* Y, const Geom& g, int recon,
+                     double coef, cudaStream_t s);
+
 // Host pointer offset helper.
 inline void* off(void* p, size_t bytes) { return static_cast<char*>(p) + bytes; }
 inline const void* off(const void* p, size_t bytes) { return static_cast<const char*>(p) + bytes; }
