@@ -133,3 +133,38 @@ def test_gauge_force_mutations_are_caught(monkeypatch, mutation):
         orig = gauge.force
         monkeypatch.setattr(gauge, "force", lambda U, beta: orig(U, beta / 2))
     assert _gauge_fd_error(gauge) > 1e-3
+
+
+def _gparity_doubled_error(gp):
+    dims, bc, mu_g = (2, 4, 2, 4), (1.0, 1.0, 1.0, -1.0), 1
+    U = gauge_field(dims, "haar", 1801)
+    psi2 = gaussian_spinor(dims, 1802, lead=(2,))
+    out = gp.dirac(U, psi2, 0.1, bc, (mu_g,))
+    ax = 3 - mu_g
+    ref = wilson.dirac(np.concatenate([U, np.conj(U)], axis=ax), np.concatenate([psi2[0], psi2[1]], axis=ax), 0.1,
+                       (1.0, -1.0, 1.0, -1.0))
+    return np.abs(np.concatenate([out[0], out[1]], axis=ax) - ref).max()
+
+
+@pytest.mark.parametrize("mutation", ["twist_sign", "backward_link_owner", "no_conjugate_links"])
+def test_gparity_mutations_are_caught(monkeypatch, mutation):
+    from oracle import gparity
+    assert _gparity_doubled_error(gparity) < 1e-12
+    if mutation == "twist_sign":
+        orig = gparity._neighbour
+
+        def flipped(psi2, mu, sign, bc, twisted):
+            out = orig(psi2, mu, sign, bc, twisted)
+            if twisted:
+                ax = wilson.site_axis(mu)
+                edge = [slice(None)] * psi2.ndim
+                edge[psi2.ndim + ax] = psi2.shape[ax] - 1 if sign > 0 else 0
+                out[tuple(edge)] *= -1
+            return out
+        monkeypatch.setattr(gparity, "_neighbour", flipped)
+    elif mutation == "backward_link_owner":
+        orig = gparity._backward_links
+        monkeypatch.setattr(gparity, "_backward_links", lambda U, mu, twisted: orig(U, mu, False))
+    elif mutation == "no_conjugate_links":
+        monkeypatch.setattr(gparity, "_flavour_links", lambda u: np.stack([u, u]))
+    assert _gparity_doubled_error(gparity) > 1e-3
