@@ -621,6 +621,7 @@ def run_extras(L, F, flush, stream):
     del g64, gsl, be, x, ws, wsb
     torch.cuda.empty_cache()
 
+    out["gparity_16x3x32_xy_mixed_fp32"] = gparity_bench(L, F, flush, stream)
     out["su3_mul_footprint"] = su3_sweep(L, F, flush, stream)
     out["hmc_16x4"] = hmc_bench(L, F, stream)
 
@@ -751,6 +752,65 @@ def su3_sweep(L, F, flush, stream):
             del f
     torch.cuda.empty_cache()
     return rows
+
+
+def gparity_bench(L, F, flush, stream):
+    """Even-odd Wilson CG with G-parity boundary conditions in x and y (two flavours as
+    n5 = 2), 16^3 x 32, Haar links, m = 0.05, FP32 / 12-real inner, delta 1e-5, to 1e-10;
+    plus the cold-L2 G-parity hop (8 links read once for both flavours)."""
+    import torch
+    from synthetic import config_seed, gauge_field, gaussian_spinor
+    dims, m, mask = (16, 16, 16, 32), 0.05, 3
+    lat = L.lattice(dims, n5=2, bc=BC)
+    op = L.operator(mass=m, gparity=mask)
+    U = gauge_field(dims, "haar", config_seed(60, 0))
+    g64 = F.gauge_to_device(U, lat, 0, 18)
+    g32 = F.gauge_to_device(U, lat, 1, 12)
+    bd = F.spinor_to_device(gaussian_spinor(dims, config_seed(60, 1), lead=(2,)), lat, 0, 2)
+    del U
+    tmp = F.empty(L.lqcd_operator_workspace_bytes(lat, op, 0))
+    bhat = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
+    src = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
+    x = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
+    prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=12, delta=DELTA[1], check_interval=64)
+    ws = F.empty(L.lqcd_cg_workspace_bytes(lat, op, prm, 0))
+
+    def solve():
+        L.lqcd_eo_prepare(bhat, bd, g64, lat, op, tmp)
+        L.lqcd_M(src, bhat, g64, lat, op, L.LQCD_EVEN, 1, tmp)
+        info = L.lqcd_cg_solve(x, src, g64, g32, lat, op, prm, L.LQCD_EVEN, ws)
+        L.lqcd_eo_reconstruct(x, bd, g64, lat, op, tmp)
+        return info
+
+    solve()
+    ms, info = _events_time(solve, stream, flush)
+    dx = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
+    L.lqcd_M(dx, x, g64, lat, op, L.LQCD_FULL, 0, None)
+    n = 2 * int(np.prod(dims)) * 24
+    a = torch.empty(n, dtype=torch.float64, device="cuda")
+    bb = torch.empty(n, dtype=torch.float64, device="cuda")
+    L.lqcd_spinor_unpack(a, dx, 0, 2, lat)
+    L.lqcd_spinor_unpack(bb, bd, 0, 2, lat)
+    res = float(torch.linalg.vector_norm(a - bb) / torch.linalg.vector_norm(bb))
+    vh = int(np.prod(dims)) // 2
+    hops = 1 + 2 + 4 * (info.iterations + info.reliable_updates) + 1
+    opg = L.operator(prec=1, recon=12, gparity=mask)
+    fin = F.empty(L.lqcd_spinor_bytes(lat, 1, L.LQCD_ODD))
+    fin.zero_()
+    out = F.empty(L.lqcd_spinor_bytes(lat, 1, L.LQCD_EVEN))
+    for _ in range(2):
+        L.lqcd_dslash(out, fin, g32, lat, opg, L.LQCD_EVEN, 0)
+    ts = [_events_time(lambda: L.lqcd_dslash(out, fin, g32, lat, opg, L.LQCD_EVEN, 0), stream, flush)[0]
+          for _ in range(10)]
+    t = float(np.mean(ts)) * 1e-3
+    bps = 8 * 48 / 2 + 96 + 96
+    peak, _ = measured_peak()
+    return {"ms": round(ms, 3), "iterations": info.iterations, "reliable_updates": info.reliable_updates,
+            "full_system_rel_residual": res,
+            "dslash_gflops_in_solve": round(hops * FLOP_PER_SITE * vh * 2 / (ms * 1e-3) / 1e9, 1),
+            "hop_f32r12_gparity": {"launch_us": round(t * 1e6, 2), "algorithmic_bytes_per_site": bps,
+                                   "achieved_gbs": round(bps * vh * 2 / t / 1e9, 1),
+                                   "frac_of_measured_hbm": round(bps * vh * 2 / t / 1e9 / peak, 4)}}
 
 
 def hmc_bench(L, F, stream):

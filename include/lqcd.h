@@ -94,7 +94,15 @@ typedef struct {
 } lqcd_lattice;
 
 /* Operator parameters. Wilson: D_W = (4 + mass) - H/2. Domain wall (Shamir):
- * D_DW = (5 - M5) - P_- S_up - P_+ S_down - H/2 with mf corners. */
+ * D_DW = (5 - M5) - P_- S_up - P_+ S_down - H/2 with mf corners.
+ * G-parity (the paper lists G-parity boundary conditions, Sec. 4): with
+ * gparity != 0 (Wilson only, n5 = 2 flavours, LQCD_F64 or LQCD_F32) the field
+ * holds Psi = (Psi_0, Psi_1) as i5 = 0, 1; flavour 1 couples to the conjugate
+ * links U*, and a hop across the boundary of a direction in the mask maps
+ * Psi_0 -> +Psi_1, Psi_1 -> -Psi_0 in place of that direction's phase; the
+ * forward link belongs to the site, the backward link to its neighbour (whose
+ * flavour decides the conjugation). The solvers treat the two flavours as
+ * one system. */
 typedef struct {
     int kind;        /* LQCD_WILSON or LQCD_DWF */
     double mass;     /* Wilson bare mass m */
@@ -102,6 +110,7 @@ typedef struct {
     double mf;       /* domain-wall quark mass */
     int prec;        /* storage precision of the gauge field and spinors */
     int recon;       /* 18 or 12 reals per stored link */
+    int gparity;     /* bit mask of G-parity directions: 1 x, 2 y, 4 z, 8 t; 0 = none */
 } lqcd_operator;
 
 typedef struct {

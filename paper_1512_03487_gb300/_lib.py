@@ -34,7 +34,7 @@ class lqcd_lattice(C.Structure):
 
 class lqcd_operator(C.Structure):
     _fields_ = [("kind", C.c_int), ("mass", C.c_double), ("M5", C.c_double), ("mf", C.c_double),
-                ("prec", C.c_int), ("recon", C.c_int)]
+                ("prec", C.c_int), ("recon", C.c_int), ("gparity", C.c_int)]
 
 
 class lqcd_solver_params(C.Structure):

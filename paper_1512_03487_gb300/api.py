@@ -65,8 +65,8 @@ def lattice(dims: Sequence[int], n5: int = 1, bc: Sequence[float] = (1.0, 1.0, 1
 
 
 def operator(kind: int = LQCD_WILSON, mass: float = 0.0, M5: float = 1.8, mf: float = 0.02,
-             prec: int = LQCD_F64, recon: int = 18) -> lqcd_operator:
-    return lqcd_operator(kind=kind, mass=mass, M5=M5, mf=mf, prec=prec, recon=recon)
+             prec: int = LQCD_F64, recon: int = 18, gparity: int = 0) -> lqcd_operator:
+    return lqcd_operator(kind=kind, mass=mass, M5=M5, mf=mf, prec=prec, recon=recon, gparity=gparity)
 
 
 def solver_params(tol: float = 1e-10, maxiter: int = 10000, sloppy_prec: int = LQCD_F64,

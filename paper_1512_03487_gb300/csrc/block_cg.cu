@@ -567,7 +567,8 @@ static int block_validate(const lqcd_lattice* lat, const lqcd_operator* op, cons
   if (st) return st;
   if ((st = check_operator(op, *g))) return st;
   if (!p) return fail(LQCD_ERR_ARG, "block cg: null params");
-  if (op->kind != LQCD_WILSON) return fail(LQCD_ERR_UNSUPPORTED, "block cg: Wilson operator only");
+  if (op->kind != LQCD_WILSON || op->gparity)
+    return fail(LQCD_ERR_UNSUPPORTED, "block cg: Wilson operator without G-parity only");
   if (op->prec != LQCD_F64) return fail(LQCD_ERR_ARG, "block cg: x, b and gauge must be LQCD_F64 (op->prec)");
   if (g->n5 > BMAX) return fail(LQCD_ERR_ARG, "block cg: %d right-hand sides exceed %d", g->n5, BMAX);
   if (p->sloppy_prec != LQCD_F64 && p->sloppy_prec != LQCD_F32 && p->sloppy_prec != LQCD_F16)

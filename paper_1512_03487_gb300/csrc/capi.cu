@@ -77,6 +77,7 @@ int make_geom(const lqcd_lattice* lat, Geom* g) {
   g->st[1] = g->X;
   g->st[2] = g->X * g->Y;
   g->st[3] = g->X * g->Y * g->Z;
+  g->gp = 0;
   return LQCD_OK;
 }
 
@@ -85,7 +86,7 @@ size_t field_bytes(const Geom& g, int prec, int subset) {
   return subset == LQCD_FULL ? 2 * cb : cb;
 }
 
-int check_operator(const lqcd_operator* op, const Geom& g) {
+int check_operator(const lqcd_operator* op, Geom& g) {
   if (!op) return fail(LQCD_ERR_ARG, "null operator");
   if (op->kind != LQCD_WILSON && op->kind != LQCD_DWF) return fail(LQCD_ERR_ARG, "bad operator kind %d", op->kind);
   if (op->prec != LQCD_F64 && op->prec != LQCD_F32 && op->prec != LQCD_F16)
@@ -98,6 +99,13 @@ int check_operator(const lqcd_operator* op, const Geom& g) {
   } else if (g.n5 > MAX_SYS) {
     return fail(LQCD_ERR_ARG, "n5 = %d right-hand sides exceed %d", g.n5, MAX_SYS);
   }
+  if (op->gparity < 0 || op->gparity > 15) return fail(LQCD_ERR_ARG, "bad G-parity mask %d", op->gparity);
+  if (op->gparity) {
+    if (op->kind != LQCD_WILSON || g.n5 != 2)
+      return fail(LQCD_ERR_ARG, "G-parity needs the Wilson operator and n5 = 2 flavours");
+    if (op->prec == LQCD_F16) return fail(LQCD_ERR_UNSUPPORTED, "G-parity with LQCD_F16 storage");
+  }
+  g.gp = op->gparity;
   return LQCD_OK;
 }
 

@@ -177,6 +177,7 @@ static int validate(const lqcd_lattice* lat, const lqcd_operator* op, const lqcd
   if (p->sloppy_prec != LQCD_F64 && p->sloppy_prec != LQCD_F32 && p->sloppy_prec != LQCD_F16)
     return fail(LQCD_ERR_ARG, "cg: bad sloppy precision %d", p->sloppy_prec);
   if (p->sloppy_recon != 18 && p->sloppy_recon != 12) return fail(LQCD_ERR_ARG, "cg: bad sloppy recon");
+  if (op->gparity && p->sloppy_prec == LQCD_F16) return fail(LQCD_ERR_UNSUPPORTED, "cg: G-parity with FP16 inner");
   if (!(p->tol > 0.0) || p->maxiter < 1) return fail(LQCD_ERR_ARG, "cg: tol must be > 0 and maxiter >= 1");
   if (p->delta < 0.0 || p->delta >= 1.0) return fail(LQCD_ERR_ARG, "cg: delta must be in [0, 1)");
   if (subset != LQCD_EVEN && subset != LQCD_FULL) return fail(LQCD_ERR_ARG, "cg: subset must be EVEN or FULL");
@@ -268,7 +269,7 @@ size_t lqcd_cg_workspace_bytes(const lqcd_lattice* lat, const lqcd_operator* op,
                                int subset) {
   Geom g;
   if (validate(lat, op, p, subset, &g)) return 0;
-  const int nsys = op->kind == LQCD_WILSON ? g.n5 : 1;
+  const int nsys = op->kind == LQCD_WILSON && !op->gparity ? g.n5 : 1;  // G-parity flavours form one system
   return carve(nullptr, g, *op, *p, subset, nsys).total;
 }
 
@@ -295,7 +296,7 @@ int lqcd_cg_solve(void* x, const void* b, const void* gauge, const void* gauge_s
   S.prm = *prm;
   if (S.prm.check_interval <= 0) S.prm.check_interval = 16;
   S.subset = subset;
-  S.nsys = op->kind == LQCD_WILSON ? S.g.n5 : 1;
+  S.nsys = op->kind == LQCD_WILSON && !op->gparity ? S.g.n5 : 1;  // G-parity flavours form one system
   S.w = carve(workspace, S.g, *op, *prm, subset, S.nsys);
   if (workspace_bytes < S.w.total)
     return finish(fail(LQCD_ERR_WORKSPACE, "cg: workspace %zu < %zu bytes", workspace_bytes, S.w.total));
@@ -368,6 +369,7 @@ int lqcd_cg_solve(void* x, const void* b, const void* gauge, const void* gauge_s
   key_append(key, op->M5);
   key_append(key, op->mf);
   key_append(key, op->recon);
+  key_append(key, op->gparity);
   key_append(key, prm->sloppy_prec);
   key_append(key, prm->sloppy_recon);
   key_append(key, S.prm.check_interval);

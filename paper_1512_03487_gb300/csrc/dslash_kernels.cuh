@@ -187,7 +187,17 @@ __device__ __forceinline__ typename PrecTraits<P>::real load_project(const void*
   return wrap ? bc_phase<T>(g, MU) * f : f;
 }
 
-template <int MU, int P, int R, bool DAG>
+template <typename T> __device__ __forceinline__ void conj_link(Link<T>& u) {
+#pragma unroll
+  for (int k = 0; k < 9; k++) u.v[k].i = -u.v[k].i;
+}
+
+// Both hops along mu. With GP (G-parity, n5 = 2 flavours i5 = f): a hop that
+// wraps in a direction of g.gp reads the other flavour with sign +1 / -1
+// (forward, f = 0 / 1) or -1 / +1 (backward) instead of the boundary phase,
+// and the link is conjugated when its owner -- the site for the forward hop,
+// the neighbour (flavour f') for the backward hop -- is flavour 1.
+template <int MU, int P, int R, bool DAG, bool GP = false>
 __device__ __forceinline__ void hop_dir(Spinor<typename PrecTraits<P>::real>& acc, const Geom& g,
                                         const void* gauge, const Coord& x, int64_t cb, int64_t i5,
                                         int parity, const void* in) {
@@ -197,10 +207,18 @@ __device__ __forceinline__ void hop_dir(Spinor<typename PrecTraits<P>::real>& ac
   {
     bool wrap;
     const int64_t nb = neighbour_cb<MU>(g, x, +1, wrap);
+    int64_t f_nb = i5;
+    T sgn = T(1);
+    if (GP && wrap && ((g.gp >> MU) & 1)) {
+      f_nb = 1 - i5;
+      sgn = i5 == 0 ? T(1) : T(-1);
+      wrap = false;  // the twist replaces the boundary phase
+    }
     Half<T> h;
-    const T f = load_project<P, MU, SF>(in, g, nb * n5 + i5, wrap, h);
+    const T f = sgn * load_project<P, MU, SF>(in, g, nb * n5 + f_nb, wrap, h);
     Link<T> u;
     LinkIO<P, R>::load(gauge, g.gstride, parity * 4 + MU, cb, u);
+    if (GP && i5 == 1) conj_link(u);
     Half<T> w;
     link_mul(u, h, w);
     accumulate_scaled<MU, SF>(acc, w, f);
@@ -208,10 +226,18 @@ __device__ __forceinline__ void hop_dir(Spinor<typename PrecTraits<P>::real>& ac
   {
     bool wrap;
     const int64_t nb = neighbour_cb<MU>(g, x, -1, wrap);
+    int64_t f_nb = i5;
+    T sgn = T(1);
+    if (GP && wrap && ((g.gp >> MU) & 1)) {
+      f_nb = 1 - i5;
+      sgn = i5 == 0 ? T(-1) : T(1);
+      wrap = false;
+    }
     Half<T> h;
-    const T f = load_project<P, MU, -SF>(in, g, nb * n5 + i5, wrap, h);
+    const T f = sgn * load_project<P, MU, -SF>(in, g, nb * n5 + f_nb, wrap, h);
     Link<T> u;
     LinkIO<P, R>::load(gauge, g.gstride, (1 - parity) * 4 + MU, nb, u);
+    if (GP && f_nb == 1) conj_link(u);
     Half<T> w;
     link_mul_dag(u, h, w);
     accumulate_scaled<MU, -SF>(acc, w, f);
@@ -235,7 +261,7 @@ struct EpiCoef {
 };
 
 // The result at output site j (= cb * n5 + i5) of checkerboard `parity`.
-template <int P, int R, bool DAG, int EPI>
+template <int P, int R, bool DAG, int EPI, bool GP = false>
 __device__ __forceinline__ void hop_site(const Geom& g, const void* gauge, const void* in, const void* xb,
                                          int parity, int64_t j, const EpiCoef& c,
                                          Spinor<typename PrecTraits<P>::real>& res) {
@@ -253,10 +279,10 @@ __device__ __forceinline__ void hop_site(const Geom& g, const void* gauge, const
   const Coord x = cb_to_coord(g, cb, parity);
   Spinor<T> acc;
   zero(acc);
-  hop_dir<0, P, R, DAG>(acc, g, gauge, x, cb, i5, parity, in);
-  hop_dir<1, P, R, DAG>(acc, g, gauge, x, cb, i5, parity, in);
-  hop_dir<2, P, R, DAG>(acc, g, gauge, x, cb, i5, parity, in);
-  hop_dir<3, P, R, DAG>(acc, g, gauge, x, cb, i5, parity, in);
+  hop_dir<0, P, R, DAG, GP>(acc, g, gauge, x, cb, i5, parity, in);
+  hop_dir<1, P, R, DAG, GP>(acc, g, gauge, x, cb, i5, parity, in);
+  hop_dir<2, P, R, DAG, GP>(acc, g, gauge, x, cb, i5, parity, in);
+  hop_dir<3, P, R, DAG, GP>(acc, g, gauge, x, cb, i5, parity, in);
   const T b = (T)c.b;
   if (EPI == EPI_PLAIN) {
 #pragma unroll
@@ -299,7 +325,7 @@ template <typename T> __device__ __forceinline__ double norm2_site(const Spinor<
   return (double)s;
 }
 
-template <int P, int R, bool DAG, int EPI, int RED, int BLOCK>
+template <int P, int R, bool DAG, int EPI, int RED, int BLOCK, bool GP = false>
 __global__ void __launch_bounds__(BLOCK) hop_kernel(const HopArgs A) {
   using T = typename PrecTraits<P>::real;
   if (gate_closed(A.gate)) return;
@@ -317,7 +343,7 @@ __global__ void __launch_bounds__(BLOCK) hop_kernel(const HopArgs A) {
   if (j < A.g.nsites) {
     Spinor<T> res;
     const EpiCoef c{A.a, A.b, A.m5d, A.mf};
-    hop_site<P, R, DAG, EPI>(A.g, A.gauge, in, xb, parity, j, c, res);
+    hop_site<P, R, DAG, EPI, GP>(A.g, A.gauge, in, xb, parity, j, c, res);
     if (RED == RED_CG_UPDATE) {
       const int64_t ps = A.full ? parity * A.half_bytes : 0, vs = A.full ? parity * A.upd_half_bytes : 0;
       red = update_site_ap<vec_prec(P), P>(A.g, j, A.red.sys[sys_of(j, A.red.nsys)].alpha,

@@ -57,6 +57,7 @@ struct Geom {
   int st[4];        // lexicographic strides 1, X, X Y, X Y Z (4D volume < 2^31)
   float bcf[4];
   double bcd[4];
+  int gp;           // G-parity direction mask of the operator (0: none); n5 = 2 flavours then
 };
 
 int make_geom(const lqcd_lattice* lat, Geom* g);  // validates, LQCD_OK or LQCD_ERR_ARG

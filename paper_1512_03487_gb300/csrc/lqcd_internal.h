@@ -11,6 +11,7 @@ int launch_hop(int prec, int recon, bool dagger, int epi, int reduce, HopArgs a,
 int launch_hop_f64(int recon, bool dagger, int epi, int reduce, HopArgs a, cudaStream_t s);
 int launch_hop_f32(int recon, bool dagger, int epi, int reduce, HopArgs a, cudaStream_t s);
 int launch_hop_f16(int recon, bool dagger, int epi, int reduce, HopArgs a, cudaStream_t s);
+int launch_hop_gparity(int prec, int recon, bool dagger, int epi, int reduce, HopArgs a, cudaStream_t s);
 
 // Blocks of the hop kernel per checkerboard (the reduction buffers are sized from it).
 constexpr int HOP_BLOCK = 128;
@@ -52,7 +53,8 @@ int op_apply(const OpCtx& c, void* out, const void* in, int subset, int dagger,
 size_t op_tmp_bytes(const Geom& g, int kind, int prec, int subset);
 // Bytes of a field of the given subset.
 size_t field_bytes(const Geom& g, int prec, int subset);
-int check_operator(const lqcd_operator* op, const Geom& g);
+// Validates op against g and records the operator's G-parity mask in g.gp.
+int check_operator(const lqcd_operator* op, Geom& g);
 
 // ---- fermion force accumulated into a momentum field: mom -= coef * F (traceless
 // Hermitian force of lqcd_force, kind LQCD_FORCE_TA); FP64 fields, gauge in recon.

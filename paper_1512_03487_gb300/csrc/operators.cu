@@ -9,6 +9,7 @@
 namespace lqcd {
 
 int launch_hop(int prec, int recon, bool dagger, int epi, int reduce, HopArgs a, cudaStream_t s) {
+  if (a.g.gp) return launch_hop_gparity(prec, recon, dagger, epi, reduce, a, s);
   switch (prec) {
     case LQCD_F64: return launch_hop_f64(recon, dagger, epi, reduce, a, s);
     case LQCD_F32: return launch_hop_f32(recon, dagger, epi, reduce, a, s);

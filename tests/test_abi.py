@@ -127,3 +127,16 @@ def test_colour_matrix_sizes_and_rejections(api):
         with pytest.raises(api.LqcdError) as ei:
             api.lqcd_su3_mul(z, x, y, lat, prec, stream=0)
         assert ei.value.status == -1
+
+
+def test_gparity_rejected_on_host(api):
+    lat1 = api.lattice((4, 4, 4, 4), n5=1)
+    lat2 = api.lattice((4, 4, 4, 4), n5=2)
+    buf = 4096
+    for lat, op in ((lat1, api.operator(gparity=1)),            # n5 must be 2 flavours
+                    (lat2, api.operator(prec=2, gparity=1)),    # FP16 storage
+                    (lat2, api.operator(kind=1, gparity=1)),    # domain wall
+                    (lat2, api.operator(gparity=16))):          # mask beyond t
+        with pytest.raises(api.LqcdError) as ei:
+            api.lqcd_dslash(buf, buf + 8192, buf + 16384, lat, op, api.LQCD_EVEN, 0, stream=0)
+        assert ei.value.status in (-1, -6)
