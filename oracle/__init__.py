@@ -1,7 +1,8 @@
 """Plain, slow FP64 CPU oracle for the Wilson / domain-wall Dirac operators,
 the even-odd Schur complement, conjugate gradient, the fermion force, the
 SU(3) x SU(3) field product, the Wilson gauge action with its force, the
-HMC molecular-dynamics trajectory and the G-parity Wilson operator.
+HMC molecular-dynamics trajectory, the G-parity Wilson operator and the
+multigrid aggregation and coarse-grid operator.
 
 TEST INFRASTRUCTURE ONLY. Nothing in the library imports this package; only
 the test suite, the smoke check and the CPU-baseline / reference leg of the
@@ -18,4 +19,4 @@ convention chosen where the paper is silent, and each function is pinned by a
 test against a closed form, an identity or brute force; see the module
 headers. No function here is "parity unpinned".
 """
-from . import gamma, wilson, dwf, cg, force, su3, gauge, hmc, gparity  # noqa: F401
+from . import gamma, wilson, dwf, cg, force, su3, gauge, hmc, gparity, mg  # noqa: F401

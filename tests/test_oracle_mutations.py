@@ -168,3 +168,39 @@ def test_gparity_mutations_are_caught(monkeypatch, mutation):
     elif mutation == "no_conjugate_links":
         monkeypatch.setattr(gparity, "_flavour_links", lambda u: np.stack([u, u]))
     assert _gparity_doubled_error(gparity) > 1e-3
+
+
+def _galerkin_error(mg_mod):
+    from tests.test_oracle_mg import _coarse_random, _dense_prolongator
+    dims, b, nv, m = (4, 2, 2, 4), 2, 2, 0.1
+    U = gauge_field(dims, "haar", 2011)
+    P = mg_mod.orthonormalize(gaussian_spinor(dims, 2012, lead=(nv,)), b)
+    Y = mg_mod.coarse_operator(U, m, BC_AP, P, b)
+    Pm = _dense_prolongator(P, dims, b)
+    Dc = Pm.conj().T @ wilson_dense(U, dims, m, BC_AP) @ Pm
+    c = _coarse_random(mg_mod.coarse_dims(dims, b), 2 * nv, 2013)
+    return np.abs(mg_mod.coarse_apply(Y, c).reshape(-1) - Dc @ c.reshape(-1)).max()
+
+
+@pytest.mark.parametrize("mutation", ["no_boundary_phase", "backward_link_unshifted"])
+def test_coarse_operator_mutations_are_caught(monkeypatch, mutation):
+    from oracle import mg
+    assert _galerkin_error(mg) < 1e-11
+    if mutation == "no_boundary_phase":
+        orig = mg.wilson.shift
+        monkeypatch.setattr(mg.wilson, "shift", lambda f, mu, sign, bc: orig(f, mu, sign, (1, 1, 1, 1)))
+    elif mutation == "backward_link_unshifted":
+        orig_roll = mg.np.roll
+        monkeypatch.setattr(mg.np, "roll", lambda a, s, axis=None: a if a.ndim == 6 else orig_roll(a, s, axis=axis))
+    assert _galerkin_error(mg) > 1e-3
+
+
+def test_mixed_chirality_aggregation_is_caught(monkeypatch):
+    """Aggregates that mix chiralities still give a Galerkin operator, but lose
+    gamma_5-hermiticity: the gamma_5 pin catches that reading error."""
+    from oracle import mg
+    from tests.test_oracle_mg import test_coarse_gamma5_hermiticity
+    test_coarse_gamma5_hermiticity()
+    monkeypatch.setattr(mg, "CHIRAL_SPINS", ((0, 2), (1, 3)))
+    with pytest.raises(AssertionError):
+        test_coarse_gamma5_hermiticity()
