@@ -416,6 +416,67 @@ int lqcd_hmc_trajectory(void* gauge_dev, void* mom_dev, const void* phi_dev, con
                         const lqcd_solver_params* params, lqcd_hmc_info* info,
                         void* workspace_dev, size_t workspace_bytes, void* stream);
 
+/* ---------------------------------------------------------------- multigrid */
+
+/* Two-level adaptive multigrid for the Wilson operator (the paper shows the
+ * coarse-grid operator of an adaptive multigrid inverter as its stencil
+ * example, Sec. 2, and lists multigrid-preconditioned solvers, Sec. 4).
+ * Aggregates are blocks of block^4 fine sites (block 2 or 4, dividing every
+ * extent) split by chirality (spins 0, 1 / 2, 3); a coarse site carries
+ * Nc = 2 nvec complex components ordered (chirality, k). Fine vector sets:
+ * nvec full-lattice spinors (n5 = 1) in the device layout at consecutive
+ * field offsets. Coarse vectors: [coarse site][Nc] complex (FP64 double2 or
+ * FP32 float2), coarse sites lexicographic with x fastest. Coarse operator:
+ * [9][coarse site][Nc][Nc], d = 0 self, 1 + 2 mu the +mu and 2 + 2 mu the -mu
+ * neighbour, with (D_c c)(X) = sum_d Y_d(X) c(X + d). All calls asynchronous
+ * except lqcd_mg_solve. */
+typedef struct {
+    int block;         /* aggregate extent in every direction: 2 or 4 */
+    int nvec;          /* near-null vectors, 1..32 */
+    int setup_iters;   /* CG iterations on M^dag M v = random, per vector */
+    int pre_smooth;    /* MR steps before the coarse correction */
+    int post_smooth;   /* MR steps after it */
+    int coarse_iters;  /* fixed CGNR iterations of the coarse solve */
+    int restart;       /* flexible-GCR restart length (>= 4) */
+} lqcd_mg_params;
+
+size_t lqcd_mg_coarse_bytes(const lqcd_lattice* lat, int nvec, int block, int prec);
+size_t lqcd_mg_coarse_op_bytes(const lqcd_lattice* lat, int nvec, int block, int prec);
+/* In place: per aggregate and chirality, modified Gram-Schmidt of the nvec FP64 vectors. */
+int lqcd_mg_block_orthonormalize(void* vecs_dev, int nvec, int block, const lqcd_lattice* lat, void* stream);
+/* coarse = P^dag fine and fine = P coarse, with P = vecs (orthonormalised); prec F64 or F32 for all three. */
+int lqcd_mg_restrict(void* coarse_dev, const void* fine_dev, const void* vecs_dev, int nvec, int block, int prec,
+                     const lqcd_lattice* lat, void* stream);
+int lqcd_mg_prolong(void* fine_dev, const void* coarse_dev, const void* vecs_dev, int nvec, int block, int prec,
+                    const lqcd_lattice* lat, void* stream);
+/* Y = the Galerkin coarse operator P^dag D_W P (FP64) from the FP64 gauge field
+ * (op: Wilson, LQCD_F64, recon 18; boundary phases from lat) and FP64 vecs. */
+int lqcd_mg_coarse_build(void* Y_dev, const void* gauge_dev, const void* vecs_dev, int nvec, int block,
+                         const lqcd_lattice* lat, const lqcd_operator* op, void* stream);
+/* out = D_c in (dagger 0) or D_c^dag in (dagger 1), in the precision prec of Y, in and out (out != in). */
+int lqcd_mg_coarse_apply(void* out_dev, const void* in_dev, const void* Y_dev, int nvec, int block, int prec,
+                         int dagger, const lqcd_lattice* lat, void* stream);
+/* Solver: lqcd_mg_setup computes nvec near-null vectors from the caller's
+ * random FP64 full-lattice fields (setup_iters CG iterations on M^dag M each),
+ * orthonormalises them and builds the coarse operator, all inside the
+ * workspace; lqcd_mg_solve then solves D_W x = b (FP64 full-lattice fields) by
+ * flexible GCR in FP64, preconditioned by an FP32 V-cycle (MR smoothing,
+ * restriction, coarse_iters CGNR iterations on D_c, prolongation, MR
+ * smoothing) replayed as one CUDA graph, until the FP64 true residual
+ * |b - D x| / |b| <= params->tol (checked at every restart and at the end).
+ * gauge64: FP64 18-real; gauge32: FP32 12-real of the same field. The
+ * workspace (lqcd_mg_workspace_bytes, 256-byte aligned) must have gone
+ * through lqcd_mg_setup with the same lattice, operator and parameters.
+ * info->iterations counts preconditioned GCR iterations. Synchronises. */
+size_t lqcd_mg_workspace_bytes(const lqcd_lattice* lat, const lqcd_operator* op, const lqcd_mg_params* mg);
+int lqcd_mg_setup(const void* gauge64_dev, const void* gauge32_dev, const double* random_vectors_dev,
+                  const lqcd_lattice* lat, const lqcd_operator* op, const lqcd_mg_params* mg,
+                  void* workspace_dev, size_t workspace_bytes, void* stream);
+int lqcd_mg_solve(void* x_dev, const void* b_dev, const void* gauge64_dev, const void* gauge32_dev,
+                  const lqcd_lattice* lat, const lqcd_operator* op, const lqcd_mg_params* mg,
+                  const lqcd_solver_params* params, lqcd_solve_info* info, void* workspace_dev,
+                  size_t workspace_bytes, void* stream);
+
 /* ---------------------------------------------------------------- force */
 
 /* Pseudofermion force for S = phi^dag (M^dag M)^-1 phi with M = D_W (Grid

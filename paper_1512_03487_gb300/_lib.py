@@ -64,6 +64,11 @@ class lqcd_hmc_info(C.Structure):
                 ("force_evaluations", C.c_int), ("cg_iterations", C.c_int), ("status", C.c_int)]
 
 
+class lqcd_mg_params(C.Structure):
+    _fields_ = [("block", C.c_int), ("nvec", C.c_int), ("setup_iters", C.c_int), ("pre_smooth", C.c_int),
+                ("post_smooth", C.c_int), ("coarse_iters", C.c_int), ("restart", C.c_int)]
+
+
 _P = C.c_void_p
 _LAT = C.POINTER(lqcd_lattice)
 _OP = C.POINTER(lqcd_operator)
@@ -106,6 +111,16 @@ SIGNATURES = {
     "lqcd_gauge_force": (_I, [_P, _P, _LAT, C.c_double, _P]),
     "lqcd_gauge_exp_update": (_I, [_P, _P, C.c_double, _LAT, _P]),
     "lqcd_hmc_workspace_bytes": (_SZ, [_LAT, _OP, _PRM]),
+    "lqcd_mg_coarse_bytes": (_SZ, [_LAT, _I, _I, _I]),
+    "lqcd_mg_coarse_op_bytes": (_SZ, [_LAT, _I, _I, _I]),
+    "lqcd_mg_block_orthonormalize": (_I, [_P, _I, _I, _LAT, _P]),
+    "lqcd_mg_restrict": (_I, [_P, _P, _P, _I, _I, _I, _LAT, _P]),
+    "lqcd_mg_prolong": (_I, [_P, _P, _P, _I, _I, _I, _LAT, _P]),
+    "lqcd_mg_coarse_build": (_I, [_P, _P, _P, _I, _I, _LAT, _OP, _P]),
+    "lqcd_mg_coarse_apply": (_I, [_P, _P, _P, _I, _I, _I, _I, _LAT, _P]),
+    "lqcd_mg_workspace_bytes": (_SZ, [_LAT, _OP, C.POINTER(lqcd_mg_params)]),
+    "lqcd_mg_setup": (_I, [_P, _P, _P, _LAT, _OP, C.POINTER(lqcd_mg_params), _P, _SZ, _P]),
+    "lqcd_mg_solve": (_I, [_P, _P, _P, _P, _LAT, _OP, C.POINTER(lqcd_mg_params), _PRM, _INFO, _P, _SZ, _P]),
     "lqcd_hmc_trajectory": (_I, [_P, _P, _P, _LAT, _OP, C.POINTER(lqcd_hmc_params), _PRM,
                                  C.POINTER(lqcd_hmc_info), _P, _SZ, _P]),
     "lqcd_M_noalloc": (_I, [_P, _P, _P, _LAT, _OP, _I, _I, _P]),

@@ -17,7 +17,7 @@ from . import _lib
 from ._lib import (  # noqa: F401  (re-exported constants and structs)
     LQCD_DWF, LQCD_EVEN, LQCD_F16, LQCD_F32, LQCD_F64, LQCD_FORCE_GRAD, LQCD_FORCE_TA, LQCD_FULL,
     LQCD_LEAPFROG, LQCD_MINNORM2, LQCD_ODD, LQCD_WILSON, lqcd_hmc_info, lqcd_hmc_params, lqcd_lattice,
-    lqcd_operator, lqcd_solve_info, lqcd_solver_params,
+    lqcd_mg_params, lqcd_operator, lqcd_solve_info, lqcd_solver_params,
 )
 
 lib = _lib.load()
@@ -302,6 +302,65 @@ def lqcd_hmc_trajectory(gauge, mom, phi, lat, op, hmc, params, workspace, stream
     nbytes = workspace.numel() * workspace.element_size()
     st = lib.lqcd_hmc_trajectory(_ptr(gauge), _ptr(mom), _ptr(phi), C.byref(lat), C.byref(op), C.byref(hmc),
                                  C.byref(params), C.byref(info), _ptr(workspace), nbytes, _stream(stream))
+    if raise_on_error:
+        _check(st)
+    return info
+
+
+def mg_params(block: int = 4, nvec: int = 12, setup_iters: int = 40, pre_smooth: int = 0, post_smooth: int = 4,
+              coarse_iters: int = 30, restart: int = 16) -> lqcd_mg_params:
+    return lqcd_mg_params(block=block, nvec=nvec, setup_iters=setup_iters, pre_smooth=pre_smooth,
+                          post_smooth=post_smooth, coarse_iters=coarse_iters, restart=restart)
+
+
+def lqcd_mg_coarse_bytes(lat, nvec, block, prec) -> int:
+    return int(lib.lqcd_mg_coarse_bytes(C.byref(lat), nvec, block, prec))
+
+
+def lqcd_mg_coarse_op_bytes(lat, nvec, block, prec) -> int:
+    return int(lib.lqcd_mg_coarse_op_bytes(C.byref(lat), nvec, block, prec))
+
+
+def lqcd_mg_block_orthonormalize(vecs, nvec, block, lat, stream=None):
+    _check(lib.lqcd_mg_block_orthonormalize(_ptr(vecs), nvec, block, C.byref(lat), _stream(stream)))
+
+
+def lqcd_mg_restrict(coarse, fine, vecs, nvec, block, prec, lat, stream=None):
+    _check(lib.lqcd_mg_restrict(_ptr(coarse), _ptr(fine), _ptr(vecs), nvec, block, prec, C.byref(lat),
+                                _stream(stream)))
+
+
+def lqcd_mg_prolong(fine, coarse, vecs, nvec, block, prec, lat, stream=None):
+    _check(lib.lqcd_mg_prolong(_ptr(fine), _ptr(coarse), _ptr(vecs), nvec, block, prec, C.byref(lat),
+                               _stream(stream)))
+
+
+def lqcd_mg_coarse_build(Y, gauge, vecs, nvec, block, lat, op, stream=None):
+    _check(lib.lqcd_mg_coarse_build(_ptr(Y), _ptr(gauge), _ptr(vecs), nvec, block, C.byref(lat), C.byref(op),
+                                    _stream(stream)))
+
+
+def lqcd_mg_coarse_apply(out, inp, Y, nvec, block, prec, dagger, lat, stream=None):
+    _check(lib.lqcd_mg_coarse_apply(_ptr(out), _ptr(inp), _ptr(Y), nvec, block, prec, int(dagger), C.byref(lat),
+                                    _stream(stream)))
+
+
+def lqcd_mg_workspace_bytes(lat, op, mg) -> int:
+    return int(lib.lqcd_mg_workspace_bytes(C.byref(lat), C.byref(op), C.byref(mg)))
+
+
+def lqcd_mg_setup(gauge64, gauge32, random_vectors, lat, op, mg, workspace, stream=None):
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(lib.lqcd_mg_setup(_ptr(gauge64), _ptr(gauge32), _ptr(random_vectors), C.byref(lat), C.byref(op),
+                             C.byref(mg), _ptr(workspace), nbytes, _stream(stream)))
+
+
+def lqcd_mg_solve(x, b, gauge64, gauge32, lat, op, mg, params, workspace, stream=None,
+                  raise_on_error=True) -> lqcd_solve_info:
+    info = lqcd_solve_info()
+    nbytes = workspace.numel() * workspace.element_size()
+    st = lib.lqcd_mg_solve(_ptr(x), _ptr(b), _ptr(gauge64), _ptr(gauge32), C.byref(lat), C.byref(op), C.byref(mg),
+                           C.byref(params), C.byref(info), _ptr(workspace), nbytes, _stream(stream))
     if raise_on_error:
         _check(st)
     return info

@@ -71,7 +71,7 @@ template <> struct PrecTraits<LQCD_F16> { using real = float; static constexpr i
 // FP64 stays FP64, FP32 and FP16 storage iterate in FP32.
 __host__ __device__ constexpr int vec_prec(int sloppy) { return sloppy == LQCD_F64 ? LQCD_F64 : LQCD_F32; }
 
-inline int spinor_site_bytes(int prec) {
+__host__ __device__ inline int spinor_site_bytes(int prec) {
   return prec == LQCD_F64 ? 192 : prec == LQCD_F32 ? 96 : prec == LQCD_F16 ? 52 : 0;
 }
 inline int link_bytes(int prec, int recon) {
@@ -79,7 +79,7 @@ inline int link_bytes(int prec, int recon) {
   return reals * (prec == LQCD_F64 ? 8 : prec == LQCD_F32 ? 4 : 2);
 }
 // bytes of one checkerboard of a spinor field
-inline size_t cb_spinor_bytes(const Geom& g, int prec) {
+__host__ __device__ inline size_t cb_spinor_bytes(const Geom& g, int prec) {
   return (size_t)g.sstride * spinor_site_bytes(prec);
 }
 
