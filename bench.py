@@ -624,6 +624,7 @@ def run_extras(L, F, flush, stream):
     out["gparity_16x3x32_xy_mixed_fp32"] = gparity_bench(L, F, flush, stream)
     out["su3_mul_footprint"] = su3_sweep(L, F, flush, stream)
     out["hmc_16x4"] = hmc_bench(L, F, stream)
+    out["multigrid_24x3x48_m0.01"] = mg_bench(L, F, flush, stream)
 
     # uneven batch: 4 each of 8^4, 12^4, 16^4, 20^4, Haar links, m = 0.05, FP32-inner, one persistent launch per phase
     shapes = [(n_, n_, n_, n_) for n_ in (8, 12, 16, 20) for _ in range(4)]
@@ -811,6 +812,33 @@ def gparity_bench(L, F, flush, stream):
             "hop_f32r12_gparity": {"launch_us": round(t * 1e6, 2), "algorithmic_bytes_per_site": bps,
                                    "achieved_gbs": round(bps * vh * 2 / t / 1e9, 1),
                                    "frac_of_measured_hbm": round(bps * vh * 2 / t / 1e9 / peak, 4)}}
+
+
+def mg_bench(L, F, flush, stream):
+    """Two-level multigrid (b = 4, 12 near-null vectors, 40 set-up CG iterations each, 4 MR
+    post-smoothing steps, 16 coarse CGNR iterations) on the bench field, solving the full
+    D_W x = b to a 1e-10 FP64 residual: set-up and solve time, and outer iterations."""
+    import torch
+    from synthetic import config_seed, gauge_field, gaussian_spinor
+    dims, m, nv = (24, 24, 24, 48), 0.01, 12
+    lat = L.lattice(dims, bc=BC)
+    op = L.operator(mass=m)
+    U = gauge_field(dims, "exp", config_seed(1, 0), eps=0.3)
+    g64 = F.gauge_to_device(U, lat, 0, 18)
+    g32 = F.gauge_to_device(U, lat, 1, 12)
+    del U
+    bd = F.spinor_to_device(gaussian_spinor(dims, config_seed(1, 1), lead=(1,)), lat, 0, 2)
+    rnd = torch.cat([F.spinor_to_device(v, lat, 0, 2) for v in gaussian_spinor(dims, config_seed(70, 0), lead=(nv,))])
+    mgp = L.mg_params(block=4, nvec=nv, setup_iters=40, pre_smooth=0, post_smooth=4, coarse_iters=16, restart=16)
+    ws = F.empty(L.lqcd_mg_workspace_bytes(lat, op, mgp))
+    setup_ms, _ = _events_time(lambda: L.lqcd_mg_setup(g64, g32, rnd, lat, op, mgp, ws), stream, flush)
+    x = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
+    prm = L.solver_params(tol=1e-10, maxiter=500)
+    L.lqcd_mg_solve(x, bd, g64, g32, lat, op, mgp, prm, ws)
+    ms, info = _events_time(lambda: L.lqcd_mg_solve(x, bd, g64, g32, lat, op, mgp, prm, ws), stream, flush)
+    return {"setup_ms": round(setup_ms, 1), "solve_ms": round(ms, 2), "outer_iterations": info.iterations,
+            "true_rel_residual": info.true_rel_residual,
+            "note": "full (not even-odd) operator; the even-odd CG of the headline needs 61 iterations here"}
 
 
 def hmc_bench(L, F, stream):

@@ -460,10 +460,12 @@ int lqcd_mg_coarse_apply(void* out_dev, const void* in_dev, const void* Y_dev, i
  * random FP64 full-lattice fields (setup_iters CG iterations on M^dag M each),
  * orthonormalises them and builds the coarse operator, all inside the
  * workspace; lqcd_mg_solve then solves D_W x = b (FP64 full-lattice fields) by
- * flexible GCR in FP64, preconditioned by an FP32 V-cycle (MR smoothing,
- * restriction, coarse_iters CGNR iterations on D_c, prolongation, MR
- * smoothing) replayed as one CUDA graph, until the FP64 true residual
- * |b - D x| / |b| <= params->tol (checked at every restart and at the end).
+ * refinement cycles: r = b - D x in FP64, then flexible GCR in FP32 on D c = r
+ * (up to `restart` vectors, until |r| drops 1e-5-fold or below tol),
+ * preconditioned by an FP32 V-cycle (MR smoothing, restriction, coarse_iters
+ * CGNR iterations on D_c, prolongation, MR smoothing) replayed as one CUDA
+ * graph, and x += c in FP64; it returns when the FP64 true residual
+ * |b - D x| / |b| <= params->tol.
  * gauge64: FP64 18-real; gauge32: FP32 12-real of the same field. The
  * workspace (lqcd_mg_workspace_bytes, 256-byte aligned) must have gone
  * through lqcd_mg_setup with the same lattice, operator and parameters.

@@ -159,11 +159,21 @@ __device__ __forceinline__ bool grid_sum(double v[N], double* partials, unsigned
   __syncthreads();
   if (!is_last) return false;
   __threadfence();
+  // every thread sums a fixed strided subset of the partials, then a fixed-order block sum
+#pragma unroll
+  for (int n = 0; n < N; n++) {
+    double s = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) s += __ldcg(partials + (int64_t)n * gridDim.x + b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) sh[n][warp] = s;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int n = 0; n < N; n++) {
       double s = 0.0;
-      for (unsigned b = 0; b < gridDim.x; b++) s += __ldcg(partials + (int64_t)n * gridDim.x + b);
+      for (int w = 0; w < nw; w++) s += sh[n][w];
       out[n] = s;
     }
     *counter = 0u;
@@ -232,12 +242,13 @@ __global__ void __launch_bounds__(MG_BLOCK) k_block_orth(void* vecs, MGGeom m) {
   }
 }
 
-// c(X)[(s, k)] = sum_{x in X} P_k(x)|_s^dag psi(x)|_s
+// c(X)[(s, k)] = sum_{x in X} P_k(x)|_s^dag psi(x)|_s; one CTA per (aggregate X, vector k)
 template <int P>
 __global__ void __launch_bounds__(MG_BLOCK) k_restrict(void* coarse, const void* fine, const void* vecs, MGGeom m) {
   using T = typename PrecTraits<P>::real;
   __shared__ double2 sh[2 * (MG_BLOCK / 32)];
   const int64_t agg = blockIdx.x;
+  const int k = blockIdx.y;
   const bool act = threadIdx.x < m.b * m.b * m.b * m.b;
   int c[4], parity;
   int64_t cb;
@@ -246,22 +257,21 @@ __global__ void __launch_bounds__(MG_BLOCK) k_restrict(void* coarse, const void*
   zero(psi);
   if (act) SpinorIO<P>::load(fine_ptr<P>(fine, m, 0, parity), m.g.sstride, cb, psi);
   cpx<T>* out = static_cast<cpx<T>*>(coarse) + agg * m.nc;
-  for (int k = 0; k < m.nv; k++) {
-    Spinor<T> v;
-    zero(v);
-    if (act) SpinorIO<P>::load(fine_ptr<P>(vecs, m, k, parity), m.g.sstride, cb, v);
-    double2 d[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+  Spinor<T> v;
+  zero(v);
+  if (act) SpinorIO<P>::load(fine_ptr<P>(vecs, m, k, parity), m.g.sstride, cb, v);
+  T pr[2] = {T(0), T(0)}, pi[2] = {T(0), T(0)};
 #pragma unroll
-    for (int e = 0; e < 12; e++) {
-      const int s = e / 6;
-      d[s].x += (double)v.v[e].r * psi.v[e].r + (double)v.v[e].i * psi.v[e].i;
-      d[s].y += (double)v.v[e].r * psi.v[e].i - (double)v.v[e].i * psi.v[e].r;
-    }
-    block_sum<2>(d, sh);
-    if (threadIdx.x == 0) {
-      out[k] = mk((T)d[0].x, (T)d[0].y);
-      out[m.nv + k] = mk((T)d[1].x, (T)d[1].y);
-    }
+  for (int e = 0; e < 12; e++) {
+    const int s = e / 6;
+    pr[s] = fma(v.v[e].r, psi.v[e].r, fma(v.v[e].i, psi.v[e].i, pr[s]));
+    pi[s] = fma(v.v[e].r, psi.v[e].i, fma(-v.v[e].i, psi.v[e].r, pi[s]));
+  }
+  double2 d[2] = {make_double2((double)pr[0], (double)pi[0]), make_double2((double)pr[1], (double)pi[1])};
+  block_sum<2>(d, sh);
+  if (threadIdx.x == 0) {
+    out[k] = mk((T)d[0].x, (T)d[0].y);
+    out[m.nv + k] = mk((T)d[1].x, (T)d[1].y);
   }
 }
 
@@ -309,29 +319,75 @@ __device__ __forceinline__ int64_t coarse_nb(const MGGeom& m, int64_t X, int d) 
   return cc[0] + (int64_t)m.cX * (cc[1] + (int64_t)m.cY * (cc[2] + (int64_t)m.cZ * cc[3]));
 }
 
-// out(X)_i = sum_d sum_j Y_d(X)_ij in(X + d)_j; dagger: sum_d sum_j conj(Y_{-d}(X + d)_ji) in(X + d)_j
+// out(X)_i = sum_d sum_j Y_d(X)_ij in(X + d)_j; dagger: sum_d sum_j conj(Y_{-d}(X + d)_ji) in(X + d)_j.
+// One warp per (coarse site, row): the lanes take the 9 Nc products in turn
+// (consecutive j for consecutive lanes) and the warp sums them.
 template <typename T>
 __global__ void __launch_bounds__(MG_BLOCK) k_coarse_apply(cpx<T>* out, const cpx<T>* in, const cpx<T>* Y, MGGeom m,
                                                            int dagger) {
-  const int64_t t = (int64_t)blockIdx.x * MG_BLOCK + threadIdx.x;
-  if (t >= m.Vc * m.nc) return;
-  const int64_t X = t / m.nc;
-  const int i = (int)(t - X * m.nc);
+  const int64_t wid = ((int64_t)blockIdx.x * MG_BLOCK + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= m.Vc * m.nc) return;  // whole warps exit together
   const int nc = m.nc;
-  cpx<T> acc = mk(T(0), T(0));
-  for (int d = 0; d < 9; d++) {
-    const int64_t Xn = coarse_nb(m, X, d);
-    const cpx<T>* v = in + Xn * nc;
+  const int X = (int)(wid / nc);
+  const int i = (int)(wid - (int64_t)X * nc);
+  // lanes 0..8 find the nine stencil neighbours once (32-bit index arithmetic)
+  int nb_l = X;
+  if (lane < 9 && lane > 0) {
+    const int mu = (lane - 1) >> 1, sgn = (lane & 1) ? 1 : -1;
+    int cc[4];
+    int a = X;
+    cc[0] = a % m.cX;
+    a /= m.cX;
+    cc[1] = a % m.cY;
+    a /= m.cY;
+    cc[2] = a % m.cZ;
+    cc[3] = a / m.cZ;
+    const int L[4] = {m.cX, m.cY, m.cZ, m.cT};
+    cc[mu] = (cc[mu] + sgn + L[mu]) % L[mu];
+    nb_l = cc[0] + m.cX * (cc[1] + m.cY * (cc[2] + m.cZ * cc[3]));
+  }
+  float ar = 0.f, ai = 0.f;
+  double dr_ = 0.0, di_ = 0.0;
+  const int total = 9 * nc;
+  for (int base = 0; base < total; base += 32) {  // warp-uniform trip count: every lane joins the shuffle
+    const int q = base + lane;
+    const int d = q < total ? q / nc : 0;
+    const int Xn = __shfl_sync(0xffffffffu, nb_l, d);
+    if (q >= total) continue;
+    const int j = q - d * nc;
+    const cpx<T> v = in[(int64_t)Xn * nc + j];
+    cpx<T> y;
     if (!dagger) {
-      const cpx<T>* row = Y + (((int64_t)d * m.Vc + X) * nc + i) * nc;
-      for (int j = 0; j < nc; j++) acc = cmadd(acc, row[j], v[j]);
+      y = Y[(((int64_t)d * m.Vc + X) * nc + i) * nc + j];
     } else {
       const int dr = d == 0 ? 0 : (((d - 1) ^ 1) + 1);  // opposite direction
-      const cpx<T>* blk = Y + ((int64_t)dr * m.Vc + Xn) * nc * nc;
-      for (int j = 0; j < nc; j++) acc = cmadd_conj(acc, blk[(int64_t)j * nc + i], v[j]);
+      y = conj(Y[(((int64_t)dr * m.Vc + Xn) * nc + j) * nc + i]);
+    }
+    const cpx<T> p = cmul(y, v);
+    if (sizeof(T) == 8) {
+      dr_ += (double)p.r;
+      di_ += (double)p.i;
+    } else {
+      ar += (float)p.r;
+      ai += (float)p.i;
     }
   }
-  out[t] = acc;
+  if (sizeof(T) == 8) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      dr_ += __shfl_down_sync(0xffffffffu, dr_, o);
+      di_ += __shfl_down_sync(0xffffffffu, di_, o);
+    }
+    if (lane == 0) out[wid] = mk((T)dr_, (T)di_);
+  } else {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ar += __shfl_down_sync(0xffffffffu, ar, o);
+      ai += __shfl_down_sync(0xffffffffu, ai, o);
+    }
+    if (lane == 0) out[wid] = mk((T)ar, (T)ai);
+  }
 }
 
 // One coarse basis vector j of aggregate X + d seen from site x of aggregate X:
@@ -479,18 +535,24 @@ __global__ void __launch_bounds__(MG_BLOCK) k_dot(const void* x, const void* y, 
                                                   unsigned int* counter, double* out, double2* mr_alpha) {
   using T = typename PrecTraits<P>::real;
   MG_FINE_SITE
+  // per-site sums in the field precision (FP64 arithmetic is scarce on this GPU),
+  // the sum over sites in FP64
   double v[3] = {0.0, 0.0, 0.0};
   if (valid) {
     const int64_t h = (int64_t)cb_spinor_bytes(g, P);
     Spinor<T> xv, yv;
     SpinorIO<P>::load(static_cast<const char*>(x) + parity * h, g.sstride, cb, xv);
     SpinorIO<P>::load(static_cast<const char*>(y) + parity * h, g.sstride, cb, yv);
+    T a0 = T(0), a1 = T(0), a2 = T(0);
 #pragma unroll
     for (int e = 0; e < 12; e++) {
-      v[0] += (double)xv.v[e].r * yv.v[e].r + (double)xv.v[e].i * yv.v[e].i;
-      v[1] += (double)xv.v[e].r * yv.v[e].i - (double)xv.v[e].i * yv.v[e].r;
-      v[2] += (double)xv.v[e].r * xv.v[e].r + (double)xv.v[e].i * xv.v[e].i;
+      a0 = fma(xv.v[e].r, yv.v[e].r, fma(xv.v[e].i, yv.v[e].i, a0));
+      a1 = fma(xv.v[e].r, yv.v[e].i, fma(-xv.v[e].i, yv.v[e].r, a1));
+      a2 = fma(xv.v[e].r, xv.v[e].r, fma(xv.v[e].i, xv.v[e].i, a2));
     }
+    v[0] = (double)a0;
+    v[1] = (double)a1;
+    v[2] = (double)a2;
   }
   double tot[3];
   if (grid_sum<3>(v, partials, counter, tot)) {
@@ -501,6 +563,20 @@ __global__ void __launch_bounds__(MG_BLOCK) k_dot(const void* x, const void* y, 
     }
     if (mr_alpha) *mr_alpha = tot[2] > 0.0 ? make_double2(tot[0] / tot[2], tot[1] / tot[2]) : make_double2(0.0, 0.0);
   }
+}
+
+// y64 += x32 (the FP32 correction of a refinement cycle added to the FP64 solution)
+__global__ void __launch_bounds__(MG_BLOCK) k_acc64(void* y, const void* x, Geom g) {
+  MG_FINE_SITE
+  if (!valid) return;
+  const int64_t h64 = (int64_t)cb_spinor_bytes(g, LQCD_F64), h32 = (int64_t)cb_spinor_bytes(g, LQCD_F32);
+  Spinor<double> yv;
+  Spinor<float> xv;
+  SpinorIO<LQCD_F64>::load(static_cast<const char*>(y) + parity * h64, g.sstride, cb, yv);
+  SpinorIO<LQCD_F32>::load(static_cast<const char*>(x) + parity * h32, g.sstride, cb, xv);
+#pragma unroll
+  for (int e = 0; e < 12; e++) yv.v[e] = mk(yv.v[e].r + (double)xv.v[e].r, yv.v[e].i + (double)xv.v[e].i);
+  SpinorIO<LQCD_F64>::store(static_cast<char*>(y) + parity * h64, g.sstride, cb, yv);
 }
 
 // MR step: e += alpha s, s -= alpha t (alpha from the device)
@@ -577,7 +653,8 @@ template <typename F> static int dispatch_prec(int prec, F&& f) {
 
 static int restrict_(const MGGeom& m, int prec, void* coarse, const void* fine, const void* vecs, cudaStream_t s) {
   return dispatch_prec(prec, [&](auto P) {
-    k_restrict<decltype(P)::value><<<(unsigned)m.Vc, agg_threads(m), 0, s>>>(coarse, fine, vecs, m);
+    k_restrict<decltype(P)::value><<<dim3((unsigned)m.Vc, (unsigned)m.nv), agg_threads(m), 0, s>>>(coarse, fine, vecs,
+                                                                                                 m);
     return after_launch("k_restrict");
   });
 }
@@ -590,7 +667,7 @@ static int prolong_(const MGGeom& m, int prec, void* fine, const void* coarse, c
 }
 static int coarse_apply_(const MGGeom& m, int prec, void* out, const void* in, const void* Y, int dagger,
                          cudaStream_t s) {
-  const unsigned grid = n_grid(m.Vc * m.nc);
+  const unsigned grid = n_grid(m.Vc * m.nc * 32);
   if (prec == LQCD_F64)
     k_coarse_apply<double><<<grid, MG_BLOCK, 0, s>>>(static_cast<cpx<double>*>(out),
                                                      static_cast<const cpx<double>*>(in),
@@ -618,6 +695,22 @@ __global__ void k_c_to_f32(cpx<float>* dst, const cpx<double>* src, int64_t n) {
   if (t < n) dst[t] = mk((float)src[t].r, (float)src[t].i);
 }
 
+// The adjoint stencil in FP32, stored explicitly so that D_c^dag runs with the
+// coalesced row access of D_c: Yd_d(X)_ij = conj(Y_{-d}(X + d)_ji).
+__global__ void k_c_dagger(cpx<float>* Yd, const cpx<double>* Y, MGGeom m) {
+  const int64_t t = (int64_t)blockIdx.x * MG_BLOCK + threadIdx.x;
+  const int nc = m.nc;
+  if (t >= 9 * m.Vc * nc * nc) return;
+  const int64_t ij = t % ((int64_t)nc * nc);
+  const int64_t dX = t / ((int64_t)nc * nc);
+  const int64_t X = dX % m.Vc;
+  const int d = (int)(dX / m.Vc);
+  const int i = (int)(ij / nc), j = (int)(ij % nc);
+  const int dr = d == 0 ? 0 : (((d - 1) ^ 1) + 1);
+  const cpx<double> y = Y[(((int64_t)dr * m.Vc + coarse_nb(m, X, d)) * nc + j) * nc + i];
+  Yd[t] = mk((float)y.r, (float)-y.i);
+}
+
 // ---- solver workspace
 struct MGWs {
   double* partials;       // reduction scratch (3 x max blocks)
@@ -629,16 +722,19 @@ struct MGWs {
   void* P32;              // Nv FP32 fields
   void* Y64;              // coarse operator FP64
   void* Y32;              // coarse operator FP32
+  void* Y32d;             // its adjoint stencil FP32
   void* cvec[6];          // FP32 coarse: c, x, r, p, q, s
   void* f32[5];           // FP32 fine: r, e, s (MR residual), t, tmp
-  void* x64;              // outer solution accumulator (FP64)
-  void* r64;              // outer residual
-  void* Z;                // restart x FP64 fields z_i
-  void* W;                // restart x FP64 fields w_i = D z_i
+  void* r64;              // FP64 true residual of a refinement cycle
+  void* x32;              // FP32 correction accumulated within a cycle
+  void* Z;                // restart x FP32 fields z_i = K r
+  void* W;                // restart x FP32 fields w_i = D z_i
+  void* scratch;          // the region of Z and W, lent to the set-up CG
+  size_t scratch_bytes;
   size_t total;
 };
 
-static MGWs mg_carve(void* base, const MGGeom& m, int restart) {
+static MGWs mg_carve(void* base, const MGGeom& m, int restart, size_t setup_cg_bytes) {
   MGWs w;
   memset(&w, 0, sizeof(w));
   size_t o = 0;
@@ -660,12 +756,15 @@ static MGWs mg_carve(void* base, const MGGeom& m, int restart) {
   const size_t ybytes = (size_t)9 * m.Vc * m.nc * m.nc;
   w.Y64 = take(ybytes * sizeof(cpx<double>));
   w.Y32 = take(ybytes * sizeof(cpx<float>));
+  w.Y32d = take(ybytes * sizeof(cpx<float>));
   for (int k = 0; k < 6; k++) w.cvec[k] = take((size_t)m.Vc * m.nc * sizeof(cpx<float>));
   for (int k = 0; k < 5; k++) w.f32[k] = take(f32);
-  w.x64 = take(f64);
   w.r64 = take(f64);
-  w.Z = take(f64 * restart);
-  w.W = take(f64 * restart);
+  w.x32 = take(f32);
+  w.scratch_bytes = std::max(2 * f32 * (size_t)restart, setup_cg_bytes);
+  w.scratch = take(w.scratch_bytes);
+  w.Z = w.scratch;
+  w.W = b ? static_cast<char*>(w.scratch) + f32 * (size_t)restart : nullptr;
   w.total = o;
   return w;
 }
@@ -697,8 +796,8 @@ struct MGSolver {
     return after_launch("k_axpby");
   }
   // <x, y>, |x|^2 on the host
-  int dot64(const void* x, const void* y, double out[3]) {
-    k_dot<LQCD_F64><<<fine_grid(m.g), MG_BLOCK, 0, s>>>(x, y, m.g, w.partials, w.counter, w.dots, nullptr);
+  template <int P> int dot(const void* x, const void* y, double out[3]) {
+    k_dot<P><<<fine_grid(m.g), MG_BLOCK, 0, s>>>(x, y, m.g, w.partials, w.counter, w.dots, nullptr);
     int st = after_launch("k_dot");
     if (st) return st;
     cudaError_t e = cudaMemcpyAsync(out, w.dots, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -741,14 +840,14 @@ struct MGSolver {
     const unsigned gr = n_grid(n);
     int st;
     k_c_update<float><<<gr, MG_BLOCK, 0, s>>>(x, r, p, q, sv, c, n, w.csc, 0);
-    if ((st = coarse_apply_(m, LQCD_F32, sv, r, w.Y32, 1, s))) return st;
+    if ((st = coarse_apply_(m, LQCD_F32, sv, r, w.Y32d, 0, s))) return st;
     k_c_update<float><<<gr, MG_BLOCK, 0, s>>>(x, r, p, q, sv, c, n, w.csc, 3);
     k_c_norm<float><<<gr, MG_BLOCK, 0, s>>>(sv, n, w.partials, w.counter, w.csc, 0);
     for (int it = 0; it < mp.coarse_iters; it++) {
       if ((st = coarse_apply_(m, LQCD_F32, q, p, w.Y32, 0, s))) return st;
       k_c_norm<float><<<gr, MG_BLOCK, 0, s>>>(q, n, w.partials, w.counter, w.csc, 1);
       k_c_update<float><<<gr, MG_BLOCK, 0, s>>>(x, r, p, q, sv, c, n, w.csc, 1);
-      if ((st = coarse_apply_(m, LQCD_F32, sv, r, w.Y32, 1, s))) return st;
+      if ((st = coarse_apply_(m, LQCD_F32, sv, r, w.Y32d, 0, s))) return st;
       k_c_norm<float><<<gr, MG_BLOCK, 0, s>>>(sv, n, w.partials, w.counter, w.csc, 2);
       k_c_update<float><<<gr, MG_BLOCK, 0, s>>>(x, r, p, q, sv, c, n, w.csc, 2);
     }
@@ -818,12 +917,12 @@ static int mg_setup_impl(const MGGeom& m, const MGWs& w, const void* gauge64, co
   sp.use_graph = 1;
   const size_t cgb = lqcd_cg_workspace_bytes(lat, op, &sp, LQCD_FULL);
   // the CG workspace borrows the outer-solver region (Z, W), unused during set-up
-  if (cgb > 2 * f64 * (size_t)mp->restart) return fail(LQCD_ERR_WORKSPACE, "multigrid: set-up CG workspace");
+  if (cgb > w.scratch_bytes) return fail(LQCD_ERR_WORKSPACE, "multigrid: set-up CG workspace");
   for (int k = 0; k < m.nv; k++) {
     lqcd_solve_info info;
     const void* src = static_cast<const char*>(static_cast<const void*>(rnd)) + (size_t)k * f64;
-    int st = lqcd_cg_solve(field_at(w.P64, f64, k), src, gauge64, gauge32, lat, op, &sp, LQCD_FULL, &info, w.Z, cgb,
-                           s);
+    int st = lqcd_cg_solve(field_at(w.P64, f64, k), src, gauge64, gauge32, lat, op, &sp, LQCD_FULL, &info, w.scratch,
+                           cgb, s);
     if (st && st != LQCD_ERR_NOT_CONVERGED) return st;
   }
   int st = orthonormalize_(m, w.P64, s);
@@ -838,7 +937,21 @@ static int mg_setup_impl(const MGGeom& m, const MGWs& w, const void* gauge64, co
   const int64_t ny = (int64_t)9 * m.Vc * m.nc * m.nc;
   k_c_to_f32<<<n_grid(ny), MG_BLOCK, 0, s>>>(static_cast<cpx<float>*>(w.Y32), static_cast<const cpx<double>*>(w.Y64),
                                              ny);
-  return after_launch("k_c_to_f32");
+  if ((st = after_launch("k_c_to_f32"))) return st;
+  k_c_dagger<<<n_grid(ny), MG_BLOCK, 0, s>>>(static_cast<cpx<float>*>(w.Y32d), static_cast<const cpx<double>*>(w.Y64), m);
+  return after_launch("k_c_dagger");
+}
+
+static size_t setup_cg_bytes(const lqcd_lattice* lat, const lqcd_operator* op, const lqcd_mg_params* mp) {
+  lqcd_solver_params sp;
+  memset(&sp, 0, sizeof(sp));
+  sp.tol = 1e-14;
+  sp.maxiter = mp->setup_iters;
+  sp.sloppy_prec = LQCD_F32;
+  sp.sloppy_recon = 12;
+  sp.check_interval = mp->setup_iters;
+  sp.use_graph = 1;
+  return lqcd_cg_workspace_bytes(lat, op, &sp, LQCD_FULL);
 }
 
 static int mg_check(const lqcd_lattice* lat, const lqcd_operator* op, const lqcd_mg_params* mp, MGGeom* m) {
@@ -929,7 +1042,7 @@ int lqcd_mg_coarse_apply(void* out, const void* in, const void* Y, int nvec, int
 size_t lqcd_mg_workspace_bytes(const lqcd_lattice* lat, const lqcd_operator* op, const lqcd_mg_params* mp) {
   MGGeom m;
   if (mg_check(lat, op, mp, &m) != LQCD_OK) return 0;
-  return mg_carve(nullptr, m, mp->restart).total;
+  return mg_carve(nullptr, m, mp->restart, setup_cg_bytes(lat, op, mp)).total;
 }
 
 int lqcd_mg_setup(const void* gauge64, const void* gauge32, const double* random_vectors, const lqcd_lattice* lat,
@@ -940,7 +1053,7 @@ int lqcd_mg_setup(const void* gauge64, const void* gauge32, const double* random
   if (st) return st;
   if (!gauge64 || !gauge32 || !random_vectors || !workspace || ((uintptr_t)workspace & 255))
     return fail(LQCD_ERR_ARG, "lqcd_mg_setup: null or misaligned pointer");
-  const MGWs w = mg_carve(workspace, m, mp->restart);
+  const MGWs w = mg_carve(workspace, m, mp->restart, setup_cg_bytes(lat, op, mp));
   if (workspace_bytes < w.total) return fail(LQCD_ERR_WORKSPACE, "lqcd_mg_setup: workspace %zu < %zu", workspace_bytes,
                                              w.total);
   cudaStream_t s = (cudaStream_t)stream;
@@ -967,7 +1080,7 @@ int lqcd_mg_solve(void* x, const void* b, const void* gauge64, const void* gauge
   if (!prm || !(prm->tol > 0.0) || prm->maxiter < 1) return finish(fail(LQCD_ERR_ARG, "multigrid: bad solver params"));
   if (!x || !b || !gauge64 || !gauge32 || !workspace || ((uintptr_t)workspace & 255) || (((uintptr_t)x | (uintptr_t)b) & 15))
     return finish(fail(LQCD_ERR_ARG, "lqcd_mg_solve: null or misaligned pointer"));
-  S.w = mg_carve(workspace, S.m, mp->restart);
+  S.w = mg_carve(workspace, S.m, mp->restart, setup_cg_bytes(lat, op, mp));
   if (workspace_bytes < S.w.total)
     return finish(fail(LQCD_ERR_WORKSPACE, "lqcd_mg_solve: workspace %zu < %zu", workspace_bytes, S.w.total));
   S.mp = *mp;
@@ -978,63 +1091,72 @@ int lqcd_mg_solve(void* x, const void* b, const void* gauge64, const void* gauge
   S.gauge64 = gauge64;
   S.gauge32 = gauge32;
   S.s = (cudaStream_t)stream;
-  const size_t f64 = S.f64();
+  const size_t f32 = S.f32();
   const int mres = mp->restart;
-  // x = 0, r = b
-  if ((st = S.axpby<LQCD_F64>(x, b, 0.0, 0.0, nullptr, 0.0))) return finish(st);
-  if ((st = S.axpby<LQCD_F64>(S.w.r64, b, 1.0, 0.0, nullptr, 0.0))) return finish(st);
+  void* r32 = S.w.f32[0];  // the V-cycle graph reads its right-hand side here
+  void* e32 = S.w.f32[1];  // and leaves K r here
+  // Refinement cycles: FP64 true residual r = b - D x; FP32 flexible GCR on D c = r
+  // (Krylov vectors, dots and updates in FP32) until |r| drops by delta_cycle or
+  // below the tolerance; x += c in FP64; repeat until the FP64 residual <= tol.
+  const double delta_cycle = 1e-5;
+  if ((st = S.axpby<LQCD_F64>(x, b, 0.0, 0.0, nullptr, 0.0))) return finish(st);           // x = 0
+  if ((st = S.axpby<LQCD_F64>(S.w.r64, b, 1.0, 0.0, nullptr, 0.0))) return finish(st);     // r = b
   double d3[3];
-  if ((st = S.dot64(b, b, d3))) return finish(st);
+  if ((st = S.dot<LQCD_F64>(b, b, d3))) return finish(st);
   const double bnorm = std::sqrt(d3[2]);
   if (bnorm == 0.0) return finish(LQCD_OK);
   if ((st = S.capture_vcycle())) return finish(st);
   int iters = 0;
   double rel = 1.0;
   int status = LQCD_ERR_NOT_CONVERGED;
-  while (iters < prm->maxiter) {
-    for (int i = 0; i < mres && iters < prm->maxiter; i++, iters++) {
-      void* zi = field_at(S.w.Z, f64, i);
-      void* wi = field_at(S.w.W, f64, i);
-      // z_i = K r (FP32 V-cycle), w_i = D z_i (FP64)
-      k_convert<LQCD_F32, LQCD_F64><<<fine_grid(S.m.g), MG_BLOCK, 0, S.s>>>(S.w.f32[0], S.w.r64, S.m.g);
-      cudaError_t e = cudaGraphLaunch(S.vgraph, S.s);
-      if (e != cudaSuccess) { st = cuda_fail(e, "multigrid: V-cycle launch"); break; }
-      k_convert<LQCD_F64, LQCD_F32><<<fine_grid(S.m.g), MG_BLOCK, 0, S.s>>>(zi, S.w.f32[1], S.m.g);
-      if ((st = after_launch("k_convert")) || (st = S.D64(wi, zi))) break;
-      // orthogonalise w_i against w_j (orthonormal), same combination on z_i
-      for (int j = 0; j < i && !st; j++) {
-        void* wj = field_at(S.w.W, f64, j);
-        if ((st = S.dot64(wj, wi, d3))) break;
-        if ((st = S.axpby<LQCD_F64>(wi, wj, -d3[0], -d3[1], nullptr, 1.0))) break;
-        st = S.axpby<LQCD_F64>(zi, field_at(S.w.Z, f64, j), -d3[0], -d3[1], nullptr, 1.0);
-      }
-      if (st) break;
-      if ((st = S.dot64(wi, wi, d3))) break;
-      const double nw = std::sqrt(d3[2]);
-      if (!(nw > 0.0) || !std::isfinite(nw)) { st = fail(LQCD_ERR_NAN, "multigrid: breakdown (|w| = %g)", nw); break; }
-      if ((st = S.axpby<LQCD_F64>(wi, wi, 0.0, 0.0, nullptr, 1.0 / nw))) break;
-      if ((st = S.axpby<LQCD_F64>(zi, zi, 0.0, 0.0, nullptr, 1.0 / nw))) break;
-      // alpha = <w_i, r>; x += alpha z_i; r -= alpha w_i
-      if ((st = S.dot64(wi, S.w.r64, d3))) break;
-      if ((st = S.axpby<LQCD_F64>(x, zi, d3[0], d3[1], nullptr, 1.0))) break;
-      if ((st = S.axpby<LQCD_F64>(S.w.r64, wi, -d3[0], -d3[1], nullptr, 1.0))) break;
-      if ((st = S.dot64(S.w.r64, S.w.r64, d3))) break;
-      rel = std::sqrt(d3[2]) / bnorm;
-      if (rel <= prm->tol) { iters++; break; }
-    }
-    if (st) break;
-    // restart (and final check): true residual r = b - D x in FP64
-    if ((st = S.D64(S.w.r64, x))) break;
-    if ((st = S.axpby<LQCD_F64>(S.w.r64, b, 1.0, 0.0, nullptr, -1.0))) break;
-    if ((st = S.dot64(S.w.r64, S.w.r64, d3))) break;
+  std::vector<double> wnorm2(mres);
+  for (;;) {
+    if ((st = S.dot<LQCD_F64>(S.w.r64, S.w.r64, d3))) break;
     rel = std::sqrt(d3[2]) / bnorm;
     if (!std::isfinite(rel)) { st = fail(LQCD_ERR_NAN, "multigrid: NaN residual"); break; }
     if (rel <= prm->tol) { status = LQCD_OK; break; }
+    if (iters >= prm->maxiter) break;
     if (prm->timeout_ms > 0 &&
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() > prm->timeout_ms) {
       st = fail(LQCD_ERR_TIMEOUT, "multigrid: wall-clock limit exceeded");
       break;
     }
+    const double target = std::max(delta_cycle * rel, 0.5 * prm->tol) * bnorm;
+    k_convert<LQCD_F32, LQCD_F64><<<fine_grid(S.m.g), MG_BLOCK, 0, S.s>>>(r32, S.w.r64, S.m.g);
+    if ((st = after_launch("k_convert"))) break;
+    if ((st = S.axpby<LQCD_F32>(S.w.x32, r32, 0.0, 0.0, nullptr, 0.0))) break;  // c = 0
+    for (int i = 0; i < mres && iters < prm->maxiter; i++) {
+      void* zi = field_at(S.w.Z, f32, i);
+      void* wi = field_at(S.w.W, f32, i);
+      cudaError_t e = cudaGraphLaunch(S.vgraph, S.s);  // e32 = K r32
+      if (e != cudaSuccess) { st = cuda_fail(e, "multigrid: V-cycle launch"); break; }
+      if ((st = S.axpby<LQCD_F32>(zi, e32, 1.0, 0.0, nullptr, 0.0)) || (st = S.D32(wi, zi))) break;
+      // w_i -= beta_j w_j, z_i -= beta_j z_j with beta_j = <w_j, w_i> / |w_j|^2 (modified Gram-Schmidt)
+      for (int j = 0; j < i && !st; j++) {
+        void* wj = field_at(S.w.W, f32, j);
+        if ((st = S.dot<LQCD_F32>(wj, wi, d3))) break;
+        const double br = d3[0] / wnorm2[j], bi = d3[1] / wnorm2[j];
+        if ((st = S.axpby<LQCD_F32>(wi, wj, -br, -bi, nullptr, 1.0))) break;
+        st = S.axpby<LQCD_F32>(zi, field_at(S.w.Z, f32, j), -br, -bi, nullptr, 1.0);
+      }
+      if (st) break;
+      // alpha = <w_i, r> / |w_i|^2; c += alpha z_i; r -= alpha w_i
+      if ((st = S.dot<LQCD_F32>(wi, r32, d3))) break;
+      wnorm2[i] = d3[2];
+      if (!(d3[2] > 0.0) || !std::isfinite(d3[2])) { st = fail(LQCD_ERR_NAN, "multigrid: GCR breakdown"); break; }
+      const double ar = d3[0] / d3[2], ai = d3[1] / d3[2];
+      if ((st = S.axpby<LQCD_F32>(S.w.x32, zi, ar, ai, nullptr, 1.0))) break;
+      if ((st = S.axpby<LQCD_F32>(r32, wi, -ar, -ai, nullptr, 1.0))) break;
+      iters++;
+      if ((st = S.dot<LQCD_F32>(r32, r32, d3))) break;
+      if (std::sqrt(d3[2]) <= target) break;
+    }
+    if (st) break;
+    // x += c in FP64, then the FP64 true residual
+    k_acc64<<<fine_grid(S.m.g), MG_BLOCK, 0, S.s>>>(x, S.w.x32, S.m.g);
+    if ((st = after_launch("k_acc64"))) break;
+    if ((st = S.D64(S.w.r64, x))) break;
+    if ((st = S.axpby<LQCD_F64>(S.w.r64, b, 1.0, 0.0, nullptr, -1.0))) break;
   }
   if (S.vgraph) cudaGraphExecDestroy(S.vgraph);
   inf->iterations = iters;
