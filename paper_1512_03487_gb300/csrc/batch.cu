@@ -75,7 +75,9 @@ __device__ __forceinline__ void block_add(double v, double* sh, double* acc) {
   __syncthreads();
 }
 
-template <int P, int R, bool DAG, int EPI, bool RED>
+// RED: RED_NONE, RED_NORM (|out|^2 per instance) or RED_CG_UPDATE (out = A p is
+// not stored; x_s += alpha p, r_s -= alpha A p and |r_s|^2 per instance instead).
+template <int P, int R, bool DAG, int EPI, int RED>
 __global__ void __launch_bounds__(TILE) batch_hop_kernel(const BatchArgs A) {
   using T = typename PrecTraits<P>::real;
   if (gate_closed(A.gate)) return;
@@ -101,8 +103,12 @@ __global__ void __launch_bounds__(TILE) batch_hop_kernel(const BatchArgs A) {
       Spinor<T> res;
       hop_site<P, R, DAG, EPI>(I.g, A.use64 ? I.gauge64 : I.gauge_s, I.f[A.f_in],
                                A.f_x == BF_NONE ? nullptr : I.f[A.f_x], A.out_parity, j, c, res);
-      SpinorIO<P>::store(I.f[A.f_out], I.g.sstride, j, res);
-      if (RED) v = norm2_site(res);
+      if (RED == RED_CG_UPDATE) {
+        v = update_site_ap<vec_prec(P), P>(I.g, j, A.red.sys[k].alpha, I.f[BF_P], res, I.f[BF_XS], I.f[BF_RS]);
+      } else {
+        SpinorIO<P>::store(I.f[A.f_out], I.g.sstride, j, res);
+        if (RED == RED_NORM) v = norm2_site(res);
+      }
     }
     if (RED) block_add(v, sh, &s_acc[k]);
   }
@@ -158,22 +164,24 @@ __global__ void __launch_bounds__(TILE) batch_vec_kernel(const BatchArgs A) {
 // ------------------------------------------------------------------ launchers
 
 template <int P, int R>
-static void launch_bhop_pr(bool dag, int epi, bool red, unsigned grid, const BatchArgs& a, cudaStream_t s) {
+static void launch_bhop_pr(bool dag, int epi, int red, unsigned grid, const BatchArgs& a, cudaStream_t s) {
 #define LQCD_BHOP(DG, EP, RD) batch_hop_kernel<P, R, DG, EP, RD><<<grid, TILE, 0, s>>>(a)
   if (epi == EPI_PLAIN) {
-    if (dag) LQCD_BHOP(true, EPI_PLAIN, false);
-    else LQCD_BHOP(false, EPI_PLAIN, false);
-  } else if (red) {
-    if (dag) LQCD_BHOP(true, EPI_XPAY, true);
-    else LQCD_BHOP(false, EPI_XPAY, true);
+    if (dag) LQCD_BHOP(true, EPI_PLAIN, RED_NONE);
+    else LQCD_BHOP(false, EPI_PLAIN, RED_NONE);
+  } else if (red == RED_CG_UPDATE) {  // the last hop of M_hat^dag M_hat
+    LQCD_BHOP(true, EPI_XPAY, RED_CG_UPDATE);
+  } else if (red == RED_NORM) {
+    if (dag) LQCD_BHOP(true, EPI_XPAY, RED_NORM);
+    else LQCD_BHOP(false, EPI_XPAY, RED_NORM);
   } else {
-    if (dag) LQCD_BHOP(true, EPI_XPAY, false);
-    else LQCD_BHOP(false, EPI_XPAY, false);
+    if (dag) LQCD_BHOP(true, EPI_XPAY, RED_NONE);
+    else LQCD_BHOP(false, EPI_XPAY, RED_NONE);
   }
 #undef LQCD_BHOP
 }
 
-static int launch_bhop(int prec, int recon, bool dag, int epi, bool red, unsigned grid, const BatchArgs& a,
+static int launch_bhop(int prec, int recon, bool dag, int epi, int red, unsigned grid, const BatchArgs& a,
                        cudaStream_t s) {
   if (prec == LQCD_F64) {
     if (recon == 18) launch_bhop_pr<LQCD_F64, 18>(dag, epi, red, grid, a, s);
@@ -299,17 +307,18 @@ struct BatchSolver : CgEngine {
     a.gate = gate;
     return a;
   }
-  // out = M_hat in (dagger), through the odd temporary; optional |out|^2 reduction
+  // out = M_hat in (dagger), through the odd temporary; with red, red_mode RED_NORM
+  // reduces |out|^2 and RED_CG_UPDATE applies the CG update instead of storing out
   int schur(int f_out, int f_in, int f_tmp, bool dag, bool use64, const ReduceCtx* red, const Control* gate,
-            cudaStream_t s) {
+            cudaStream_t s, int red_mode = RED_NORM) {
     const int P = use64 ? LQCD_F64 : sloppy;
     const int R = use64 ? recon : sloppy_recon;
     BatchArgs a1 = args(f_tmp, f_in, BF_NONE, use64, LQCD_ODD, gate);
-    int st = launch_bhop(P, R, dag, EPI_PLAIN, false, grid, a1, s);
+    int st = launch_bhop(P, R, dag, EPI_PLAIN, RED_NONE, grid, a1, s);
     if (st) return st;
     BatchArgs a2 = args(f_out, f_tmp, f_in, use64, LQCD_EVEN, gate);
     if (red) a2.red = *red;
-    return launch_bhop(P, R, dag, EPI_XPAY, red != nullptr, grid, a2, s);
+    return launch_bhop(P, R, dag, EPI_XPAY, red ? red_mode : RED_NONE, grid, a2, s);
   }
   int init(cudaStream_t s) override {
     cudaError_t e = cudaMemsetAsync(base.red.counter, 0, 64, s);
@@ -318,16 +327,15 @@ struct BatchSolver : CgEngine {
     a.red = rc_init;
     return launch_bvec(BV_INIT, sloppy, grid, a, s);
   }
+  // M_hat p with |M_hat p|^2 = p^dag A p -> alpha; M_hat^dag (M_hat p) = A p whose last
+  // hop applies x_s += alpha p, r_s -= alpha A p and reduces |r_s|^2 instead of storing A p
   int head(cudaStream_t s, int cond, cudaGraphConditionalHandle h_rel) override {
     int st = schur(BF_MP, BF_P, BF_T1S, false, false, &rc_alpha, ctrl, s);
     if (st) return st;
-    if ((st = schur(BF_AP, BF_MP, BF_T1S, true, false, nullptr, ctrl, s))) return st;
-    BatchArgs a = base;
-    a.red = rc_update;
-    a.red.cond = cond;
-    a.red.h_rel = h_rel;
-    a.gate = ctrl;
-    return launch_bvec(BV_UPDATE, sloppy, grid, a, s);
+    ReduceCtx ru = rc_update;
+    ru.cond = cond;
+    ru.h_rel = h_rel;
+    return schur(BF_AP, BF_MP, BF_T1S, true, false, &ru, ctrl, s, RED_CG_UPDATE);  // BF_AP is not written
   }
   int tail(cudaStream_t s) override {
     BatchArgs a = base;
