@@ -352,7 +352,9 @@ def run_lqcd(args, world, rank, local):
         "data": "synthetic (seeded exp(0.3 i H) links, Gaussian source)",
         "config": {"workload": WORKLOAD, "lattice": list(dims), "mass": mass, "bc": list(BC),
                    "solver": f"even-odd CG on M_hat^dag M_hat, FP32 / 12-real inner, delta {DELTA[HEADLINE]}",
-                   "tol": 1e-10, "l2": "flushed before every timed step (512 MB write, then 256 MB read)",
+                   "tol": 1e-10, "tol_applies_to": "FP64 true residual of the normal equations M_hat^dag M_hat x = "
+                                                   "M_hat^dag b_hat (the full-system residual is reported beside it)",
+                   "l2": "flushed before every timed step (512 MB write, then 256 MB read)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "full_system_rel_residual": res,
         "iterations_per_step": infos[-1].iterations, "reliable_updates_per_step": infos[-1].reliable_updates,
