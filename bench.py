@@ -299,9 +299,7 @@ def run_lqcd(args, world, rank, local):
     launches = L.lqcd_launch_count() - launches0
     clk = clocks.stop()
     barrier(world)
-    max_ms = allreduce_max(total_ms, world)
-    flops_all = allreduce_sum(float(total_hops) * FLOP_PER_SITE * vh, world)
-    value = flops_all / (max_ms * 1e-3) / 1e9
+    max_ms, flops_all, value = aggregate(total_ms, float(total_hops) * FLOP_PER_SITE * vh, world)
 
     # the solve must meet the FP64 true residual of the full system (checked on the device result)
     res = full_residual(L, F, lat, op64, g64, x, b_dev, tmp)
@@ -929,9 +927,18 @@ def _allreduce(v, world, op):
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def aggregate(local_ms, local_flop, world):
+    """Whole-job figures of a replicated run: the slowest rank's time, the flops of
+    all ranks, and the aggregate GFLOP/s (all ranks' work over the slowest time)."""
+    max_ms = allreduce_max(local_ms, world)
+    flop = allreduce_sum(local_flop, world)
+    return max_ms, flop, flop / (max_ms * 1e-3) / 1e9
 
 
 def main():
