@@ -34,16 +34,23 @@ METRIC = "Dslash GFLOP/s & HBM-roofline %; mixed vs FP64 CG time to 1e-10 residu
 FLOP_PER_SITE = 1320
 BC = (1.0, 1.0, 1.0, -1.0)
 WORKLOAD = "wilson_eo_cg_24x24x24x48_m0.01_exp0.3_tol1e-10"
-# Inner (sloppy) precision of the headline solve and the reliable-update threshold per inner
-# precision. A reliable update recomputes r = b - A x with the FP64 operator, which on GB300 is
-# bound by the FP64 pipe and costs as much as ~10 FP32 iterations, so the largest drop per
-# update that the inner precision sustains wins: sweeps on this workload gave delta = 1e-5 for
-# FP32 storage (2 updates, 61 iterations) and 0.003 for FP16 storage (4 updates, 63
-# iterations; smaller deltas add iterations), and FP32 inner is the faster of the two.
-HEADLINE = 1
-DELTA = {0: 0.1, 1: 1e-5, 2: 0.003}
-PROFILE_JSON = os.path.join(ROOT, "profiles", "hop_f32r12_24x24x24x48.json")
-DSLASH_SOURCES = ["dslash_kernels.cuh", "lqcd_common.cuh", "cg_site.cuh", "dslash_launch.cuh", "dslash_f32.cu"]
+# Solver variants of the headline workload, key -> (inner storage precision, delta, delta_mid).
+# A reliable update recomputes r = b - A x with the FP64 operator, which on GB300 is bound by the
+# FP64 pipe and costs as much as ~10 FP32 iterations, so the largest drop per update that the inner
+# iteration sustains wins: sweeps on this workload gave delta = 1e-5 for FP32 storage (2 updates,
+# 61 iterations) and 0.003 for FP16 storage (4 updates, 62 iterations; smaller deltas add
+# iterations). Variant 3 keeps FP16 storage but puts FP32-arithmetic residual replacements
+# (delta_mid = 0.003) between FP64 updates at delta = 1e-5: 2 FP64 updates, 2 replacements,
+# 62 iterations, the fastest of the four (15.7 ms against 17.6 ms for FP32 storage, solve only).
+VARIANTS = {0: (0, 0.1, 0.0), 1: (1, 1e-5, 0.0), 2: (2, 0.003, 0.0), 3: (2, 1e-5, 0.003)}
+VARIANT_NAMES = {0: "fp64", 1: "mixed_fp32", 2: "mixed_fp16", 3: "mixed_fp16_three_level"}
+HEADLINE = 3
+HEADLINE_PREC = VARIANTS[HEADLINE][0]
+DELTA = {q: VARIANTS[q][1] for q in (0, 1, 2)}
+DELTA_3LVL, DELTA_MID = VARIANTS[3][1], VARIANTS[3][2]
+PREC_TAG = {1: "f32", 2: "f16"}
+PROFILE_JSON = {q: os.path.join(ROOT, "profiles", f"hop_{PREC_TAG[q]}r12_24x24x24x48.json") for q in (1, 2)}
+DSLASH_COMMON = ["dslash_kernels.cuh", "lqcd_common.cuh", "cg_site.cuh", "dslash_launch.cuh"]
 
 
 def parse_args():
@@ -66,6 +73,8 @@ def parse_args():
     ap.add_argument("--hop-shape", default=None,
                     help="hops mode: run only this shape (f32r12_24x24x24x48, f16r12_24x24x24x48, "
                          "dwf_f32r12_16x4_ls16, f32r12_32x4_12rhs)")
+    ap.add_argument("--hop-prec", type=int, choices=[1, 2], default=HEADLINE_PREC,
+                    help="storage precision of the hop timed by --mode hop (1 FP32, 2 FP16)")
     ap.add_argument("--mode", choices=["full", "step", "hop", "hops"], default="full",
                     help="step: only the timed solves; hop: only the dominant kernel's roofline loop; "
                          "hops: the three hop shapes (profiling)")
@@ -188,9 +197,10 @@ def threads_used():
 
 # ------------------------------------------------------------------ lqcd arm
 
-def dslash_sources_hash():
+def dslash_sources_hash(prec):
+    """Hash of the sources that make the hop kernel of one storage precision."""
     h = hashlib.sha256()
-    for f in DSLASH_SOURCES:
+    for f in DSLASH_COMMON + [f"dslash_{PREC_TAG[prec]}.cu"]:
         with open(os.path.join(ROOT, "paper_1512_03487_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -239,18 +249,18 @@ def run_lqcd(args, world, rank, local):
     gs = {p: F.empty(L.lqcd_gauge_bytes(lat, p, 12)) for p in (L.LQCD_F32, L.LQCD_F16)}
     bfull = F.empty(L.lqcd_spinor_bytes(lat, L.LQCD_F64, L.LQCD_FULL))
     bhat = F.empty(L.lqcd_spinor_bytes(lat, L.LQCD_F64, L.LQCD_EVEN))
-    src = F.empty(L.lqcd_spinor_bytes(lat, L.LQCD_F64, L.LQCD_EVEN))
     x = F.empty(L.lqcd_spinor_bytes(lat, L.LQCD_F64, L.LQCD_FULL))
     tmp = F.empty(L.lqcd_operator_workspace_bytes(lat, op64, L.LQCD_EVEN))
-    prms = {p: L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=p, sloppy_recon=12 if p else 18,
-                               delta=DELTA[p], check_interval=args.check_interval,
+    prms = {k: L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=q, sloppy_recon=12 if q else 18,
+                               delta=d, delta_mid=dm, check_interval=args.check_interval,
                                use_graph=0 if args.no_graph else 1)
-            for p in (0, 1, 2)}
-    ws = F.empty(max(L.lqcd_cg_workspace_bytes(lat, op64, prms[p], L.LQCD_EVEN) for p in (0, 1, 2)))
+            for k, (q, d, dm) in VARIANTS.items()}
+    ws = F.empty(max(L.lqcd_cg_workspace_bytes(lat, op64, prms[k], L.LQCD_EVEN) for k in prms))
     flush = L2Flush(dev)
 
-    def step(sloppy):
+    def step(key):
         """One solve of D_W x = b from the resident FP64 inputs; returns hops executed."""
+        sloppy = prms[key].sloppy_prec
         L.lqcd_gauge_pack(g64, L.LQCD_F64, 18, U_dev, lat)
         gsl = g64
         if sloppy:
@@ -258,10 +268,10 @@ def run_lqcd(args, world, rank, local):
             L.lqcd_gauge_pack(gsl, sloppy, 12, U_dev, lat)
         L.lqcd_spinor_pack(bfull, L.LQCD_F64, L.LQCD_FULL, b_dev, lat)
         L.lqcd_eo_prepare(bhat, bfull, g64, lat, op64, tmp)
-        L.lqcd_M(src, bhat, g64, lat, op64, L.LQCD_EVEN, 1, tmp)
-        info = L.lqcd_cg_solve(x, src, g64, gsl, lat, op64, prms[sloppy], L.LQCD_EVEN, ws)
+        info = L.lqcd_cgnr_solve(x, bhat, g64, gsl, lat, op64, prms[key], L.LQCD_EVEN, ws)
         L.lqcd_eo_reconstruct(x, bfull, g64, lat, op64, tmp)
-        return 1 + 2 + 4 * (info.iterations + info.reliable_updates) + 1, info
+        hops = 1 + 2 + 4 * (info.iterations + info.reliable_updates + info.residual_replacements) + 1
+        return hops, info
 
     def timed(fn, *a):
         flush()
@@ -276,13 +286,13 @@ def run_lqcd(args, world, rank, local):
 
     if args.mode == "hop":
         # profiling mode: only the dominant kernel's roofline loop
-        L.lqcd_gauge_pack(gs[HEADLINE], HEADLINE, 12, U_dev, lat)
-        roof = hop_roofline(L, F, lat, gs[HEADLINE], flush, stream, vh, launches=args.steps)
+        L.lqcd_gauge_pack(gs[args.hop_prec], args.hop_prec, 12, U_dev, lat)
+        roof = hop_roofline(L, F, lat, gs[args.hop_prec], args.hop_prec, flush, stream, vh, launches=args.steps)
         if rank == 0:
             print(json.dumps({"mode": "hop", "roofline": roof}), flush=True)
         return
 
-    # ---- headline: FP32-inner mixed precision solve
+    # ---- headline: the fastest mixed precision solve (FP16 storage, three levels)
     for _ in range(args.warmup):
         step(HEADLINE)
     barrier(world)
@@ -313,32 +323,38 @@ def run_lqcd(args, world, rank, local):
 
     # ---- mixed vs FP64 comparison (one timed solve each after one warm-up)
     cgcmp = {}
-    for name, p in (("fp64", 0), ("mixed_fp32", 1), ("mixed_fp16", 2)):
+    for p, name in VARIANT_NAMES.items():
         if p != HEADLINE:
             step(p)
         ms, (hops, info) = timed(step, p)
         cgcmp[name] = {"ms": round(ms, 3), "iterations": info.iterations,
-                       "reliable_updates": info.reliable_updates, "delta": DELTA[p],
+                       "reliable_updates": info.reliable_updates, "delta": prms[p].delta,
                        "true_rel_residual_normal_eq": info.true_rel_residual,
                        "dslash_gflops": round(hops * FLOP_PER_SITE * vh / (ms * 1e-3) / 1e9, 1)}
-    cgcmp["speedup_fp16_vs_fp64"] = round(cgcmp["fp64"]["ms"] / cgcmp["mixed_fp16"]["ms"], 2)
-    cgcmp["speedup_fp32_vs_fp64"] = round(cgcmp["fp64"]["ms"] / cgcmp["mixed_fp32"]["ms"], 2)
+        if p == 3:
+            cgcmp[name].update({"delta_mid": prms[p].delta_mid,
+                                "fp32_replacements": info.residual_replacements})
+    for name in ("mixed_fp32", "mixed_fp16", "mixed_fp16_three_level"):
+        cgcmp["speedup_" + name[6:] + "_vs_fp64"] = round(cgcmp["fp64"]["ms"] / cgcmp[name]["ms"], 2)
 
-    # ---- roofline of the dominant kernel: the inner hop (FP32, 12-real links), one checkerboard;
-    # and of the FP64 hop of the reliable updates, bound by the FP64 pipe
-    roof = hop_roofline(L, F, lat, gs[HEADLINE], flush, stream, vh)
+    # ---- roofline of the dominant kernel: the inner hop (12-real links, the headline's storage
+    # precision), one checkerboard; the FP32 storage hop beside it; and the FP64 hop of the
+    # reliable updates, bound by the FP64 pipe
+    roof = hop_roofline(L, F, lat, gs[HEADLINE_PREC], HEADLINE_PREC, flush, stream, vh)
+    L.lqcd_gauge_pack(gs[1], 1, 12, U_dev, lat)
+    roof32 = hop_roofline(L, F, lat, gs[1], 1, flush, stream, vh)
     roof64 = fp64_hop_roofline(L, F, lat, g64, flush, stream, vh)
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(L, F, lat, op64, U, b, prms[HEADLINE], ws, tmp, x, gs[HEADLINE], g64, bfull, bhat, src,
+        e2e = run_e2e(L, F, lat, op64, U, b, prms[HEADLINE], ws, tmp, x, gs[HEADLINE_PREC], g64, bfull, bhat,
                       flush, stream, vh, args, world)
 
     # ---- the other hot-path workloads (domain wall, multi-RHS, uneven batch, force)
     extras = None
     if not args.no_extras:
-        del U_dev, g64, gs, ws, tmp, x, bfull, bhat, src
+        del U_dev, g64, gs, ws, tmp, x, bfull, bhat
         torch.cuda.empty_cache()
         extras = run_extras(L, F, flush, stream)
 
@@ -346,18 +362,24 @@ def run_lqcd(args, world, rank, local):
         "metric": METRIC, "value": round(value, 1), "unit": "GFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 inner iteration (f32 storage, 12-real links), f64 reliable updates",
+        "dtype": "f32 arithmetic on f16 storage (per-site norm, 12-real links) in the inner iteration, "
+                 "f32-arithmetic residual replacements, f64 reliable updates and true residual",
         "data": "synthetic (seeded exp(0.3 i H) links, Gaussian source)",
         "config": {"workload": WORKLOAD, "lattice": list(dims), "mass": mass, "bc": list(BC),
-                   "solver": f"even-odd CG on M_hat^dag M_hat, FP32 / 12-real inner, delta {DELTA[HEADLINE]}",
-                   "tol": 1e-10, "tol_applies_to": "FP64 true residual of the normal equations M_hat^dag M_hat x = "
-                                                   "M_hat^dag b_hat (the full-system residual is reported beside it)",
+                   "solver": "even-odd CGNR (CG on M_hat^dag M_hat x = M_hat^dag b_hat), FP16-storage / 12-real "
+                             f"inner iteration, FP32-arithmetic residual replacements at delta_mid {DELTA_MID}, FP64 "
+                             f"reliable updates r = M_hat^dag (b_hat - M_hat x) at delta {DELTA_3LVL}",
+                   "tol": 1e-10, "tol_applies_to": "FP64 true residual of the normal equations, ||M_hat^dag (b_hat - "
+                                                   "M_hat x)|| / ||M_hat^dag b_hat|| (the full-system residual is "
+                                                   "reported beside it)",
                    "l2": "flushed before every timed step (512 MB write, then 256 MB read)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "full_system_rel_residual": res,
         "iterations_per_step": infos[-1].iterations, "reliable_updates_per_step": infos[-1].reliable_updates,
+        "fp32_replacements_per_step": infos[-1].residual_replacements,
         "cg": cgcmp,
         "roofline": roof,
+        "roofline_fp32_hop": roof32,
         "roofline_fp64_hop": roof64,
         "gpu_launches": int(launches),
         "clocks": clk,
@@ -411,21 +433,21 @@ def _cold_hop_seconds(L, F, lat, g, prec, recon, flush, stream, launches):
     return float(np.mean(times)) * 1e-3
 
 
-def hop_roofline(L, F, lat, gsl, flush, stream, vh, launches=20):
-    t = _cold_hop_seconds(L, F, lat, gsl, HEADLINE, 12, flush, stream, launches)
+def hop_roofline(L, F, lat, gsl, prec, flush, stream, vh, launches=20):
+    t = _cold_hop_seconds(L, F, lat, gsl, prec, 12, flush, stream, launches)
     # 8 links of 12 reals + input and output spinor, in the inner precision
-    bytes_per_site = {1: 8 * 48 + 96 + 96, 2: 8 * 24 + 52 + 52}[HEADLINE]
+    bytes_per_site = {1: 8 * 48 + 96 + 96, 2: 8 * 24 + 52 + 52}[prec]
     achieved = bytes_per_site * vh / t / 1e9
     peak, peak_src = measured_peak()
     traffic = None
     try:
-        with open(PROFILE_JSON) as fh:
+        with open(PROFILE_JSON[prec]) as fh:
             prof = json.load(fh)
-        if prof.get("source_hash") == dslash_sources_hash() and list(prof.get("lattice", [])) == list(lat.dims):
+        if prof.get("source_hash") == dslash_sources_hash(prec) and list(prof.get("lattice", [])) == list(lat.dims):
             traffic = prof.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
-    name = {1: "F32", 2: "F16"}[HEADLINE]
+    name = {1: "F32", 2: "F16"}[prec]
     return {"bound": "hbm", "kernel": f"hop_kernel<{name}, recon 12> (one checkerboard, cold L2)",
             "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
             "peak_source": peak_src, "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_site * vh,
@@ -451,7 +473,7 @@ def measured_peak():
         return 6800.0, "fallback 6.8 TB/s (of fallback)"
 
 
-def run_e2e(L, F, lat, op64, U, b, prm, ws, tmp, x, gsl, g64, bfull, bhat, src, flush, stream, vh, args, world):
+def run_e2e(L, F, lat, op64, U, b, prm, ws, tmp, x, gsl, g64, bfull, bhat, flush, stream, vh, args, world):
     """Same solve through the C ABI from pinned host buffers: H2D of the FP64
     gauge field and source, pack, solve, reconstruct, D2H of the solution."""
     import torch
@@ -462,14 +484,13 @@ def run_e2e(L, F, lat, op64, U, b, prm, ws, tmp, x, gsl, g64, bfull, bhat, src, 
 
     def e2e_step():
         L.lqcd_gauge_upload(g64, L.LQCD_F64, 18, U_h, staging, lat)
-        L.lqcd_gauge_pack(gsl, HEADLINE, 12, staging, lat)
+        L.lqcd_gauge_pack(gsl, HEADLINE_PREC, 12, staging, lat)
         L.lqcd_spinor_upload(bfull, L.LQCD_F64, L.LQCD_FULL, b_h, staging, lat)
         L.lqcd_eo_prepare(bhat, bfull, g64, lat, op64, tmp)
-        L.lqcd_M(src, bhat, g64, lat, op64, L.LQCD_EVEN, 1, tmp)
-        info = L.lqcd_cg_solve(x, src, g64, gsl, lat, op64, prm, L.LQCD_EVEN, ws)
+        info = L.lqcd_cgnr_solve(x, bhat, g64, gsl, lat, op64, prm, L.LQCD_EVEN, ws)
         L.lqcd_eo_reconstruct(x, bfull, g64, lat, op64, tmp)
         L.lqcd_spinor_download(x_h, x, L.LQCD_F64, L.LQCD_FULL, staging, lat)
-        return 1 + 2 + 4 * (info.iterations + info.reliable_updates) + 1
+        return 1 + 2 + 4 * (info.iterations + info.reliable_updates + info.residual_replacements) + 1
 
     for _ in range(max(1, args.warmup // 2)):
         e2e_step()
@@ -550,19 +571,22 @@ def run_extras(L, F, flush, stream):
     del b
     tmp = F.empty(L.lqcd_operator_workspace_bytes(lat, op, 0))
     bhat = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
-    src = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
     x = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
     prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=12, delta=DELTA[1],
                           check_interval=64)
-    ws = F.empty(L.lqcd_cg_workspace_bytes(lat, op, prm, 0))
+    prm3 = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=2, sloppy_recon=12, delta=DELTA_3LVL,
+                           delta_mid=DELTA_MID, check_interval=64)
+    g16 = F.gauge_to_device(U, lat, 2, 12)
+    ws = F.empty(max(L.lqcd_cg_workspace_bytes(lat, op, q, 0) for q in (prm, prm3)))
 
-    def dwf_solve():
+    def dwf_solve(p=prm, gs=g32):
         L.lqcd_eo_prepare(bhat, bd, g64, lat, op, tmp)
-        L.lqcd_M(src, bhat, g64, lat, op, L.LQCD_EVEN, 1, tmp)
-        info = L.lqcd_cg_solve(x, src, g64, g32, lat, op, prm, L.LQCD_EVEN, ws)
+        info = L.lqcd_cgnr_solve(x, bhat, g64, gs, lat, op, p, L.LQCD_EVEN, ws)
         L.lqcd_eo_reconstruct(x, bd, g64, lat, op, tmp)
         return info
 
+    dwf_solve(prm3, g16)
+    ms3, info3 = _events_time(lambda: dwf_solve(prm3, g16), stream, flush)
     dwf_solve()
     ms, info = _events_time(dwf_solve, stream, flush)
     dx = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
@@ -578,12 +602,17 @@ def run_extras(L, F, flush, stream):
         "ms": round(ms, 3), "iterations": info.iterations, "reliable_updates": info.reliable_updates,
         "full_system_rel_residual": res,
         "dslash_gflops_in_solve": round(hops * FLOP_PER_SITE * 16 ** 4 // 2 * Ls / (ms * 1e-3) / 1e9, 1),
-        "hop_f32r12_ls16": _hop_gbs(L, F, lat, 1, 12, 8 * 48 / Ls + 96 + 96, flush, stream, kind=L.LQCD_DWF)}
-    del g64, g32, bd, tmp, bhat, src, x, ws, dx, a, bb
+        "hop_f32r12_ls16": _hop_gbs(L, F, lat, 1, 12, 8 * 48 / Ls + 96 + 96, flush, stream, kind=L.LQCD_DWF),
+        "fp16_inner_three_level": {"ms": round(ms3, 3), "iterations": info3.iterations,
+                                   "reliable_updates": info3.reliable_updates,
+                                   "fp32_replacements": info3.residual_replacements,
+                                   "true_rel_residual_normal_eq": info3.true_rel_residual}}
+    del g64, g32, g16, bd, tmp, bhat, x, ws, dx, a, bb
     torch.cuda.empty_cache()
 
     # 32^4 with 12 right-hand sides sharing the links, m = 0.01, mixed CG per RHS to 1e-10:
-    # FP32 inner (delta 1e-5, the faster), FP16 inner (delta 0.003), and block CG with FP32 inner
+    # FP32 inner (delta 1e-5), FP16 inner (delta 0.003), FP16 inner with FP32-arithmetic replacements
+    # (three levels), and block CG with FP32 inner
     dims, nr = (32, 32, 32, 32), 12
     U = gauge_field(dims, "haar", config_seed(3, 0))
     lat = L.lattice(dims, n5=nr, bc=BC)
@@ -597,17 +626,21 @@ def run_extras(L, F, flush, stream):
     x = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
     prm = {q: L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=q, sloppy_recon=12, delta=DELTA[q],
                               check_interval=64) for q in (1, 2)}
-    ws = F.empty(max(L.lqcd_cg_workspace_bytes(lat, op, prm[q], 0) for q in (1, 2)))
+    prm[3] = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=2, sloppy_recon=12, delta=DELTA_3LVL,
+                             delta_mid=DELTA_MID, check_interval=64)
+    ws = F.empty(max(L.lqcd_cg_workspace_bytes(lat, op, prm[q], 0) for q in prm))
     vh = 32 ** 4 // 2
     mr = {}
-    for q, name in ((1, "fp32_inner"), (2, "fp16_inner")):
-        L.lqcd_cg_solve(x, be, g64, gsl[q], lat, op, prm[q], 0, ws)
-        ms, info = _events_time(lambda: L.lqcd_cg_solve(x, be, g64, gsl[q], lat, op, prm[q], 0, ws), stream, flush)
+    for q, name in ((1, "fp32_inner"), (2, "fp16_inner"), (3, "fp16_inner_three_level")):
+        g = gsl[prm[q].sloppy_prec]
+        L.lqcd_cg_solve(x, be, g64, g, lat, op, prm[q], 0, ws)
+        ms, info = _events_time(lambda: L.lqcd_cg_solve(x, be, g64, g, lat, op, prm[q], 0, ws), stream, flush)
+        nop = info.iterations + info.reliable_updates + info.residual_replacements
         mr[name] = {
             "ms": round(ms, 3), "iterations": info.iterations, "reliable_updates": info.reliable_updates,
-            "delta": DELTA[q], "max_true_rel_residual_normal_eq": info.true_rel_residual,
-            "dslash_gflops_in_solve": round(4 * (info.iterations + info.reliable_updates) * FLOP_PER_SITE * vh * nr
-                                            / (ms * 1e-3) / 1e9, 1)}
+            "fp32_replacements": info.residual_replacements, "delta": prm[q].delta, "delta_mid": prm[q].delta_mid,
+            "max_true_rel_residual_normal_eq": info.true_rel_residual,
+            "dslash_gflops_in_solve": round(4 * nop * FLOP_PER_SITE * vh * nr / (ms * 1e-3) / 1e9, 1)}
     wsb = F.empty(L.lqcd_block_cg_workspace_bytes(lat, op, prm[1]))
     L.lqcd_block_cg_solve(x, be, g64, gsl[1], lat, op, prm[1], wsb)
     msb, infb = _events_time(lambda: L.lqcd_block_cg_solve(x, be, g64, gsl[1], lat, op, prm[1], wsb), stream, flush)
@@ -771,15 +804,13 @@ def gparity_bench(L, F, flush, stream):
     del U
     tmp = F.empty(L.lqcd_operator_workspace_bytes(lat, op, 0))
     bhat = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
-    src = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
     x = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
     prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=12, delta=DELTA[1], check_interval=64)
     ws = F.empty(L.lqcd_cg_workspace_bytes(lat, op, prm, 0))
 
     def solve():
         L.lqcd_eo_prepare(bhat, bd, g64, lat, op, tmp)
-        L.lqcd_M(src, bhat, g64, lat, op, L.LQCD_EVEN, 1, tmp)
-        info = L.lqcd_cg_solve(x, src, g64, g32, lat, op, prm, L.LQCD_EVEN, ws)
+        info = L.lqcd_cgnr_solve(x, bhat, g64, g32, lat, op, prm, L.LQCD_EVEN, ws)
         L.lqcd_eo_reconstruct(x, bd, g64, lat, op, tmp)
         return info
 

@@ -122,6 +122,8 @@ typedef struct {
     int check_interval;    /* iterations per captured chunk between host checks (0 = 16) */
     int use_graph;         /* 1: replay chunks as a captured CUDA graph; 0: plain launches */
     double timeout_ms;     /* wall-clock limit; 0 = none */
+    double delta_mid;      /* lqcd_cg_solve with sloppy_prec LQCD_F16 only (0 = off): threshold of the
+                              intermediate FP32-arithmetic residual replacement (e.g. 0.003); see below */
 } lqcd_solver_params;
 
 typedef struct {
@@ -130,6 +132,7 @@ typedef struct {
     double true_rel_residual; /* max over RHS of ||b - A x|| / ||b|| in FP64 at exit */
     double time_ms;           /* wall time of the solve */
     int status;               /* same as the return value */
+    int residual_replacements; /* intermediate FP32-arithmetic replacements (delta_mid) */
 } lqcd_solve_info;
 
 /* ---------------------------------------------------------------- library */
@@ -238,6 +241,15 @@ int lqcd_eo_reconstruct(void* x_full_dev, const void* b_full_dev, const void* ga
  * in FP64; whenever ||r|| falls below delta times its maximum since the last
  * update, or below tol, r = b - A x is recomputed in FP64. Exit only when
  * every system's FP64 true residual is <= tol. Synchronises the stream.
+ * Three levels (sloppy_prec LQCD_F16, delta_mid > 0): FP16 storage needs a
+ * fresh residual every few decades, so between FP64 updates the iterated
+ * residual is replaced by r - A x_s whenever it falls below delta_mid times
+ * its maximum since the last replacement, with r the residual of the last
+ * FP64 update, x_s the sloppy solution since then, and A applied with FP32
+ * arithmetic to gauge_dev (no extra field); FP64 updates then follow delta,
+ * which this allows down to about 1e-5. The solve's result and exit test are
+ * unchanged (FP64 true residual); only the update schedule differs. Ignored
+ * by the block and batched solvers.
  * workspace_dev: lqcd_cg_workspace_bytes() bytes, 256-byte aligned. */
 size_t lqcd_cg_workspace_bytes(const lqcd_lattice* lat, const lqcd_operator* op,
                                const lqcd_solver_params* params, int subset);
@@ -246,6 +258,22 @@ int lqcd_cg_solve(void* x_dev, const void* b_dev, const void* gauge_dev,
                   const lqcd_operator* op, const lqcd_solver_params* params, int subset,
                   lqcd_solve_info* info, void* workspace_dev, size_t workspace_bytes,
                   void* stream);
+
+/* CGNR: solves M x = b (subset LQCD_FULL) or M_hat x = b (LQCD_EVEN, b = b_hat
+ * of lqcd_eo_prepare) by CG on the normal equations M^dag M x = M^dag b,
+ * without forming M^dag b in FP64: the starting residual M^dag b is applied in
+ * the inner iteration's arithmetic (FP32 arithmetic on gauge_dev for a mixed
+ * solve, FP64 for a plain one), and every reliable update recomputes
+ * r = M^dag (b - M x) in FP64. The exit test is the FP64 true residual of the
+ * normal equations, ||M^dag (b - M x)|| / ||M^dag b|| <= tol, the same
+ * quantity lqcd_cg_solve tests for b' = M^dag b; the norm of M^dag b in the
+ * denominator carries the start's relative error (about 1e-7 in FP32). Saves
+ * the two FP64 hops of forming M^dag b. Arguments, workspace
+ * (lqcd_cg_workspace_bytes), delta_mid and the rest as lqcd_cg_solve. */
+int lqcd_cgnr_solve(void* x_dev, const void* b_dev, const void* gauge_dev, const void* gauge_sloppy_dev,
+                    const lqcd_lattice* lat, const lqcd_operator* op, const lqcd_solver_params* params,
+                    int subset, lqcd_solve_info* info, void* workspace_dev, size_t workspace_bytes,
+                    void* stream);
 
 /* Block CG (O'Leary 1980) for the n5 <= 16 right-hand sides of a Wilson
  * multi-RHS field (subset LQCD_EVEN: M_hat^dag M_hat X = B): one block Krylov

@@ -40,12 +40,12 @@ class lqcd_operator(C.Structure):
 class lqcd_solver_params(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxiter", C.c_int), ("sloppy_prec", C.c_int),
                 ("sloppy_recon", C.c_int), ("delta", C.c_double), ("check_interval", C.c_int),
-                ("use_graph", C.c_int), ("timeout_ms", C.c_double)]
+                ("use_graph", C.c_int), ("timeout_ms", C.c_double), ("delta_mid", C.c_double)]
 
 
 class lqcd_solve_info(C.Structure):
     _fields_ = [("iterations", C.c_int), ("reliable_updates", C.c_int), ("true_rel_residual", C.c_double),
-                ("time_ms", C.c_double), ("status", C.c_int)]
+                ("time_ms", C.c_double), ("status", C.c_int), ("residual_replacements", C.c_int)]
 
 
 class lqcd_batch_item(C.Structure):
@@ -100,6 +100,7 @@ SIGNATURES = {
     "lqcd_eo_reconstruct": (_I, [_P, _P, _P, _LAT, _OP, _P, _P]),
     "lqcd_cg_workspace_bytes": (_SZ, [_LAT, _OP, _PRM, _I]),
     "lqcd_cg_solve": (_I, [_P, _P, _P, _P, _LAT, _OP, _PRM, _I, _INFO, _P, _SZ, _P]),
+    "lqcd_cgnr_solve": (_I, [_P, _P, _P, _P, _LAT, _OP, _PRM, _I, _INFO, _P, _SZ, _P]),
     "lqcd_force": (_I, [_P, _P, _P, _P, _LAT, _OP, _I, _P]),
     "lqcd_colour_matrix_bytes": (_SZ, [_LAT, _I]),
     "lqcd_colour_matrix_pack": (_I, [_P, _I, _P, _LAT, _P]),

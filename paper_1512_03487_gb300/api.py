@@ -71,10 +71,10 @@ def operator(kind: int = LQCD_WILSON, mass: float = 0.0, M5: float = 1.8, mf: fl
 
 def solver_params(tol: float = 1e-10, maxiter: int = 10000, sloppy_prec: int = LQCD_F64,
                   sloppy_recon: int = 18, delta: float = 0.1, check_interval: int = 16,
-                  use_graph: int = 1, timeout_ms: float = 0.0) -> lqcd_solver_params:
+                  use_graph: int = 1, timeout_ms: float = 0.0, delta_mid: float = 0.0) -> lqcd_solver_params:
     return lqcd_solver_params(tol=tol, maxiter=maxiter, sloppy_prec=sloppy_prec, sloppy_recon=sloppy_recon,
                               delta=delta, check_interval=check_interval, use_graph=use_graph,
-                              timeout_ms=timeout_ms)
+                              timeout_ms=timeout_ms, delta_mid=delta_mid)
 
 
 # ------------------------------------------------------------------ library
@@ -184,6 +184,17 @@ def lqcd_cg_solve(x, b, gauge, gauge_sloppy, lat, op, params, subset, workspace,
     nbytes = workspace.numel() * workspace.element_size()
     st = lib.lqcd_cg_solve(_ptr(x), _ptr(b), _ptr(gauge), _ptr(gauge_sloppy), C.byref(lat), C.byref(op),
                            C.byref(params), subset, C.byref(info), _ptr(workspace), nbytes, _stream(stream))
+    if raise_on_error:
+        _check(st)
+    return info
+
+
+def lqcd_cgnr_solve(x, b, gauge, gauge_sloppy, lat, op, params, subset, workspace, stream=None,
+                    raise_on_error=True) -> lqcd_solve_info:
+    info = lqcd_solve_info()
+    nbytes = workspace.numel() * workspace.element_size()
+    st = lib.lqcd_cgnr_solve(_ptr(x), _ptr(b), _ptr(gauge), _ptr(gauge_sloppy), C.byref(lat), C.byref(op),
+                             C.byref(params), subset, C.byref(info), _ptr(workspace), nbytes, _stream(stream))
     if raise_on_error:
         _check(st)
     return info

@@ -329,7 +329,7 @@ struct BatchSolver : CgEngine {
   }
   // M_hat p with |M_hat p|^2 = p^dag A p -> alpha; M_hat^dag (M_hat p) = A p whose last
   // hop applies x_s += alpha p, r_s -= alpha A p and reduces |r_s|^2 instead of storing A p
-  int head(cudaStream_t s, int cond, cudaGraphConditionalHandle h_rel) override {
+  int head(cudaStream_t s, int cond, cudaGraphConditionalHandle h_rel, cudaGraphConditionalHandle) override {
     int st = schur(BF_MP, BF_P, BF_T1S, false, false, &rc_alpha, ctrl, s);
     if (st) return st;
     ReduceCtx ru = rc_update;

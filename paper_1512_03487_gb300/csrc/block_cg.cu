@@ -277,8 +277,10 @@ __global__ void __launch_bounds__(GRAM_BLOCK) k_gram(const BlockArgs a) {
     }
     __syncthreads();
   }
-  if (tid < NN) a.partials[(int64_t)blockIdx.x * NN + tid] = mk(accr, acci);
-  __threadfence();
+  if (tid < NN) {
+    a.partials[(int64_t)blockIdx.x * NN + tid] = mk(accr, acci);
+    __threadfence();  // the writers alone fence, before the ticket below
+  }
   __syncthreads();
   if (tid == 0) is_last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
   __syncthreads();
@@ -485,7 +487,7 @@ struct BlockSolver : CgEngine {
     return (unsigned)((g.Vh + spb - 1) / spb);
   }
   int init(cudaStream_t s) override;
-  int head(cudaStream_t s, int cond, cudaGraphConditionalHandle h_rel) override;
+  int head(cudaStream_t s, int cond, cudaGraphConditionalHandle h_rel, cudaGraphConditionalHandle) override;
   int tail(cudaStream_t s) override;
   int reliable(cudaStream_t s) override;
 };
@@ -523,7 +525,7 @@ int BlockSolver::init(cudaStream_t s) {
   return gram(LQCD_F64, LQCD_F64, args(BF_S_INIT, w.r64, w.r64, nullptr), s);
 }
 
-int BlockSolver::head(cudaStream_t s, int cond, cudaGraphConditionalHandle h_rel) {
+int BlockSolver::head(cudaStream_t s, int cond, cudaGraphConditionalHandle h_rel, cudaGraphConditionalHandle) {
   OpCtx cs{g, ops, gauge_s};
   int st = op_apply(cs, w.mp, w.p, LQCD_EVEN, 0, w.t1s, nullptr, nullptr, ctrl, s);
   if (st) return st;

@@ -10,6 +10,15 @@
 // its maximum since the last update (or below the tolerance) the residual
 // r = b - A x is recomputed with the FP64 operator.
 //
+// With FP16 storage a third level sits between the two (delta_mid > 0): FP16
+// needs a fresh residual every two to three decades, and on GB300 an FP64
+// recomputation costs as much as ten FP32 iterations. So whenever |r_s| falls
+// below delta_mid times its maximum since the last replacement, the iterated
+// residual is replaced by r - A x_s, with r the residual of the last FP64
+// update and A x_s applied with FP32 arithmetic to the FP64 links (accurate
+// to about 1e-7 of |r|); the FP64 updates then only follow delta, which FP32
+// accuracy allows to be as small as about 1e-5.
+//
 // Every scalar (alpha, beta, the convergence and update decisions) lives on
 // the device and is produced by the last block of the reducing kernel, so an
 // iteration is a fixed sequence of launches with no host round trip:
@@ -17,6 +26,10 @@
 //   Ap = M^dag Mp
 //   x_s += alpha p, r_s -= alpha Ap   (|r_s|^2 -> beta, or pause)
 //   p = r_s + beta p
+// CGNR (lqcd_cgnr_solve) runs the same iteration for M x = b: r_0 = M^dag b is
+// applied in the inner arithmetic and each reliable update recomputes
+// r = M^dag (b - M x) in FP64, so M^dag b is never formed in FP64.
+//
 // A chunk of such iterations is captured once as a CUDA graph and replayed;
 // kernels return immediately once the control block is paused, so the host
 // only looks at the control block between chunks.
@@ -38,6 +51,7 @@ struct VecArgs {
   const double* b64;  // FP64 source
   double* r64;        // FP64 residual
   const double* ax64; // FP64 A x
+  const void* ax32;   // FP32 A x_s of the intermediate replacement (FP32 field)
   void* xs;           // sloppy-vector solution increment (VF)
   void* rs;           // sloppy-vector residual (VF)
   void* p;            // search direction (SF)
@@ -101,6 +115,44 @@ __global__ void __launch_bounds__(BLAS_BLOCK) k_residual(VecArgs a) {
   if (vec_site(a, parity, j, first))
     red = residual_site<VF>(a.g, j, PAR_PTR(a.b64, a.hb64), PAR_PTR(a.ax64, a.hb64), PAR_PTR(a.r64, a.hb64),
                             PAR_PTR(a.rs, a.hbv));
+  block_reduce_finalize<BLAS_BLOCK>(red, first, a.red);
+}
+// dst = src between formats (the CGNR start: M^dag b in FP32 arithmetic)
+template <int DP, int SP>
+__global__ void __launch_bounds__(BLAS_BLOCK) k_copy_field(VecArgs a, void* dst, const void* src) {
+  int parity;
+  int64_t j, first;
+  if (!vec_site(a, parity, j, first)) return;
+  const int64_t hd = parity * (int64_t)cb_spinor_bytes(a.g, DP), hs = parity * (int64_t)cb_spinor_bytes(a.g, SP);
+  Spinor<typename PrecTraits<SP>::real> v;
+  SpinorIO<SP>::load(static_cast<const char*>(src) + hs, a.g.sstride, j, v);
+  Spinor<typename PrecTraits<DP>::real> w;
+  convert(v, w);
+  SpinorIO<DP>::store(static_cast<char*>(dst) + hd, a.g.sstride, j, w);
+}
+
+// out = b - mx in FP64 (CGNR reliable update: b - M x; out may alias mx)
+__global__ void __launch_bounds__(BLAS_BLOCK) k_b_minus(VecArgs a, double* out, const double* mx) {
+  int parity;
+  int64_t j, first;
+  if (!vec_site(a, parity, j, first)) return;
+  const int64_t h = parity * a.hb64;
+  Spinor<double> b, m;
+  SpinorIO<LQCD_F64>::load(reinterpret_cast<const char*>(a.b64) + h, a.g.sstride, j, b);
+  SpinorIO<LQCD_F64>::load(reinterpret_cast<const char*>(mx) + h, a.g.sstride, j, m);
+#pragma unroll
+  for (int k = 0; k < 12; k++) b.v[k] = b.v[k] - m.v[k];
+  SpinorIO<LQCD_F64>::store(reinterpret_cast<char*>(out) + h, a.g.sstride, j, b);
+}
+
+// r_s = r - A x_s (FP32 arithmetic); |r_s|^2 -> beta, resume (FIN_MID)
+template <int VF>
+__global__ void __launch_bounds__(BLAS_BLOCK) k_mid_residual(VecArgs a) {
+  int parity;
+  int64_t j, first;
+  double red = 0.0;
+  if (vec_site(a, parity, j, first))
+    red = mid_residual_site<VF>(a.g, j, PAR_PTR(a.r64, a.hb64), PAR_PTR(a.ax32, a.hbv), PAR_PTR(a.rs, a.hbv));
   block_reduce_finalize<BLAS_BLOCK>(red, first, a.red);
 }
 #undef PAR_PTR
@@ -180,12 +232,13 @@ static int validate(const lqcd_lattice* lat, const lqcd_operator* op, const lqcd
   if (op->gparity && p->sloppy_prec == LQCD_F16) return fail(LQCD_ERR_UNSUPPORTED, "cg: G-parity with FP16 inner");
   if (!(p->tol > 0.0) || p->maxiter < 1) return fail(LQCD_ERR_ARG, "cg: tol must be > 0 and maxiter >= 1");
   if (p->delta < 0.0 || p->delta >= 1.0) return fail(LQCD_ERR_ARG, "cg: delta must be in [0, 1)");
+  if (!(p->delta_mid >= 0.0 && p->delta_mid < 1.0)) return fail(LQCD_ERR_ARG, "cg: delta_mid must be in [0, 1)");
   if (subset != LQCD_EVEN && subset != LQCD_FULL) return fail(LQCD_ERR_ARG, "cg: subset must be EVEN or FULL");
   return LQCD_OK;
 }
 
 // Launch helpers for the (VF, SF) instantiations.
-enum VecKernel { VK_INIT, VK_PUPDATE, VK_ACCUM, VK_RESIDUAL };
+enum VecKernel { VK_INIT, VK_PUPDATE, VK_ACCUM, VK_RESIDUAL, VK_MID_RESIDUAL };
 
 template <int VF, int SF>
 static void launch_vec_t(VecKernel k, unsigned grid, const VecArgs& a, cudaStream_t s) {
@@ -194,6 +247,7 @@ static void launch_vec_t(VecKernel k, unsigned grid, const VecArgs& a, cudaStrea
     case VK_PUPDATE: k_pupdate<VF, SF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
     case VK_ACCUM: k_accumulate<VF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
     case VK_RESIDUAL: k_residual<VF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
+    case VK_MID_RESIDUAL: k_mid_residual<VF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
   }
 }
 
@@ -208,33 +262,56 @@ static int launch_vec(VecKernel k, int sloppy, const VecArgs& a, cudaStream_t s)
 
 struct Solver : CgEngine {
   Geom g;
-  lqcd_operator op64, ops;
+  lqcd_operator op64, ops, opm;  // FP64, sloppy, and FP32 arithmetic on the FP64 links (replacements)
   lqcd_solver_params prm;
   int subset;
+  bool mid_on = false;
+  bool normal = false;  // CGNR: b is the right-hand side of M x = b, not of M^dag M x = b
   Workspace w;
   const void* gauge64;
   const void* gauge_s;
   VecArgs va;
-  ReduceCtx rc_init, rc_alpha, rc_update, rc_reliable;
+  ReduceCtx rc_init, rc_alpha, rc_update, rc_reliable, rc_mid;
 
   int init(cudaStream_t s) override {
     cudaError_t e = cudaMemsetAsync(w.counter, 0, 64, s);
     if (e != cudaSuccess) return cuda_fail(e, "cg: memset");
     VecArgs a = va;
     a.red = rc_init;
+    if (normal) {
+      // r_0 = M^dag b in the inner iteration's arithmetic: the FP64 operator for a
+      // plain solve, else FP32 arithmetic on the FP64 links (every reliable update
+      // then recomputes r = M^dag (b - M x) in FP64, so the start needs no more)
+      int st;
+      if (prm.sloppy_prec == LQCD_F64) {
+        OpCtx c64{g, op64, gauge64};
+        if ((st = op_apply(c64, w.ax64, a.b64, subset, 1, w.t1_64, w.t2_64, nullptr, nullptr, s))) return st;
+        a.b64 = w.ax64;
+      } else {
+        const unsigned grid = (unsigned)(a.full ? 2 * a.bpp : a.bpp);
+        k_copy_field<LQCD_F32, LQCD_F64><<<grid, BLAS_BLOCK, 0, s>>>(a, w.xs, a.b64);
+        if ((st = after_launch("cgnr: b to FP32"))) return st;
+        OpCtx cm{g, opm, gauge64, LQCD_F64};
+        if ((st = op_apply(cm, w.ax64, w.xs, subset, 1, w.t1_64, w.t2_64, nullptr, nullptr, s))) return st;
+        k_copy_field<LQCD_F64, LQCD_F32><<<grid, BLAS_BLOCK, 0, s>>>(a, w.mid64, w.ax64);
+        if ((st = after_launch("cgnr: M^dag b to FP64"))) return st;
+        a.b64 = w.mid64;
+      }
+    }
     return launch_vec(VK_INIT, prm.sloppy_prec, a, s);
   }
 
   // M_hat p with |M_hat p|^2 = p^dag A p -> alpha; then M_hat^dag (M_hat p) = A p,
   // whose last hop applies x_s += alpha p, r_s -= alpha A p and reduces |r_s|^2
   // (beta, or a reliable-update request) instead of storing A p.
-  int head(cudaStream_t s, int cond, cudaGraphConditionalHandle h_rel) override {
+  int head(cudaStream_t s, int cond, cudaGraphConditionalHandle h_rel, cudaGraphConditionalHandle h_mid) override {
     OpCtx cs{g, ops, gauge_s};
     int st = op_apply(cs, w.mp, w.p, subset, 0, w.t1_s, w.t2_s, &rc_alpha, w.ctrl, s);
     if (st) return st;
     ReduceCtx ru = rc_update;
     ru.cond = cond;
     ru.h_rel = h_rel;
+    ru.h_mid = h_mid;
     const HopUpdate upd{w.p, w.xs, w.rs, va.hbv};
     return op_apply(cs, nullptr, w.mp, subset, 1, w.t1_s, w.t2_s, &ru, w.ctrl, s, &upd);
   }
@@ -251,9 +328,31 @@ struct Solver : CgEngine {
     if (st) return st;
     OpCtx c64{g, op64, gauge64};
     if ((st = op_apply(c64, w.mid64, a.x64, subset, 0, w.t1_64, w.t2_64, nullptr, nullptr, s))) return st;
+    if (normal) {  // r = M^dag (b - M x)
+      const unsigned grid = (unsigned)(a.full ? 2 * a.bpp : a.bpp);
+      k_b_minus<<<grid, BLAS_BLOCK, 0, s>>>(a, w.mid64, w.mid64);
+      if ((st = after_launch("cgnr: b - M x"))) return st;
+    }
     if ((st = op_apply(c64, w.ax64, w.mid64, subset, 1, w.t1_64, w.t2_64, nullptr, nullptr, s))) return st;
     a.red = rc_reliable;
+    if (normal) a.b64 = nullptr;  // ax64 already holds the residual
     return launch_vec(VK_RESIDUAL, prm.sloppy_prec, a, s);
+  }
+
+  bool has_mid() const override { return mid_on; }
+
+  // r_s = r - M^dag M x_s with FP32 arithmetic on the FP64 links. The FP64
+  // update's buffers (mid64, ax64, t1_64, t2_64) are idle here and hold the
+  // FP32 intermediates.
+  int mid(cudaStream_t s) override {
+    OpCtx cm{g, opm, gauge64, LQCD_F64};
+    int st = op_apply(cm, w.mid64, w.xs, subset, 0, w.t1_64, w.t2_64, nullptr, nullptr, s);
+    if (st) return st;
+    if ((st = op_apply(cm, w.ax64, w.mid64, subset, 1, w.t1_64, w.t2_64, nullptr, nullptr, s))) return st;
+    VecArgs a = va;
+    a.ax32 = w.ax64;
+    a.red = rc_mid;
+    return launch_vec(VK_MID_RESIDUAL, prm.sloppy_prec, a, s);
   }
 };
 
@@ -273,9 +372,13 @@ size_t lqcd_cg_workspace_bytes(const lqcd_lattice* lat, const lqcd_operator* op,
   return carve(nullptr, g, *op, *p, subset, nsys).total;
 }
 
-int lqcd_cg_solve(void* x, const void* b, const void* gauge, const void* gauge_sloppy, const lqcd_lattice* lat,
-                  const lqcd_operator* op, const lqcd_solver_params* prm, int subset, lqcd_solve_info* info,
-                  void* workspace, size_t workspace_bytes, void* stream) {
+}  // extern "C"
+
+namespace lqcd {
+
+static int cg_solve_impl(void* x, const void* b, const void* gauge, const void* gauge_sloppy, const lqcd_lattice* lat,
+                         const lqcd_operator* op, const lqcd_solver_params* prm, int subset, lqcd_solve_info* info,
+                         void* workspace, size_t workspace_bytes, void* stream, bool normal) {
   const auto t0 = std::chrono::steady_clock::now();
   lqcd_solve_info local;
   lqcd_solve_info* inf = info ? info : &local;
@@ -296,6 +399,7 @@ int lqcd_cg_solve(void* x, const void* b, const void* gauge, const void* gauge_s
   S.prm = *prm;
   if (S.prm.check_interval <= 0) S.prm.check_interval = 16;
   S.subset = subset;
+  S.normal = normal;
   S.nsys = op->kind == LQCD_WILSON && !op->gparity ? S.g.n5 : 1;  // G-parity flavours form one system
   S.w = carve(workspace, S.g, *op, *prm, subset, S.nsys);
   if (workspace_bytes < S.w.total)
@@ -307,6 +411,9 @@ int lqcd_cg_solve(void* x, const void* b, const void* gauge, const void* gauge_s
   S.ops.prec = prm->sloppy_prec;
   // the FP64 inner operator runs on the FP64 field itself, in that field's format
   S.ops.recon = prm->sloppy_prec == LQCD_F64 ? op->recon : prm->sloppy_recon;
+  S.opm = *op;
+  S.opm.prec = LQCD_F32;
+  S.mid_on = prm->sloppy_prec == LQCD_F16 && prm->delta_mid > 0.0;
   S.gauge64 = gauge;
   S.gauge_s = gauge_sloppy;
   cudaStream_t s = (cudaStream_t)stream;
@@ -347,6 +454,9 @@ int lqcd_cg_solve(void* x, const void* b, const void* gauge, const void* gauge_s
   S.rc_update.maxiter = prm->maxiter;
   S.rc_reliable = base;
   S.rc_reliable.fin = FIN_RELIABLE;
+  S.rc_mid = base;
+  S.rc_mid.fin = FIN_MID;
+  S.rc_init.delta2_mid = S.mid_on ? prm->delta_mid * prm->delta_mid : 0.0;
 
   // what the captured graph bakes in (tol and delta live in device state, not in the graph)
   std::vector<unsigned char> key;
@@ -375,6 +485,8 @@ int lqcd_cg_solve(void* x, const void* b, const void* gauge, const void* gauge_s
   key_append(key, S.prm.check_interval);
   key_append(key, prm->maxiter);
   key_append(key, subset);
+  key_append(key, S.mid_on);
+  key_append(key, S.normal);
 
   Control ctrl;
   memset(&ctrl, 0, sizeof(ctrl));
@@ -392,8 +504,27 @@ int lqcd_cg_solve(void* x, const void* b, const void* gauge, const void* gauge_s
   }
   inf->iterations = ctrl.iter;
   inf->reliable_updates = ctrl.n_reliable;
+  inf->residual_replacements = ctrl.n_mid;
   inf->true_rel_residual = worst;
   return finish(out_status);
+}
+
+}  // namespace lqcd
+
+extern "C" {
+
+int lqcd_cg_solve(void* x, const void* b, const void* gauge, const void* gauge_sloppy, const lqcd_lattice* lat,
+                  const lqcd_operator* op, const lqcd_solver_params* prm, int subset, lqcd_solve_info* info,
+                  void* workspace, size_t workspace_bytes, void* stream) {
+  return cg_solve_impl(x, b, gauge, gauge_sloppy, lat, op, prm, subset, info, workspace, workspace_bytes, stream,
+                       false);
+}
+
+int lqcd_cgnr_solve(void* x, const void* b, const void* gauge, const void* gauge_sloppy, const lqcd_lattice* lat,
+                    const lqcd_operator* op, const lqcd_solver_params* prm, int subset, lqcd_solve_info* info,
+                    void* workspace, size_t workspace_bytes, void* stream) {
+  return cg_solve_impl(x, b, gauge, gauge_sloppy, lat, op, prm, subset, info, workspace, workspace_bytes, stream,
+                       true);
 }
 
 }  // extern "C"

@@ -4,6 +4,7 @@
 //
 //   chunk_start --> WHILE (go) {
 //                     head: 4 sloppy hops (alpha), x_s / r_s update (beta, or request)
+//                     IF (replacement requested) { r_s = r - A x_s, FP32 arithmetic }  [three-level only]
 //                     IF (reliable update requested) { x += x_s; r = b - A x in FP64 }
 //                     tail: p = r_s + beta p
 //                     loop control: go = active && chunks left && iter < maxiter
@@ -32,8 +33,9 @@ __global__ void k_chunk_start(Control* c, int chunk, int maxiter, cudaGraphCondi
 }
 
 __global__ void k_loop_control(Control* c, int maxiter, cudaGraphConditionalHandle h_loop,
-                               cudaGraphConditionalHandle h_rel) {
+                               cudaGraphConditionalHandle h_rel, cudaGraphConditionalHandle h_mid, int has_mid) {
   cudaGraphSetConditional(h_rel, 0u);  // the next iteration's update decides afresh
+  if (has_mid) cudaGraphSetConditional(h_mid, 0u);
   c->chunk_left -= 1;
   const int go = c->active && c->chunk_left > 0 && c->iter < maxiter && c->n_done < c->nsys &&
                  !(c->reason & REASON_NAN);
@@ -43,7 +45,7 @@ __global__ void k_loop_control(Control* c, int maxiter, cudaGraphConditionalHand
 struct GraphEntry {
   std::vector<unsigned char> key;
   cudaGraphExec_t exec;
-  uint64_t head_kernels, tail_kernels, reliable_kernels;
+  uint64_t head_kernels, tail_kernels, reliable_kernels, mid_kernels;
   uint64_t last_use;
 };
 
@@ -118,14 +120,18 @@ static int build_graph(CgEngine& E, int chunk, int maxiter, GraphEntry* out) {
   cudaGraphNode_t wnode;
   LQCD_TRY_CUDA(cudaGraphAddNode(&wnode, outer, &start, nullptr, 1, &wp), "cg graph: while node");
   cudaGraph_t body = wp.conditional.phGraph_out[0];
-  cudaGraphConditionalHandle h_rel;
+  cudaGraphConditionalHandle h_rel, h_mid = 0;
   LQCD_TRY_CUDA(cudaGraphConditionalHandleCreate(&h_rel, body, 0, cudaGraphCondAssignDefault),
                 "cg graph: reliable handle");
+  const bool has_mid = E.has_mid();
+  if (has_mid)
+    LQCD_TRY_CUDA(cudaGraphConditionalHandleCreate(&h_mid, body, 0, cudaGraphCondAssignDefault),
+                  "cg graph: replacement handle");
 
   // body: head
   LQCD_TRY_CUDA(cudaStreamBeginCaptureToGraph(cap.s, body, nullptr, nullptr, 0, mode), "cg graph: capture");
   uint64_t c0 = g_captured_launches;
-  st = E.head(cap.s, 1, h_rel);
+  st = E.head(cap.s, 1, h_rel, h_mid);
   out->head_kernels = g_captured_launches - c0;
   cudaStreamCaptureStatus cs;
   const cudaGraphNode_t* deps = nullptr;
@@ -135,6 +141,27 @@ static int build_graph(CgEngine& E, int chunk, int maxiter, GraphEntry* out) {
   LQCD_TRY_CUDA(cudaStreamEndCapture(cap.s, &body), "cg graph: end capture");
   if (st) return st;
   if (e != cudaSuccess) return cuda_fail(e, "cg graph: capture info");
+
+  // body: IF (FP32-arithmetic replacement requested)
+  out->mid_kernels = 0;
+  if (has_mid) {
+    cudaGraphNodeParams mp = {};
+    mp.type = cudaGraphNodeTypeConditional;
+    mp.conditional.handle = h_mid;
+    mp.conditional.type = cudaGraphCondTypeIf;
+    mp.conditional.size = 1;
+    cudaGraphNode_t mnode;
+    LQCD_TRY_CUDA(cudaGraphAddNode(&mnode, body, frontier.data(), nullptr, frontier.size(), &mp),
+                  "cg graph: replacement node");
+    cudaGraph_t mg = mp.conditional.phGraph_out[0];
+    LQCD_TRY_CUDA(cudaStreamBeginCaptureToGraph(cap.s, mg, nullptr, nullptr, 0, mode), "cg graph: capture");
+    c0 = g_captured_launches;
+    st = E.mid(cap.s);
+    out->mid_kernels = g_captured_launches - c0;
+    LQCD_TRY_CUDA(cudaStreamEndCapture(cap.s, &mg), "cg graph: end capture");
+    if (st) return st;
+    frontier.assign(1, mnode);
+  }
 
   // body: IF (reliable update requested)
   cudaGraphNodeParams ip = {};
@@ -158,7 +185,7 @@ static int build_graph(CgEngine& E, int chunk, int maxiter, GraphEntry* out) {
   c0 = g_captured_launches;
   st = E.tail(cap.s);
   if (!st) {
-    k_loop_control<<<1, 1, 0, cap.s>>>(E.ctrl, maxiter, h_loop, h_rel);
+    k_loop_control<<<1, 1, 0, cap.s>>>(E.ctrl, maxiter, h_loop, h_rel, h_mid, has_mid ? 1 : 0);
     st = after_launch("k_loop_control");
   }
   out->tail_kernels = g_captured_launches - c0;
@@ -234,7 +261,9 @@ int run_cg(CgEngine& E, const lqcd_solver_params& prm, const std::vector<unsigne
       if ((st = read_ctrl(E.ctrl, ctrl, s))) return st;
       const uint64_t iters = (uint64_t)(ctrl->iter - before.iter);
       const uint64_t rels = (uint64_t)(ctrl->n_reliable - before.n_reliable);
-      count_launches(1 + iters * (ge.head_kernels + ge.tail_kernels) + rels * ge.reliable_kernels);
+      const uint64_t mids = (uint64_t)(ctrl->n_mid - before.n_mid);
+      count_launches(1 + iters * (ge.head_kernels + ge.tail_kernels) + rels * ge.reliable_kernels +
+                     mids * ge.mid_kernels);
       continue;
     }
     // host-driven
@@ -246,12 +275,14 @@ int run_cg(CgEngine& E, const lqcd_solver_params& prm, const std::vector<unsigne
       return LQCD_OK;
     }
     if (ctrl->active == 0) {
-      if ((st = E.reliable(s)) || (st = E.tail(s))) return st;
+      // paused by the update's finaliser: the reason bits say which recomputation is due
+      const bool mid_only = (ctrl->reason & REASON_MID) && !(ctrl->reason & (REASON_CONVERGED | REASON_RELIABLE));
+      if ((st = mid_only ? E.mid(s) : E.reliable(s)) || (st = E.tail(s))) return st;
       continue;
     }
     if (timed_out()) return fail(LQCD_ERR_TIMEOUT, "cg: wall-clock limit %.1f ms exceeded", prm.timeout_ms);
     for (int i = 0; i < chunk; i++)
-      if ((st = E.head(s, 0, 0)) || (st = E.tail(s))) return st;
+      if ((st = E.head(s, 0, 0, 0)) || (st = E.tail(s))) return st;
   }
 }
 

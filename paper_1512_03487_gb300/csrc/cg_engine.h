@@ -18,13 +18,18 @@ struct CgEngine {
   // r = b, x = 0, p = b; |b|^2 per system -> initial state (FIN_INIT)
   virtual int init(cudaStream_t s) = 0;
   // Mp = M p (p^dag A p -> alpha), Ap = M^dag Mp, x_s += alpha p, r_s -= alpha Ap
-  // (|r_s|^2 -> beta, or a reliable update is requested: through the IF node
-  // handle when cond = 1, by pausing for the host when cond = 0). Gated.
-  virtual int head(cudaStream_t s, int cond, cudaGraphConditionalHandle h_rel) = 0;
+  // (|r_s|^2 -> beta, or a reliable update / replacement is requested: through
+  // the IF node handles when cond = 1, by pausing for the host when cond = 0). Gated.
+  virtual int head(cudaStream_t s, int cond, cudaGraphConditionalHandle h_rel, cudaGraphConditionalHandle h_mid) = 0;
   // p = r_s + beta p. Gated.
   virtual int tail(cudaStream_t s) = 0;
   // x += x_s; r = b - A x with the FP64 operator; |r|^2 -> done flags, beta (FIN_RELIABLE)
   virtual int reliable(cudaStream_t s) = 0;
+  // Three-level scheme: r_s = r - A x_s with FP32 arithmetic on the FP64
+  // links, r the residual of the last FP64 update; |r_s|^2 -> beta (FIN_MID).
+  // Engines without the intermediate level never request it.
+  virtual bool has_mid() const { return false; }
+  virtual int mid(cudaStream_t) { return fail(LQCD_ERR_UNSUPPORTED, "cg: no intermediate replacement level"); }
 };
 
 // Runs a solve with engine E. `key` identifies everything the captured graph

@@ -104,21 +104,46 @@ __device__ __forceinline__ void accumulate_site(const Geom& g, int64_t j, double
   SpinorIO<VF>::store(xs, g.sstride, j, z);
 }
 
-// r = b - A x (FP64), r_s = r; returns |r|^2 in FP64
+// r = b - A x (FP64), r_s = r; returns |r|^2 in FP64. With b64 null, ax64
+// already holds the residual (CGNR: M^dag (b - M x)) and r = ax.
 template <int VF>
 __device__ __forceinline__ double residual_site(const Geom& g, int64_t j, const double* b64, const double* ax64,
                                                 double* r64, void* rs) {
   using TV = typename PrecTraits<VF>::real;
   Spinor<double> b, ax;
-  SpinorIO<LQCD_F64>::load(b64, g.sstride, j, b);
   SpinorIO<LQCD_F64>::load(ax64, g.sstride, j, ax);
+  if (b64) {
+    SpinorIO<LQCD_F64>::load(b64, g.sstride, j, b);
 #pragma unroll
-  for (int k = 0; k < 12; k++) b.v[k] = b.v[k] - ax.v[k];
+    for (int k = 0; k < 12; k++) b.v[k] = b.v[k] - ax.v[k];
+  } else {
+    b = ax;
+  }
   SpinorIO<LQCD_F64>::store(r64, g.sstride, j, b);
   Spinor<TV> rv;
   convert(b, rv);
   SpinorIO<VF>::store(rs, g.sstride, j, rv);
   return site_norm2(b);
+}
+
+// Intermediate replacement: r_s = r - A x_s, r the FP64 residual of the last
+// reliable update and A x_s an FP32 field computed with FP32 arithmetic;
+// returns |r_s|^2. The difference is taken in FP32: A x_s carries FP32 error
+// already, and the subtraction adds at most one rounding of r_s itself.
+template <int VF>
+__device__ __forceinline__ double mid_residual_site(const Geom& g, int64_t j, const double* r64, const void* ax32,
+                                                    void* rs) {
+  using TV = typename PrecTraits<VF>::real;
+  Spinor<double> r;
+  SpinorIO<LQCD_F64>::load(r64, g.sstride, j, r);
+  Spinor<float> ax;
+  SpinorIO<LQCD_F32>::load(ax32, g.sstride, j, ax);
+  Spinor<TV> rv;
+#pragma unroll
+  for (int k = 0; k < 12; k++)
+    rv.v[k] = mk((TV)((float)r.v[k].r - ax.v[k].r), (TV)((float)r.v[k].i - ax.v[k].i));
+  SpinorIO<VF>::store(rs, g.sstride, j, rv);
+  return site_norm2(rv);
 }
 
 }  // namespace lqcd

@@ -362,11 +362,14 @@ struct SysState {
   double tol2;    // tol^2 * rr0
   double delta2;  // delta^2 (0 disables reliable updates)
   double rr_true; // last FP64 true |r|^2
+  double maxrr_mid;   // max iterated |r|^2 since the last residual replacement of either level
+  double delta2_mid;  // delta_mid^2 (0 disables the FP32-arithmetic replacements)
   int done;
   int pad;
 };
 
-enum { REASON_CONVERGED = 1, REASON_RELIABLE = 2, REASON_NAN = 4 };
+// REASON_MID: an FP32-arithmetic residual replacement is due (three-level scheme).
+enum { REASON_CONVERGED = 1, REASON_RELIABLE = 2, REASON_NAN = 4, REASON_MID = 8 };
 
 struct Control {
   int active;      // 1 while inner iterations run; gated kernels return at once when 0
@@ -376,7 +379,7 @@ struct Control {
   int n_done;
   int n_reliable;  // FP64 residual recomputations done
   int chunk_left;  // device-driven loop: iterations left in the current graph launch
-  int pad;
+  int n_mid;       // FP32-arithmetic residual replacements done
 };
 
 // What the last block of a reducing kernel does with the per-system totals.
@@ -386,6 +389,7 @@ enum Finalize {
   FIN_UPDATE = 2,    // total = |r_new|^2 -> beta or pause
   FIN_INIT = 3,      // total = |b|^2 -> initial state
   FIN_RELIABLE = 4,  // total = FP64 true |r|^2 -> done flags, beta, resume
+  FIN_MID = 5,       // total = |r_ref - A x_s|^2 with FP32 arithmetic -> beta, resume
 };
 
 struct ReduceCtx {
@@ -398,9 +402,11 @@ struct ReduceCtx {
   int fin;
   double tol2_rel;        // FIN_INIT: tol^2
   double delta2;          // FIN_INIT: delta^2
+  double delta2_mid;      // FIN_INIT: delta_mid^2 (0 = no intermediate replacements)
   int maxiter;            // FIN_UPDATE: request a final FP64 residual once this many iterations ran
-  int cond;               // FIN_UPDATE: 1 = set h_rel (device-driven graph), 0 = pause for the host
+  int cond;               // FIN_UPDATE: 1 = set h_rel / h_mid (device-driven graph), 0 = pause for the host
   cudaGraphConditionalHandle h_rel;  // IF node running the reliable update (when cond)
+  cudaGraphConditionalHandle h_mid;  // IF node running the FP32-arithmetic replacement (when cond)
 };
 
 __device__ __forceinline__ bool gate_closed(const Control* ctrl) {
@@ -436,18 +442,21 @@ __device__ inline void finalize_totals(const ReduceCtx& rc, const double* totals
         if (!finite(totals[s])) reason |= REASON_NAN;
         else if (totals[s] <= st.tol2) reason |= REASON_CONVERGED;
         else if (totals[s] <= st.delta2 * st.maxrr) reason |= REASON_RELIABLE;
+        else if (st.delta2_mid > 0.0 && totals[s] <= st.delta2_mid * st.maxrr_mid) reason |= REASON_MID;
       }
       rc.ctrl->iter += 1;
       const bool at_cap = rc.maxiter > 0 && rc.ctrl->iter >= rc.maxiter;
+      const bool rel_due = (reason & (REASON_CONVERGED | REASON_RELIABLE)) || at_cap;
       if (reason & REASON_NAN) {
         rc.ctrl->reason |= REASON_NAN;
         rc.ctrl->active = 0;
-      } else if (reason || at_cap) {
-        // An FP64 residual recomputation is due (or the iteration cap is
-        // reached and the true residual must be known): beta waits for it.
-        rc.ctrl->reason |= reason;
-        if (rc.cond) cudaGraphSetConditional(rc.h_rel, 1);  // run the reliable-update branch now
-        else rc.ctrl->active = 0;                           // pause for the host
+      } else if (rel_due || (reason & REASON_MID)) {
+        // A residual recomputation is due -- FP64 (convergence, delta, or the
+        // iteration cap, where the true residual must be known) or, failing
+        // those, the FP32-arithmetic replacement: beta waits for it.
+        rc.ctrl->reason |= rel_due ? (reason & ~REASON_MID) : REASON_MID;
+        if (rc.cond) cudaGraphSetConditional(rel_due ? rc.h_rel : rc.h_mid, 1);  // run that branch now
+        else rc.ctrl->active = 0;                                                  // pause for the host
       } else {
         for (int s = 0; s < nsys; s++) {
           SysState& st = rc.sys[s];
@@ -455,6 +464,7 @@ __device__ inline void finalize_totals(const ReduceCtx& rc, const double* totals
           st.beta = totals[s] / st.rr;
           st.rr = totals[s];
           st.maxrr = fmax(st.maxrr, totals[s]);
+          st.maxrr_mid = fmax(st.maxrr_mid, totals[s]);
         }
       }
     } break;
@@ -464,10 +474,11 @@ __device__ inline void finalize_totals(const ReduceCtx& rc, const double* totals
       for (int s = 0; s < nsys; s++) {
         SysState& st = rc.sys[s];
         const double t = totals[s];
-        st.rr = st.rr0 = st.maxrr = st.rr_true = st.rr_new = t;
+        st.rr = st.rr0 = st.maxrr = st.maxrr_mid = st.rr_true = st.rr_new = t;
         st.alpha = st.beta = st.pAp = 0.0;
         st.tol2 = rc.tol2_rel * t;
         st.delta2 = rc.delta2;
+        st.delta2_mid = rc.delta2_mid;
         if (!finite(t)) bad = true;
         st.done = (t == 0.0) ? 1 : 0;
         n_done += st.done;
@@ -476,6 +487,7 @@ __device__ inline void finalize_totals(const ReduceCtx& rc, const double* totals
       rc.ctrl->n_done = n_done;
       rc.ctrl->iter = 0;
       rc.ctrl->n_reliable = 0;
+      rc.ctrl->n_mid = 0;
       rc.ctrl->chunk_left = 0;
       rc.ctrl->reason = bad ? REASON_NAN : 0;
       rc.ctrl->active = (!bad && n_done < nsys) ? 1 : 0;
@@ -494,6 +506,7 @@ __device__ inline void finalize_totals(const ReduceCtx& rc, const double* totals
             st.beta = t / st.rr;
             st.rr = t;
             st.maxrr = t;
+            st.maxrr_mid = t;
           }
         }
         n_done += st.done;
@@ -503,20 +516,42 @@ __device__ inline void finalize_totals(const ReduceCtx& rc, const double* totals
       rc.ctrl->reason = bad ? REASON_NAN : 0;
       rc.ctrl->active = (!bad && n_done < nsys) ? 1 : 0;
     } break;
+    case FIN_MID: {
+      // The replaced residual is only FP32-accurate: it restarts the
+      // recurrence (beta, the replacement maximum) but never decides
+      // convergence; that stays with the FP64 reliable update.
+      bool bad = false;
+      for (int s = 0; s < nsys; s++) {
+        SysState& st = rc.sys[s];
+        if (st.done) continue;
+        const double t = totals[s];
+        if (!finite(t)) { bad = true; continue; }
+        st.beta = t / st.rr;
+        st.rr = t;
+        st.maxrr = fmax(st.maxrr, t);
+        st.maxrr_mid = t;
+      }
+      rc.ctrl->n_mid += 1;
+      rc.ctrl->reason = bad ? REASON_NAN : 0;
+      rc.ctrl->active = (!bad && rc.ctrl->n_done < nsys) ? 1 : 0;
+    } break;
   }
 }
 
 // After every block has written its partials rc.partials[s * gridDim.x +
-// blockIdx.x] (s < nsys), the block that finishes last (atomic ticket; no
-// block ever waits for another) sums them per system in a fixed order and
-// runs the finaliser. `sh` is BLOCK doubles of shared scratch. Every thread of
-// the block must call it.
+// blockIdx.x] (s < nsys, written by thread s of the block), the block that
+// finishes last (atomic ticket; no block ever waits for another) sums them per
+// system in a fixed order and runs the finaliser. `sh` is BLOCK doubles of
+// shared scratch. Every thread of the block must call it. Only the writers of
+// partials fence: a fence in every thread would also wait for the thread's
+// streaming stores of the kernel's output, holding the block's warps
+// resident after their work is done.
 template <int BLOCK>
 __device__ __forceinline__ void last_block_finalize(const ReduceCtx& rc, double* sh) {
   __shared__ double totals[64];
   __shared__ int is_last;
   const int tid = threadIdx.x;
-  __threadfence();
+  if (tid < rc.nsys) __threadfence();
   __syncthreads();
   if (tid == 0) {
     unsigned int ticket = atomicAdd(rc.counter, 1u);

@@ -69,6 +69,23 @@ def test_workspace_queries(api):
     assert api.lqcd_operator_workspace_bytes(lat, op, api.LQCD_EVEN) > 0
     bad = api.solver_params(tol=-1.0)
     assert api.lqcd_cg_workspace_bytes(lat, op, bad, api.LQCD_EVEN) == 0
+    # the intermediate replacement level reuses the FP64 update's buffers: no extra workspace
+    mid = api.solver_params(sloppy_prec=api.LQCD_F16, sloppy_recon=12, delta=1e-5, delta_mid=0.003)
+    assert api.lqcd_cg_workspace_bytes(lat, op, mid, api.LQCD_EVEN) == ws_even
+    for d in (-0.1, 1.0, float("nan")):
+        assert api.lqcd_cg_workspace_bytes(lat, op, api.solver_params(delta_mid=d), api.LQCD_EVEN) == 0
+
+
+def test_struct_layouts_match_the_header(api):
+    """The ctypes mirrors of the C structs end where the header's do: the
+    fields appended last (delta_mid, residual_replacements) sit at their C
+    offsets, so older callers that zero the struct keep working."""
+    import ctypes as C
+    from paper_1512_03487_gb300 import _lib
+    P = _lib.lqcd_solver_params
+    assert P.delta_mid.offset == P.timeout_ms.offset + 8 and C.sizeof(P) == P.delta_mid.offset + 8
+    I = _lib.lqcd_solve_info
+    assert I.residual_replacements.offset == I.status.offset + 4
 
 
 @pytest.mark.parametrize("case", ["odd_lx", "odd_lz", "bad_bc", "bad_prec", "bad_recon", "null", "alias", "n5"])

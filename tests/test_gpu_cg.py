@@ -77,6 +77,162 @@ def test_eo_cg_mixed_precision(L, sloppy, recon):
         assert info.reliable_updates >= 2
 
 
+@pytest.mark.parametrize("recon64,use_graph,subset", [(18, 1, "even"), (12, 1, "even"), (18, 0, "even"),
+                                                     (18, 1, "full")])
+def test_three_level_fp16(L, recon64, use_graph, subset):
+    """FP16 inner iteration with intermediate FP32-arithmetic residual
+    replacements (delta_mid) and FP64 reliable updates only every five decades
+    (delta 1e-5): the FP64 true residual still reaches 1e-10, the replacements
+    run, and the FP64 updates stay as few as the FP32 inner solve needs. A wrong
+    replacement operator (it runs only inside the solve) would leave the
+    iterated residual inconsistent with x_s and cost FP64 updates and
+    iterations, which the bounds below catch."""
+    dims, m = (8, 4, 4, 8), 0.01
+    U = gauge_field(dims, "exp", 111, eps=0.3)
+    b = gaussian_spinor(dims, 112, lead=(1,))
+    lat = L.lattice(dims, bc=BC)
+    op = L.operator(mass=m, recon=recon64)
+    if subset == "even":
+        src, sub = to_cb(b, 0), L.LQCD_EVEN
+        A = lambda v: wilson.schur_dag_schur(U, v, m, BC)  # noqa: E731
+        check = lambda x: ocg.true_residual(A, from_cb(x, 0), from_cb(src, 0))  # noqa: E731
+    else:
+        src, sub = b, L.LQCD_FULL
+        A = lambda v: wilson.dirac_dag_dirac(U, v, m, BC)  # noqa: E731
+        check = lambda x: ocg.true_residual(A, x, src)  # noqa: E731
+    prm = L.solver_params(tol=1e-10, maxiter=5000, sloppy_prec=2, sloppy_recon=12, delta=1e-5,
+                          delta_mid=0.003, use_graph=use_graph)
+    x, info = _solve(L, U, src, lat, op, prm, sub, sloppy_recon=12)
+    assert info.status == 0, L.lqcd_last_error()
+    res = check(x)
+    assert res <= 1e-10
+    assert abs(info.true_rel_residual - res) < 1e-11
+    assert info.residual_replacements >= 1
+    assert info.reliable_updates <= 3
+    p64 = L.solver_params(tol=1e-10, maxiter=5000)
+    _, i64 = _solve(L, U, src, lat, op, p64, sub)
+    assert info.iterations <= 1.25 * i64.iterations + 10, (info.iterations, i64.iterations)
+    # without the middle level, FP16 needs an FP64 update every two to three decades
+    plain = L.solver_params(tol=1e-10, maxiter=5000, sloppy_prec=2, sloppy_recon=12, delta=0.003,
+                            use_graph=use_graph)
+    _, ip = _solve(L, U, src, lat, op, plain, sub, sloppy_recon=12)
+    assert ip.status == 0 and ip.residual_replacements == 0
+    assert info.reliable_updates < ip.reliable_updates
+
+
+def test_three_level_multi_rhs(L):
+    """The replacement level with n5 = 3 independent systems of very different
+    scales (each keeps its own replacement maximum)."""
+    dims, m, n = (4, 4, 4, 8), 0.05, 3
+    U = gauge_field(dims, "haar", 121)
+    b = gaussian_spinor(dims, 122, lead=(n,))
+    b[1] *= 1e-3
+    lat = L.lattice(dims, n5=n, bc=BC)
+    op = L.operator(mass=m)
+    prm = L.solver_params(tol=1e-10, maxiter=2000, sloppy_prec=2, sloppy_recon=12, delta=1e-5, delta_mid=0.003)
+    be = to_cb(b, 0)
+    x, info = _solve(L, U, be, lat, op, prm, L.LQCD_EVEN, sloppy_recon=12)
+    assert info.status == 0, L.lqcd_last_error()
+    assert info.residual_replacements >= 1
+    for k in range(n):
+        A = lambda v: wilson.schur_dag_schur(U, v, m, BC)  # noqa: E731
+        assert ocg.true_residual(A, from_cb(x[k:k + 1], 0), from_cb(be[k:k + 1], 0)) <= 1e-10
+
+
+def test_three_level_dwf(L):
+    """Domain wall, FP16 inner with replacements (M5 epilogue on FP64 links)."""
+    dims, Ls, M5, mf = (4, 4, 4, 4), 8, 1.8, 0.02
+    U = gauge_field(dims, "haar", 131)
+    b = gaussian_spinor(dims, 132, lead=(Ls,))
+    lat = L.lattice(dims, n5=Ls, bc=BC)
+    op = L.operator(kind=L.LQCD_DWF, M5=M5, mf=mf)
+    prm = L.solver_params(tol=1e-10, maxiter=5000, sloppy_prec=2, sloppy_recon=12, delta=1e-5, delta_mid=0.003)
+    be = to_cb(b, 0)
+    x, info = _solve(L, U, be, lat, op, prm, L.LQCD_EVEN, sloppy_recon=12)
+    assert info.status == 0, L.lqcd_last_error()
+    assert info.residual_replacements >= 1
+    A = lambda v: dwf.schur_dag_schur(U, v, M5, mf, BC)  # noqa: E731
+    assert ocg.true_residual(A, from_cb(x, 0), from_cb(be, 0)) <= 1e-10
+
+
+def _solve_nr(L, U, b, lat, op, prm, subset, sloppy_recon=12):
+    F = L.fields
+    g64 = F.gauge_to_device(U, lat, 0, op.recon)
+    gs = F.gauge_to_device(U, lat, prm.sloppy_prec, sloppy_recon) if prm.sloppy_prec != 0 else g64
+    bd = F.spinor_to_device(b, lat, 0, subset)
+    x = F.empty(L.lqcd_spinor_bytes(lat, 0, subset))
+    ws = F.empty(L.lqcd_cg_workspace_bytes(lat, op, prm, subset))
+    info = L.lqcd_cgnr_solve(x, bd, g64, gs, lat, op, prm, subset, ws, raise_on_error=False)
+    return F.spinor_to_host(x, lat, 0, subset), info
+
+
+def _normal_residual(apply_m, apply_mdag, x, b):
+    """||M^dag (b - M x)|| / ||M^dag b|| in FP64 (the oracle's own operators)."""
+    r = apply_mdag(b - apply_m(x))
+    s = apply_mdag(b)
+    return float(np.linalg.norm(r.ravel()) / np.linalg.norm(s.ravel()))
+
+
+@pytest.mark.parametrize("case", ["fp64", "fp32", "fp16_three_level", "full_fp32", "nograph_fp16", "dwf_fp32",
+                                  "mrhs_fp16_three_level"])
+def test_cgnr(L, case):
+    """CGNR for M_hat x = b_hat (or M x = b): M^dag b is never formed in FP64 --
+    the start applies it in the inner arithmetic, the reliable updates
+    recompute M^dag (b - M x) in FP64 -- and the solve still meets the FP64
+    normal-equation residual that the oracle computes from x, and x is the
+    oracle's solution."""
+    dims, m = (8, 4, 4, 8), 0.01
+    sloppy, dmid, delta, subset, n5 = 1, 0.0, 1e-5, L.LQCD_EVEN, 1
+    if case == "fp64":
+        sloppy, delta = 0, 0.1
+    elif case in ("fp16_three_level", "nograph_fp16", "mrhs_fp16_three_level"):
+        sloppy, dmid = 2, 0.003
+    elif case == "full_fp32":
+        subset = L.LQCD_FULL
+    if case == "mrhs_fp16_three_level":
+        dims, n5 = (4, 4, 4, 8), 3
+    U = gauge_field(dims, "exp", 141, eps=0.3)
+    if case == "dwf_fp32":
+        dims, n5, M5, mf = (4, 4, 4, 4), 8, 1.8, 0.02
+        U = gauge_field(dims, "haar", 142)
+        op = L.operator(kind=L.LQCD_DWF, M5=M5, mf=mf)
+        Mx = lambda v: dwf.schur(U, v, M5, mf, BC)  # noqa: E731
+        Md = lambda v: dwf.schur(U, v, M5, mf, BC, dagger=True)  # noqa: E731
+    else:
+        op = L.operator(mass=m)
+        if subset == L.LQCD_EVEN:
+            Mx = lambda v: wilson.schur(U, v, m, BC)  # noqa: E731
+            Md = lambda v: wilson.schur(U, v, m, BC, dagger=True)  # noqa: E731
+        else:
+            Mx = lambda v: wilson.dirac(U, v, m, BC)  # noqa: E731
+            Md = lambda v: wilson.dirac(U, v, m, BC, dagger=True)  # noqa: E731
+    b = gaussian_spinor(dims, 143, lead=(n5,))
+    if n5 == 3:
+        b[1] *= 1e-3
+    lat = L.lattice(dims, n5=n5, bc=BC)
+    prm = L.solver_params(tol=1e-10, maxiter=5000, sloppy_prec=sloppy, sloppy_recon=12, delta=delta,
+                          delta_mid=dmid, use_graph=0 if case == "nograph_fp16" else 1)
+    src = to_cb(b, 0) if subset == L.LQCD_EVEN else b
+    x, info = _solve_nr(L, U, src, lat, op, prm, subset)
+    assert info.status == 0, L.lqcd_last_error()
+    if dmid:
+        assert info.residual_replacements >= 1
+    full = (lambda v: from_cb(v, 0)) if subset == L.LQCD_EVEN else (lambda v: v)  # noqa: E731
+    if case == "dwf_fp32":
+        res = _normal_residual(Mx, Md, full(x), full(src))
+        assert res <= 1e-10
+        assert abs(res - info.true_rel_residual) < 1e-11
+        return
+    worst = 0.0
+    for k in range(n5):
+        res = _normal_residual(Mx, Md, full(x[k:k + 1]), full(src[k:k + 1]))
+        assert res <= 1e-10, (k, res)
+        worst = max(worst, res)
+        xo, _ = ocg.cg(lambda v: Md(Mx(v)), Md(full(src[k:k + 1])), 1e-13, 5000)
+        assert rel_l2(full(x[k:k + 1]), xo) < 1e-6
+    assert abs(worst - info.true_rel_residual) < 1e-11
+
+
 def test_multi_rhs_cg(L):
     """n5 = 3 independent right-hand sides sharing one gauge field, FP16 inner."""
     dims, m, n = (4, 4, 4, 8), 0.05, 3

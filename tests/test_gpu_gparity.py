@@ -82,9 +82,11 @@ def test_schur_operator(L, prec, dagger):
 
 @pytest.mark.parametrize("sloppy", [0, 1])
 @pytest.mark.parametrize("mask", [1, 7])
-def test_even_odd_solve_full_residual(L, sloppy, mask):
-    """b_hat = prepare(b); CG on M_hat^dag M_hat with source M_hat^dag b_hat; reconstruct x_o;
-    the oracle's G-parity operator must give |b - D x| / |b| <= 1e-9 on the full lattice."""
+@pytest.mark.parametrize("solver", ["cg", "cgnr"])
+def test_even_odd_solve_full_residual(L, sloppy, mask, solver):
+    """b_hat = prepare(b); CG on M_hat^dag M_hat with source M_hat^dag b_hat (or CGNR on
+    b_hat, whose start applies M_hat^dag with FP32 arithmetic on the FP64 links); reconstruct
+    x_o; the oracle's G-parity operator must give |b - D x| / |b| <= 1e-9 on the full lattice."""
     dims, m = (4, 4, 4, 8), 0.05
     gd = MASKS[mask]
     U = gauge_field(dims, "haar", 1921)
@@ -104,7 +106,10 @@ def test_even_odd_solve_full_residual(L, sloppy, mask):
     L.lqcd_M(src, bhat, g64, lat, op, 0, 1, tmp)
     x = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
     ws = F.empty(L.lqcd_cg_workspace_bytes(lat, op, prm, 0))
-    info = L.lqcd_cg_solve(x, src, g64, gs, lat, op, prm, 0, ws)
+    if solver == "cg":
+        info = L.lqcd_cg_solve(x, src, g64, gs, lat, op, prm, 0, ws)
+    else:
+        info = L.lqcd_cgnr_solve(x, bhat, g64, gs, lat, op, prm, 0, ws)
     L.lqcd_eo_reconstruct(x, bd, g64, lat, op, tmp)
     xh = F.spinor_to_host(x, lat, 0, 2)
     res = np.linalg.norm(b - gparity.dirac(U, xh, m, BC, gd)) / np.linalg.norm(b)
