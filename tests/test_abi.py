@@ -76,6 +76,16 @@ def test_workspace_queries(api):
         assert api.lqcd_cg_workspace_bytes(lat, op, api.solver_params(delta_mid=d), api.LQCD_EVEN) == 0
 
 
+def test_fma_probe_rejects_bad_arguments(api):
+    """Host-side validation of the probe, before any launch."""
+    import ctypes as C
+    lib = api.lib
+    assert lib.lqcd_fma_probe(None, 0, 10, 1, None) != 0
+    assert lib.lqcd_fma_probe(C.c_void_p(4096), 2, 10, 1, None) != 0  # FP16 is not a probe precision
+    assert lib.lqcd_fma_probe(C.c_void_p(4096), 0, 0, 1, None) != 0
+    assert lib.lqcd_fma_probe(C.c_void_p(4100), 0, 10, 1, None) != 0  # misaligned
+
+
 def test_struct_layouts_match_the_header(api):
     """The ctypes mirrors of the C structs end where the header's do: the
     fields appended last (delta_mid, residual_replacements) sit at their C

@@ -1,10 +1,11 @@
 """Parity at the benchmark sizes, in the launch configuration bench.py times.
 
 24^3 x 48 (the bench workload): every output of the FP16 and FP32 12-real hop
-against the oracle, and the mixed-precision solve's full-system FP64 residual.
+against the oracle, and the bench's solve (CGNR, FP16 three levels) and the
+two-level CG: normal-equation and full-system FP64 residuals from the oracle.
 16^4 x L_s = 16 (domain wall) and 32^4 x 12 RHS: the L_s-replicated /
-multi-RHS hop on sampled slices. 16^4 force kernel on the same X, Y as the
-oracle.
+multi-RHS hop on sampled slices. The force kernel at 16^4 and 24^3 x 32 on the
+same X, Y as the oracle.
 """
 import numpy as np
 import pytest
@@ -61,9 +62,13 @@ def test_bench_size_hop_all_outputs(L, bench_fields, prec, tol):
     assert rel_l2(got, expect) <= tol
 
 
-def test_bench_size_mixed_solve_residual(L, bench_fields):
-    """The bench step (FP16 / 12-real inner, FP64 reliable updates) reaches a
-    full-system residual ||b - D_W x|| / ||b|| checked by the oracle."""
+@pytest.mark.parametrize("solver", ["cgnr_three_level", "cg_fp16"])
+def test_bench_size_mixed_solve_residual(L, bench_fields, solver):
+    """The bench step -- CGNR on b_hat with FP16 / 12-real inner iteration, FP32
+    replacements (delta_mid 0.003) and FP64 reliable updates (delta 1e-5), check
+    interval 64 -- and the two-level CG on M_hat^dag b_hat: the normal-equation
+    residual recomputed by the oracle from x meets the tolerance, and so does
+    the full-system residual ||b - D_W x|| / ||b|| (loosely bounded by it)."""
     U, b = bench_fields
     F = L.fields
     m = 0.01
@@ -74,16 +79,29 @@ def test_bench_size_mixed_solve_residual(L, bench_fields):
     bd = F.spinor_to_device(b, lat, 0, 2)
     tmp = F.empty(L.lqcd_operator_workspace_bytes(lat, op, 0))
     bhat = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
-    src = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
     L.lqcd_eo_prepare(bhat, bd, g64, lat, op, tmp)
-    L.lqcd_M(src, bhat, g64, lat, op, 0, 1, tmp)
-    prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=2, sloppy_recon=12, check_interval=32)
     x = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
-    ws = F.empty(L.lqcd_cg_workspace_bytes(lat, op, prm, 0))
-    info = L.lqcd_cg_solve(x, src, g64, g16, lat, op, prm, 0, ws)
+    if solver == "cgnr_three_level":
+        prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=2, sloppy_recon=12, delta=1e-5,
+                              delta_mid=0.003, check_interval=64)
+        ws = F.empty(L.lqcd_cg_workspace_bytes(lat, op, prm, 0))
+        info = L.lqcd_cgnr_solve(x, bhat, g64, g16, lat, op, prm, 0, ws)
+        assert info.residual_replacements >= 1 and info.reliable_updates == 2
+    else:
+        src = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
+        L.lqcd_M(src, bhat, g64, lat, op, 0, 1, tmp)
+        prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=2, sloppy_recon=12, check_interval=32)
+        ws = F.empty(L.lqcd_cg_workspace_bytes(lat, op, prm, 0))
+        info = L.lqcd_cg_solve(x, src, g64, g16, lat, op, prm, 0, ws)
     assert info.status == 0 and info.true_rel_residual <= 1e-10
     L.lqcd_eo_reconstruct(x, bd, g64, lat, op, tmp)
     xh = F.spinor_to_host(x, lat, 0, 2)
+    # normal-equation residual of the even half, from the oracle's own operators
+    xe = wilson.restrict(xh, 0)
+    bh = wilson.prepare_source(U, b, m, BC)
+    r = wilson.schur(U, bh - wilson.schur(U, xe, m, BC), m, BC, dagger=True)
+    s0 = wilson.schur(U, bh, m, BC, dagger=True)
+    assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(s0)
     res = b - wilson.dirac(U, xh, m, BC)
     # ||b - D x|| <= ||M_hat^-dag|| tol ||...||: the normal-equation tolerance 1e-10 bounds it loosely
     assert np.linalg.norm(res) <= 1e-8 * np.linalg.norm(b)
@@ -125,8 +143,9 @@ def test_multi_rhs_size_hop_sampled_rhs(L):
         assert rel_l2(got[k].reshape(expect.shape), expect) <= 3e-3
 
 
-def test_force_kernel_16x4(L):
-    dims = (16, 16, 16, 16)
+@pytest.mark.parametrize("dims", [(16, 16, 16, 16), (24, 24, 24, 32)])
+def test_force_kernel_bench_sizes(L, dims):
+    """The force kernel on the two force workloads' sizes, on the same X, Y as the oracle."""
     U = gauge_field(dims, "haar", config_seed(4, 0))
     X = gaussian_spinor(dims, config_seed(4, 1))
     Y = gaussian_spinor(dims, config_seed(4, 2))
