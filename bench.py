@@ -75,7 +75,7 @@ def parse_args():
                          "dwf_f32r12_16x4_ls16, f32r12_32x4_12rhs)")
     ap.add_argument("--hop-prec", type=int, choices=[1, 2], default=HEADLINE_PREC,
                     help="storage precision of the hop timed by --mode hop (1 FP32, 2 FP16)")
-    ap.add_argument("--mode", choices=["full", "step", "hop", "hops"], default="full",
+    ap.add_argument("--mode", choices=["full", "step", "hop", "hops", "dwf"], default="full",
                     help="step: only the timed solves; hop: only the dominant kernel's roofline loop; "
                          "hops: the three hop shapes (profiling)")
     return ap.parse_args()
@@ -232,6 +232,13 @@ def run_lqcd(args, world, rank, local):
         res = {name: shapes[name]() for name in names}
         if rank == 0:
             print(json.dumps({"mode": "hops", "hops": res}), flush=True)
+        return
+    if args.mode == "dwf":
+        # profiling mode: the domain-wall solve alone (FP32 inner), honouring --no-graph / --check-interval
+        res = dwf_bench(L, F, L2Flush(dev), stream, use_graph=0 if args.no_graph else 1,
+                        check_interval=args.check_interval, three_level=False)
+        if rank == 0:
+            print(json.dumps({"mode": "dwf", "dwf": res}), flush=True)
         return
     dims = tuple(args.dims)
     mass = args.mass
@@ -584,55 +591,7 @@ def run_extras(L, F, flush, stream):
     from synthetic import config_seed, gauge_field, gaussian_spinor
     out = {}
 
-    # 16^4 x L_s = 16 domain wall, M5 = 1.8, mf = 0.02, Haar links, FP32-inner mixed CG to 1e-10
-    dims, Ls = (16, 16, 16, 16), 16
-    U = gauge_field(dims, "haar", config_seed(2, 0))
-    b = gaussian_spinor(dims, config_seed(2, 1), lead=(Ls,))
-    lat = L.lattice(dims, n5=Ls, bc=BC)
-    op = L.operator(kind=L.LQCD_DWF, M5=1.8, mf=0.02)
-    g64 = F.gauge_to_device(U, lat, 0, 18)
-    g32 = F.gauge_to_device(U, lat, 1, 12)
-    bd = F.spinor_to_device(b, lat, 0, 2)
-    del b
-    tmp = F.empty(L.lqcd_operator_workspace_bytes(lat, op, 0))
-    bhat = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
-    x = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
-    prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=12, delta=DELTA[1],
-                          check_interval=64)
-    prm3 = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=2, sloppy_recon=12, delta=DELTA_3LVL,
-                           delta_mid=DELTA_MID, check_interval=64)
-    g16 = F.gauge_to_device(U, lat, 2, 12)
-    ws = F.empty(max(L.lqcd_cg_workspace_bytes(lat, op, q, 0) for q in (prm, prm3)))
-
-    def dwf_solve(p=prm, gs=g32):
-        L.lqcd_eo_prepare(bhat, bd, g64, lat, op, tmp)
-        info = L.lqcd_cgnr_solve(x, bhat, g64, gs, lat, op, p, L.LQCD_EVEN, ws)
-        L.lqcd_eo_reconstruct(x, bd, g64, lat, op, tmp)
-        return info
-
-    dwf_solve(prm3, g16)
-    ms3, info3 = _events_time(lambda: dwf_solve(prm3, g16), stream, flush)
-    dwf_solve()
-    ms, info = _events_time(dwf_solve, stream, flush)
-    dx = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
-    L.lqcd_M(dx, x, g64, lat, op, L.LQCD_FULL, 0, None)
-    n = 2 * 16 ** 4 * Ls * 24
-    a = torch.empty(n, dtype=torch.float64, device="cuda")
-    bb = torch.empty(n, dtype=torch.float64, device="cuda")
-    L.lqcd_spinor_unpack(a, dx, 0, 2, lat)
-    L.lqcd_spinor_unpack(bb, bd, 0, 2, lat)
-    res = float(torch.linalg.vector_norm(a - bb) / torch.linalg.vector_norm(bb))
-    hops = 1 + 2 + 4 * (info.iterations + info.reliable_updates) + 1
-    out["dwf_16x4_ls16_mixed_fp32"] = {
-        "ms": round(ms, 3), "iterations": info.iterations, "reliable_updates": info.reliable_updates,
-        "full_system_rel_residual": res,
-        "dslash_gflops_in_solve": round(hops * FLOP_PER_SITE * 16 ** 4 // 2 * Ls / (ms * 1e-3) / 1e9, 1),
-        "hop_f32r12_ls16": _hop_gbs(L, F, lat, 1, 12, 8 * 48 / Ls + 96 + 96, flush, stream, kind=L.LQCD_DWF),
-        "fp16_inner_three_level": {"ms": round(ms3, 3), "iterations": info3.iterations,
-                                   "reliable_updates": info3.reliable_updates,
-                                   "fp32_replacements": info3.residual_replacements,
-                                   "true_rel_residual_normal_eq": info3.true_rel_residual}}
-    del g64, g32, g16, bd, tmp, bhat, x, ws, dx, a, bb
+    out["dwf_16x4_ls16_mixed_fp32"] = dwf_bench(L, F, flush, stream)
     torch.cuda.empty_cache()
 
     # 32^4 with 12 right-hand sides sharing the links, m = 0.01, mixed CG per RHS to 1e-10:
@@ -764,6 +723,61 @@ def run_extras(L, F, flush, stream):
 
 
 # ------------------------------------------------------------------ reference arm
+
+def dwf_bench(L, F, flush, stream, use_graph=1, check_interval=64, three_level=True):
+    """16^4 x L_s = 16 domain wall, M5 = 1.8, mf = 0.02, Haar links: even-odd CGNR to 1e-10 with FP32
+    inner storage (delta 1e-5) and, optionally, FP16 storage with three levels; one warm-up, one timed run."""
+    import torch
+    from synthetic import config_seed, gauge_field, gaussian_spinor
+    dims, Ls = (16, 16, 16, 16), 16
+    U = gauge_field(dims, "haar", config_seed(2, 0))
+    b = gaussian_spinor(dims, config_seed(2, 1), lead=(Ls,))
+    lat = L.lattice(dims, n5=Ls, bc=BC)
+    op = L.operator(kind=L.LQCD_DWF, M5=1.8, mf=0.02)
+    g64 = F.gauge_to_device(U, lat, 0, 18)
+    g32 = F.gauge_to_device(U, lat, 1, 12)
+    bd = F.spinor_to_device(b, lat, 0, 2)
+    del b
+    tmp = F.empty(L.lqcd_operator_workspace_bytes(lat, op, 0))
+    bhat = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
+    x = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
+    prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=12, delta=DELTA[1],
+                          check_interval=check_interval, use_graph=use_graph)
+    prm3 = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=2, sloppy_recon=12, delta=DELTA_3LVL,
+                           delta_mid=DELTA_MID, check_interval=check_interval, use_graph=use_graph)
+    g16 = F.gauge_to_device(U, lat, 2, 12)
+    ws = F.empty(max(L.lqcd_cg_workspace_bytes(lat, op, q, 0) for q in (prm, prm3)))
+
+    def dwf_solve(p=prm, gs=g32):
+        L.lqcd_eo_prepare(bhat, bd, g64, lat, op, tmp)
+        info = L.lqcd_cgnr_solve(x, bhat, g64, gs, lat, op, p, L.LQCD_EVEN, ws)
+        L.lqcd_eo_reconstruct(x, bd, g64, lat, op, tmp)
+        return info
+
+    if three_level:
+        dwf_solve(prm3, g16)
+        ms3, info3 = _events_time(lambda: dwf_solve(prm3, g16), stream, flush)
+    dwf_solve()
+    ms, info = _events_time(dwf_solve, stream, flush)
+    dx = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
+    L.lqcd_M(dx, x, g64, lat, op, L.LQCD_FULL, 0, None)
+    n = 2 * 16 ** 4 * Ls * 24
+    a = torch.empty(n, dtype=torch.float64, device="cuda")
+    bb = torch.empty(n, dtype=torch.float64, device="cuda")
+    L.lqcd_spinor_unpack(a, dx, 0, 2, lat)
+    L.lqcd_spinor_unpack(bb, bd, 0, 2, lat)
+    res = float(torch.linalg.vector_norm(a - bb) / torch.linalg.vector_norm(bb))
+    hops = 1 + 2 + 4 * (info.iterations + info.reliable_updates) + 1
+    return {
+        "ms": round(ms, 3), "iterations": info.iterations, "reliable_updates": info.reliable_updates,
+        "full_system_rel_residual": res,
+        "dslash_gflops_in_solve": round(hops * FLOP_PER_SITE * 16 ** 4 // 2 * Ls / (ms * 1e-3) / 1e9, 1),
+        "hop_f32r12_ls16": _hop_gbs(L, F, lat, 1, 12, 8 * 48 / Ls + 96 + 96, flush, stream, kind=L.LQCD_DWF),
+        "fp16_inner_three_level": {"ms": round(ms3, 3), "iterations": info3.iterations,
+                                   "reliable_updates": info3.reliable_updates,
+                                   "fp32_replacements": info3.residual_replacements,
+                                   "true_rel_residual_normal_eq": info3.true_rel_residual} if three_level else None}
+
 
 def su3_sweep(L, F, flush, stream):
     """SU(3) x SU(3) field product z = x y against memory footprint (the paper's first

@@ -144,8 +144,11 @@ def test_wilson_mdagm(L, subset):
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("dagger", [0, 1])
-def test_dwf_operators(L, prec, dagger):
-    dims, Ls, M5, mf = (4, 4, 2, 6), 6, 1.8, 0.02
+@pytest.mark.parametrize("Ls", [6, 2, 8, 16, 32])
+def test_dwf_operators(L, prec, dagger, Ls):
+    """Full and Schur domain-wall operators; L_s = 6 takes the closed-form M5op^-1
+    kernel, the powers of two up to 32 the warp-shuffle scan."""
+    dims, M5, mf = (4, 4, 2, 6), 1.8, 0.02
     U = gauge_field(dims, "haar", 21)
     psi = gaussian_spinor(dims, 22, lead=(Ls,))
     lat = L.lattice(dims, n5=Ls, bc=BC)

@@ -28,7 +28,7 @@ def L():
     return L
 
 
-def _solve(L, U, b, dims, m, **kw):
+def _solve(L, U, b, dims, m, cgnr=False, **kw):
     F = L.fields
     lat = L.lattice(dims, bc=BC)
     op = L.operator(mass=m)
@@ -38,7 +38,8 @@ def _solve(L, U, b, dims, m, **kw):
     bd = F.spinor_to_device(b, lat, 0, 0)
     x = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
     ws = F.empty(L.lqcd_cg_workspace_bytes(lat, op, prm, 0))
-    info = L.lqcd_cg_solve(x, bd, g64, gs, lat, op, prm, 0, ws, raise_on_error=False)
+    solve = L.lqcd_cgnr_solve if cgnr else L.lqcd_cg_solve
+    info = solve(x, bd, g64, gs, lat, op, prm, 0, ws, raise_on_error=False)
     torch.cuda.synchronize()
     return F.spinor_to_host(x, lat, 0, 0), info
 
@@ -84,5 +85,32 @@ def test_iteration_cap_reports_true_residual(L):
     assert info.status == ERR_NOT_CONVERGED
     res = ocg.true_residual(lambda v: wilson.schur_dag_schur(U, v, m, BC), from_cb(x, 0), from_cb(b, 0))
     # the reported residual is the FP64 true residual of the returned x
+    assert abs(res - info.true_rel_residual) <= 1e-6 * res
+    _healthy(L, U, b, dims, m)
+
+
+@pytest.mark.parametrize("sloppy,delta_mid,use_graph", [(0, 0.0, 1), (1, 0.0, 1), (2, 0.003, 1), (2, 0.003, 0)])
+def test_cgnr_nan_zero_and_cap(L, sloppy, delta_mid, use_graph):
+    """CGNR and the three-level scheme on the failure paths: a NaN in b is
+    reported (it reaches the start M^dag b), a zero b returns x = 0 at once, and
+    the iteration cap ends with the FP64 normal-equation residual of the
+    returned x; the context stays usable."""
+    dims, m = (4, 4, 4, 8), 0.05
+    U = gauge_field(dims, "haar", 831)
+    b = to_cb(gaussian_spinor(dims, 832, lead=(1,)), 0)
+    kw = dict(tol=1e-12, sloppy_prec=sloppy, sloppy_recon=12 if sloppy else 18, delta=1e-5 if sloppy else 0.1,
+              delta_mid=delta_mid, use_graph=use_graph, cgnr=True)
+    bad = b.copy()
+    bad.reshape(-1)[5] = np.nan
+    _, info = _solve(L, U, bad, dims, m, maxiter=500, **kw)
+    assert info.status == ERR_NAN, (info.status, L.lqcd_last_error())
+    x, info = _solve(L, U, np.zeros_like(b), dims, m, maxiter=500, **kw)
+    assert info.status == 0 and info.iterations == 0 and not np.any(x)
+    x, info = _solve(L, U, b, dims, m, maxiter=12, check_interval=5, **kw)
+    assert info.status == ERR_NOT_CONVERGED
+    Mx = lambda v: wilson.schur(U, v, m, BC)  # noqa: E731
+    Md = lambda v: wilson.schur(U, v, m, BC, dagger=True)  # noqa: E731
+    xe, be = from_cb(x, 0), from_cb(b, 0)
+    res = np.linalg.norm(Md(be - Mx(xe))) / np.linalg.norm(Md(be))
     assert abs(res - info.true_rel_residual) <= 1e-6 * res
     _healthy(L, U, b, dims, m)
