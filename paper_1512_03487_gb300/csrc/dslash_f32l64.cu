@@ -1,7 +1,7 @@
 // Hop kernel instantiations with FP32 spinors and arithmetic on FP64 links:
 // the operator of the intermediate (FP32-accurate) residual replacement of the
-// three-level mixed-precision CG and of the CGNR start M^dag b. Plain, xpay
-// and M5 epilogues (G-parity: plain and xpay), no reduction.
+// three-level mixed-precision CG and of the CGNR start M^dag b. Plain, xpay,
+// M5 and M5op^-1 epilogues (G-parity: plain and xpay), no reduction.
 #include "lqcd_internal.h"
 
 namespace lqcd {
@@ -20,6 +20,7 @@ static int launch_f32l64_epi(int epi, const HopArgs& a, cudaStream_t s) {
   if (epi == EPI_PLAIN) return launch_f32l64_inst<R, DAG, EPI_PLAIN, GP>(a, s);
   if (epi == EPI_XPAY) return launch_f32l64_inst<R, DAG, EPI_XPAY, GP>(a, s);
   if (!GP && epi == EPI_M5) return launch_f32l64_inst<R, DAG, GP ? EPI_XPAY : EPI_M5, GP>(a, s);
+  if (!GP && epi == EPI_M5INV) return launch_f32l64_inst<R, DAG, GP ? EPI_PLAIN : EPI_M5INV, GP>(a, s);
   return fail(LQCD_ERR_ARG, "bad epilogue %d", epi);
 }
 

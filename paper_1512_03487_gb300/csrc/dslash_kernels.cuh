@@ -22,10 +22,13 @@
 
 #include "cg_site.cuh"
 #include "lqcd_common.cuh"
+#include "m5_scan.cuh"
 
 namespace lqcd {
 
-enum Epilogue { EPI_PLAIN = 0, EPI_XPAY = 1, EPI_M5 = 2 };
+// EPI_M5INV: out = M5op^-1 (b H in), the inverse applied across the L_s lanes of
+// each 4D site by the warp-shuffle scan (domain wall, L_s dividing 32).
+enum Epilogue { EPI_PLAIN = 0, EPI_XPAY = 1, EPI_M5 = 2, EPI_M5INV = 3 };
 
 struct HopArgs {
   void* out;
@@ -39,6 +42,8 @@ struct HopArgs {
   int64_t half_bytes;     // bytes of one checkerboard of a full field
   double a, b;            // EPI_PLAIN: out = b H in; EPI_XPAY: out = a x + b H in
   double m5d, mf;         // EPI_M5: out = M5op(x) + b H in, M5op diagonal m5d = 5 - M5
+  int m5_dagger;          // EPI_M5INV: apply the adjoint of M5op^-1
+  double m5_den_inv;      // EPI_M5INV: 1 / (1 + mf (5 - M5)^-L_s)
   ReduceCtx red;          // |out|^2 per system (RED_NORM) or |r_s|^2 (RED_CG_UPDATE)
   const Control* gate;    // kernel returns at once when gate->active == 0
   // RED_CG_UPDATE: out = A p is not stored; instead x_s += alpha p and
@@ -307,7 +312,7 @@ __device__ __forceinline__ void hop_site(const Geom& g, const void* gauge, const
   hop_dir<2, P, R, DAG, GP, LP>(acc, g, gauge, x, cb, i5, parity, in);
   hop_dir<3, P, R, DAG, GP, LP>(acc, g, gauge, x, cb, i5, parity, in);
   const T b = (T)c.b;
-  if (EPI == EPI_PLAIN) {
+  if (EPI == EPI_PLAIN || EPI == EPI_M5INV) {
 #pragma unroll
     for (int k = 0; k < 12; k++) res.v[k] = b * acc.v[k];
   } else if (EPI == EPI_XPAY) {
@@ -364,6 +369,24 @@ __global__ void __launch_bounds__(BLOCK) hop_kernel(const HopArgs A) {
   char* out = static_cast<char*>(A.out) + (A.full ? parity * A.half_bytes : 0);
   const char* xb = A.x ? static_cast<const char*>(A.x) + (A.full ? parity * A.half_bytes : 0) : nullptr;
   const int64_t j = (int64_t)blk * BLOCK + threadIdx.x;
+  if constexpr (EPI == EPI_M5INV) {
+    // every lane takes part in the fifth-dimension scan; lanes past the end
+    // (whole 4D sites, since L_s divides the block) carry zeros and store nothing
+    static_assert(RED == RED_NONE, "M5op^-1 epilogue without reduction");
+    const bool live = j < A.g.nsites;
+    Spinor<T> res;
+    if (live) {
+      const EpiCoef c{A.a, A.b, A.m5d, A.mf};
+      hop_site<P, R, DAG, EPI, GP, LP>(A.g, A.gauge, in, xb, parity, j, c, res);
+    } else {
+      zero(res);
+    }
+    const int Ls = A.g.n5;
+    m5inv_lanes(res, (int)(threadIdx.x & (unsigned)(Ls - 1)), Ls, A.m5_dagger != 0, (T)(1.0 / A.m5d), (T)A.mf,
+                (T)A.m5_den_inv);
+    if (live) SpinorIO<P>::store(out, A.g.sstride, j, res);
+    return;
+  }
   double red = 0.0;
   if (j < A.g.nsites) {
     Spinor<T> res;

@@ -31,6 +31,8 @@ static int launch_hop_epi(int epi, int red, const HopArgs& a, cudaStream_t s) {
   if (epi == EPI_PLAIN) return launch_hop_inst<P, R, DAG, EPI_PLAIN, RED_NONE, GP>(a, s);
   if (epi == EPI_XPAY) return launch_hop_red<P, R, DAG, EPI_XPAY, GP>(red, a, s);
   if (!GP && epi == EPI_M5) return launch_hop_red<P, R, DAG, GP ? EPI_XPAY : EPI_M5, GP>(red, a, s);
+  if (!GP && epi == EPI_M5INV && red == RED_NONE)
+    return launch_hop_inst<P, R, DAG, GP ? EPI_PLAIN : EPI_M5INV, RED_NONE, GP>(a, s);
   return fail(LQCD_ERR_ARG, "bad epilogue %d", epi);
 }
 

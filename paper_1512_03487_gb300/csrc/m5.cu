@@ -12,67 +12,21 @@
 // w_k = -mf if s - k wrapped below 0, else 1. Chirality - uses b(s + k).
 // The adjoint swaps the two.
 //
-// Two kernels. When L_s divides 32 the L_s threads of a 4D site sit in one warp
-// (site index j = cb L_s + s) and solve the recurrence itself with shuffles:
-// on chirality +, with a = 1/d,
-//   y(s) = a (b(s) + y(s-1)), y(-1) = 0      (a Kogge-Stone scan: log2 L_s steps)
-//   x(s) = y(s) - mf a^(s+1) y(L_s-1) / (1 + mf a^L_s)
-// (the twisted wrap enters once, through y(L_s-1)); chirality - runs the same
-// scan from the top. Each thread reads and writes its own spinor once. Other
-// L_s use the closed-form sum above, one thread per output site reading the
-// L_s source spinors of its 4D site (through L1).
+// Two kernels. When L_s divides 32, the warp-shuffle scan of the recurrence
+// (m5_scan.cuh): each thread reads and writes its own spinor once. The
+// L_s-replicated hop runs the same scan in its epilogue (EPI_M5INV), so inside
+// the Schur operator this kernel is only needed for other L_s, where the
+// closed-form sum above runs, one thread per output site reading the L_s
+// source spinors of its 4D site (through L1).
 #include <cmath>
 
 #include "lqcd_internal.h"
+#include "m5_scan.cuh"
 
 namespace lqcd {
 
-// Shuffle of one spinor half (6 complex values) within segments of `width` lanes.
-template <typename T>
-__device__ __forceinline__ cpx<T> shfl_up_c(cpx<T> v, int o, int width) {
-  return mk(__shfl_up_sync(0xffffffffu, v.r, o, width), __shfl_up_sync(0xffffffffu, v.i, o, width));
-}
-template <typename T>
-__device__ __forceinline__ cpx<T> shfl_down_c(cpx<T> v, int o, int width) {
-  return mk(__shfl_down_sync(0xffffffffu, v.r, o, width), __shfl_down_sync(0xffffffffu, v.i, o, width));
-}
-template <typename T>
-__device__ __forceinline__ cpx<T> shfl_idx_c(cpx<T> v, int lane, int width) {
-  return mk(__shfl_sync(0xffffffffu, v.r, lane, width), __shfl_sync(0xffffffffu, v.i, lane, width));
-}
-
-// v[q0..q0+5] <- (d - L)^-1 of one chirality, in place. up: L shifts s-1 -> s
-// (the recurrence runs upward in s), else s+1 -> s. t = distance of this lane
-// from the recurrence's start (s or L_s-1-s).
-template <typename T>
-__device__ __forceinline__ void m5_scan(Spinor<T>& v, int q0, bool up, int t, int Ls, T a, T corr_t) {
-#pragma unroll
-  for (int q = 0; q < 6; q++) v.v[q0 + q] = a * v.v[q0 + q];
-  T ao = a;  // a^o
-  for (int o = 1; o < Ls; o <<= 1) {
-#pragma unroll
-    for (int q = 0; q < 6; q++) {
-      const cpx<T> w = up ? shfl_up_c(v.v[q0 + q], o, Ls) : shfl_down_c(v.v[q0 + q], o, Ls);
-      if (t >= o) v.v[q0 + q] = mk(fma(ao, w.r, v.v[q0 + q].r), fma(ao, w.i, v.v[q0 + q].i));
-    }
-    ao *= ao;
-  }
-  // wrap: x = y - corr_t y_end, corr_t = mf a^(t+1) / (1 + mf a^Ls)
-  const int end = up ? Ls - 1 : 0;
-#pragma unroll
-  for (int q = 0; q < 6; q++) {
-    const cpx<T> ye = shfl_idx_c(v.v[q0 + q], end, Ls);
-    v.v[q0 + q] = mk(fma(-corr_t, ye.r, v.v[q0 + q].r), fma(-corr_t, ye.i, v.v[q0 + q].i));
-  }
-}
-
-// corr[t] = mf a^(t+1) / (1 + mf a^L_s), t < L_s, computed on the host
-struct M5Corr {
-  double c[32];
-};
-
 template <int P>
-__global__ void __launch_bounds__(M5_BLOCK) m5inv_scan_kernel(const M5Args a, const M5Corr corr) {
+__global__ void __launch_bounds__(M5_BLOCK) m5inv_scan_kernel(const M5Args a, double den_inv) {
   using T = typename PrecTraits<P>::real;
   using IO = SpinorIO<P>;
   if (gate_closed(a.gate)) return;
@@ -83,13 +37,7 @@ __global__ void __launch_bounds__(M5_BLOCK) m5inv_scan_kernel(const M5Args a, co
   Spinor<T> v;
   if (live) IO::load(a.in, a.g.sstride, j, v);
   else zero(v);
-  const T ainv = (T)(1.0 / a.d);
-  // chirality + recurs upward without dagger, downward with it; chirality - the other way
-  const bool plus_up = !a.dagger;
-  const int t_up = s, t_down = Ls - 1 - s;
-  const T corr_up = (T)corr.c[t_up], corr_down = (T)corr.c[t_down];
-  m5_scan(v, 0, plus_up, plus_up ? t_up : t_down, Ls, ainv, plus_up ? corr_up : corr_down);
-  m5_scan(v, 6, !plus_up, plus_up ? t_down : t_up, Ls, ainv, plus_up ? corr_down : corr_up);
+  m5inv_lanes(v, s, Ls, a.dagger != 0, (T)(1.0 / a.d), (T)a.mf, (T)den_inv);
   if (live) IO::store(a.out, a.g.sstride, j, v);
 }
 
@@ -139,18 +87,12 @@ int launch_m5inv(int prec, const M5Args& a, cudaStream_t s) {
   const int64_t nb = (a.g.nsites + M5_BLOCK - 1) / M5_BLOCK;
   if (nb == 0) return LQCD_OK;
   const int Ls = a.g.n5;
-  if (Ls >= 2 && Ls <= 32 && (Ls & (Ls - 1)) == 0) {  // L_s divides the warp: the shuffle scan
-    M5Corr corr;
-    const double ainv = 1.0 / a.d, den = 1.0 + a.mf * std::pow(ainv, (double)Ls);
-    double at = ainv;  // a^(t+1)
-    for (int t = 0; t < 32; t++) {
-      corr.c[t] = t < Ls ? a.mf * at / den : 0.0;
-      at *= ainv;
-    }
+  if (m5_scan_ok(Ls)) {  // L_s divides the warp: the shuffle scan
+    const double den_inv = 1.0 / (1.0 + a.mf * std::pow(1.0 / a.d, (double)Ls));
     switch (prec) {
-      case LQCD_F64: m5inv_scan_kernel<LQCD_F64><<<(unsigned)nb, M5_BLOCK, 0, s>>>(a, corr); break;
-      case LQCD_F32: m5inv_scan_kernel<LQCD_F32><<<(unsigned)nb, M5_BLOCK, 0, s>>>(a, corr); break;
-      case LQCD_F16: m5inv_scan_kernel<LQCD_F16><<<(unsigned)nb, M5_BLOCK, 0, s>>>(a, corr); break;
+      case LQCD_F64: m5inv_scan_kernel<LQCD_F64><<<(unsigned)nb, M5_BLOCK, 0, s>>>(a, den_inv); break;
+      case LQCD_F32: m5inv_scan_kernel<LQCD_F32><<<(unsigned)nb, M5_BLOCK, 0, s>>>(a, den_inv); break;
+      case LQCD_F16: m5inv_scan_kernel<LQCD_F16><<<(unsigned)nb, M5_BLOCK, 0, s>>>(a, den_inv); break;
       default: return fail(LQCD_ERR_ARG, "bad precision %d", prec);
     }
     return after_launch("m5inv_scan_kernel");

@@ -2,9 +2,11 @@
 //   Wilson   D_W = (4 + m) - H / 2,      M_hat = (4 + m) - H_eo H_oe / (4 (4 + m))
 //   DWF      D_DW = M5op - H / 2,        M_hat = M5op - H_eo M5op^-1 H_oe / 4
 // and the even-odd source preparation / solution reconstruction.
+#include <cmath>
 #include <cstring>
 
 #include "lqcd_internal.h"
+#include "m5_scan.cuh"
 
 namespace lqcd {
 
@@ -33,6 +35,7 @@ static HopArgs base_args(const OpCtx& c, const ReduceCtx* red, const Control* ga
   if (red) a.red = *red;
   a.m5d = 5.0 - c.op.M5;
   a.mf = c.op.mf;
+  a.m5_den_inv = 1.0 / (1.0 + a.mf * std::pow(1.0 / a.m5d, (double)c.g.n5));
   return a;
 }
 
@@ -75,10 +78,16 @@ int op_apply(const OpCtx& c, void* out, const void* in, int subset, int dagger, 
   h1.out = t1;
   h1.in = in;
   h1.b = 1.0;
-  int st = launch_hop(P, R, dagger, EPI_PLAIN, RED_NONE, h1, s);
+  // domain wall with L_s dividing 32: M5op^-1 runs in the first hop's epilogue
+  const bool fuse_m5 = !wilson && m5_scan_ok(c.g.n5);
+  if (fuse_m5) {
+    h1.out = t2;
+    h1.m5_dagger = dagger;
+  }
+  int st = launch_hop(P, R, dagger, fuse_m5 ? EPI_M5INV : EPI_PLAIN, RED_NONE, h1, s);
   if (st) return st;
-  const void* src = t1;
-  if (!wilson) {
+  const void* src = fuse_m5 ? t2 : t1;
+  if (!wilson && !fuse_m5) {
     M5Args m;
     m.out = t2;
     m.in = t1;
