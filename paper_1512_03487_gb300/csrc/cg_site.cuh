@@ -9,11 +9,12 @@
 
 namespace lqcd {
 
-template <typename T> __device__ __forceinline__ double site_norm2(const Spinor<T>& s) {
+// |s|^2 in the spinor's own arithmetic type (the reductions above the warp are FP64)
+template <typename T> __device__ __forceinline__ T site_norm2(const Spinor<T>& s) {
   T acc = T(0);
 #pragma unroll
   for (int k = 0; k < 12; k++) acc = fma(s.v[k].r, s.v[k].r, fma(s.v[k].i, s.v[k].i, acc));
-  return (double)acc;
+  return acc;
 }
 
 template <typename TD, typename TS> __device__ __forceinline__ void convert(const Spinor<TS>& a, Spinor<TD>& b) {
@@ -43,9 +44,9 @@ __device__ __forceinline__ double init_site(const Geom& g, int64_t j, const doub
   return site_norm2(b);
 }
 
-// x_s += alpha p; r_s -= alpha Ap with Ap given in registers; returns |r_s|^2
+// x_s += alpha p; r_s -= alpha Ap with Ap given in registers; returns |r_s|^2 (in VF's type)
 template <int VF, int SF, typename TA>
-__device__ __forceinline__ double update_site_ap(const Geom& g, int64_t j, double alpha_d, const void* p_,
+__device__ __forceinline__ typename PrecTraits<VF>::real update_site_ap(const Geom& g, int64_t j, double alpha_d, const void* p_,
                                                  const Spinor<TA>& ap, void* xs, void* rs) {
   using TV = typename PrecTraits<VF>::real;
   using TS = typename PrecTraits<SF>::real;
@@ -65,9 +66,9 @@ __device__ __forceinline__ double update_site_ap(const Geom& g, int64_t j, doubl
   return site_norm2(r);
 }
 
-// x_s += alpha p; r_s -= alpha Ap; returns |r_s|^2
+// x_s += alpha p; r_s -= alpha Ap; returns |r_s|^2 (in VF's type)
 template <int VF, int SF>
-__device__ __forceinline__ double update_site(const Geom& g, int64_t j, double alpha_d, const void* p_,
+__device__ __forceinline__ typename PrecTraits<VF>::real update_site(const Geom& g, int64_t j, double alpha_d, const void* p_,
                                               const void* ap_, void* xs, void* rs) {
   Spinor<typename PrecTraits<SF>::real> ap;
   SpinorIO<SF>::load(ap_, g.sstride, j, ap);
@@ -131,7 +132,7 @@ __device__ __forceinline__ double residual_site(const Geom& g, int64_t j, const 
 // returns |r_s|^2. The difference is taken in FP32: A x_s carries FP32 error
 // already, and the subtraction adds at most one rounding of r_s itself.
 template <int VF>
-__device__ __forceinline__ double mid_residual_site(const Geom& g, int64_t j, const double* r64, const void* ax32,
+__device__ __forceinline__ typename PrecTraits<VF>::real mid_residual_site(const Geom& g, int64_t j, const double* r64, const void* ax32,
                                                     void* rs) {
   using TV = typename PrecTraits<VF>::real;
   Spinor<double> r;

@@ -43,6 +43,7 @@ struct HopArgs {
   double a, b;            // EPI_PLAIN: out = b H in; EPI_XPAY: out = a x + b H in
   double m5d, mf;         // EPI_M5: out = M5op(x) + b H in, M5op diagonal m5d = 5 - M5
   int m5_dagger;          // EPI_M5INV: apply the adjoint of M5op^-1
+  double m5_a;            // EPI_M5INV: 1 / (5 - M5)
   double m5_den_inv;      // EPI_M5INV: 1 / (1 + mf (5 - M5)^-L_s)
   ReduceCtx red;          // |out|^2 per system (RED_NORM) or |r_s|^2 (RED_CG_UPDATE)
   const Control* gate;    // kernel returns at once when gate->active == 0
@@ -346,11 +347,11 @@ __device__ __forceinline__ void hop_site(const Geom& g, const void* gauge, const
   }
 }
 
-template <typename T> __device__ __forceinline__ double norm2_site(const Spinor<T>& res) {
+template <typename T> __device__ __forceinline__ T norm2_site(const Spinor<T>& res) {
   T s = T(0);
 #pragma unroll
   for (int k = 0; k < 12; k++) s = fma(res.v[k].r, res.v[k].r, fma(res.v[k].i, res.v[k].i, s));
-  return (double)s;
+  return s;
 }
 
 // LP: storage precision of the links (P except for the FP32-arithmetic
@@ -382,12 +383,12 @@ __global__ void __launch_bounds__(BLOCK) hop_kernel(const HopArgs A) {
       zero(res);
     }
     const int Ls = A.g.n5;
-    m5inv_lanes(res, (int)(threadIdx.x & (unsigned)(Ls - 1)), Ls, A.m5_dagger != 0, (T)(1.0 / A.m5d), (T)A.mf,
+    m5inv_lanes(res, (int)(threadIdx.x & (unsigned)(Ls - 1)), Ls, A.m5_dagger != 0, (T)A.m5_a, (T)A.mf,
                 (T)A.m5_den_inv);
     if (live) SpinorIO<P>::store(out, A.g.sstride, j, res);
     return;
   }
-  double red = 0.0;
+  T red = T(0);
   if (j < A.g.nsites) {
     Spinor<T> res;
     const EpiCoef c{A.a, A.b, A.m5d, A.mf};

@@ -579,34 +579,38 @@ __device__ __forceinline__ void last_block_finalize(const ReduceCtx& rc, double*
   }
 }
 
-// Deterministic two-level reduction of one double per thread, grouped by
-// system (thread's system = global index mod nsys when nsys > 1). Per-block
-// partials go to rc.partials; the last block to finish (atomic ticket, no
-// waiting) sums them in a fixed order and runs the finaliser. Every thread of
-// the block must call it.
-template <int BLOCK>
-__device__ __forceinline__ void block_reduce_finalize(double v, int64_t block_first_gid, const ReduceCtx& rc) {
+// Deterministic two-level reduction of one value per thread, grouped by
+// system (thread's system = global index mod nsys when nsys > 1). V is the
+// field's arithmetic type: a warp sums its 32 values in V (FP32 for FP32 and
+// FP16 fields: on GB300 FP64 instructions are scarce, and 32 site norms summed
+// in FP32 keep a relative error near 1e-6), everything above the warp is FP64.
+// Per-block partials go to rc.partials; the last block to finish (atomic
+// ticket, no waiting) sums them in a fixed order and runs the finaliser. Every
+// thread of the block must call it.
+template <int BLOCK, typename V>
+__device__ __forceinline__ void block_reduce_finalize(V v, int64_t block_first_gid, const ReduceCtx& rc) {
   __shared__ double sh[BLOCK];
   const int tid = threadIdx.x;
   const int nsys = rc.nsys;
   if (nsys == 1) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((tid & 31) == 0) sh[tid >> 5] = v;
+    if ((tid & 31) == 0) sh[tid >> 5] = (double)v;
     __syncthreads();
-    if (tid < 32) {
-      double w = tid < BLOCK / 32 ? sh[tid] : 0.0;
+    if (tid == 0) {
+      double w = 0.0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
-      if (tid == 0) rc.partials[blockIdx.x] = w;
+      for (int k = 0; k < BLOCK / 32; k++) w += sh[k];
+      rc.partials[blockIdx.x] = w;
     }
   } else {
-    sh[tid] = v;
+    __shared__ V shv[BLOCK];
+    shv[tid] = v;
     __syncthreads();
     if (tid < nsys) {
       int first = (int)((tid - block_first_gid % nsys + nsys) % nsys);
       double s = 0.0;
-      for (int k = first; k < BLOCK; k += nsys) s += sh[k];
+      for (int k = first; k < BLOCK; k += nsys) s += (double)shv[k];
       rc.partials[(int64_t)tid * gridDim.x + blockIdx.x] = s;
     }
   }

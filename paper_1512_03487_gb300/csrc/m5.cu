@@ -26,7 +26,7 @@
 namespace lqcd {
 
 template <int P>
-__global__ void __launch_bounds__(M5_BLOCK) m5inv_scan_kernel(const M5Args a, double den_inv) {
+__global__ void __launch_bounds__(M5_BLOCK) m5inv_scan_kernel(const M5Args a, double ainv, double den_inv) {
   using T = typename PrecTraits<P>::real;
   using IO = SpinorIO<P>;
   if (gate_closed(a.gate)) return;
@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(M5_BLOCK) m5inv_scan_kernel(const M5Args a, do
   Spinor<T> v;
   if (live) IO::load(a.in, a.g.sstride, j, v);
   else zero(v);
-  m5inv_lanes(v, s, Ls, a.dagger != 0, (T)(1.0 / a.d), (T)a.mf, (T)den_inv);
+  m5inv_lanes(v, s, Ls, a.dagger != 0, (T)ainv, (T)a.mf, (T)den_inv);
   if (live) IO::store(a.out, a.g.sstride, j, v);
 }
 
@@ -88,11 +88,11 @@ int launch_m5inv(int prec, const M5Args& a, cudaStream_t s) {
   if (nb == 0) return LQCD_OK;
   const int Ls = a.g.n5;
   if (m5_scan_ok(Ls)) {  // L_s divides the warp: the shuffle scan
-    const double den_inv = 1.0 / (1.0 + a.mf * std::pow(1.0 / a.d, (double)Ls));
+    const double ainv = 1.0 / a.d, den_inv = 1.0 / (1.0 + a.mf * std::pow(ainv, (double)Ls));
     switch (prec) {
-      case LQCD_F64: m5inv_scan_kernel<LQCD_F64><<<(unsigned)nb, M5_BLOCK, 0, s>>>(a, den_inv); break;
-      case LQCD_F32: m5inv_scan_kernel<LQCD_F32><<<(unsigned)nb, M5_BLOCK, 0, s>>>(a, den_inv); break;
-      case LQCD_F16: m5inv_scan_kernel<LQCD_F16><<<(unsigned)nb, M5_BLOCK, 0, s>>>(a, den_inv); break;
+      case LQCD_F64: m5inv_scan_kernel<LQCD_F64><<<(unsigned)nb, M5_BLOCK, 0, s>>>(a, ainv, den_inv); break;
+      case LQCD_F32: m5inv_scan_kernel<LQCD_F32><<<(unsigned)nb, M5_BLOCK, 0, s>>>(a, ainv, den_inv); break;
+      case LQCD_F16: m5inv_scan_kernel<LQCD_F16><<<(unsigned)nb, M5_BLOCK, 0, s>>>(a, ainv, den_inv); break;
       default: return fail(LQCD_ERR_ARG, "bad precision %d", prec);
     }
     return after_launch("m5inv_scan_kernel");

@@ -35,7 +35,8 @@ static HopArgs base_args(const OpCtx& c, const ReduceCtx* red, const Control* ga
   if (red) a.red = *red;
   a.m5d = 5.0 - c.op.M5;
   a.mf = c.op.mf;
-  a.m5_den_inv = 1.0 / (1.0 + a.mf * std::pow(1.0 / a.m5d, (double)c.g.n5));
+  a.m5_a = 1.0 / a.m5d;
+  a.m5_den_inv = 1.0 / (1.0 + a.mf * std::pow(a.m5_a, (double)c.g.n5));
   return a;
 }
 
