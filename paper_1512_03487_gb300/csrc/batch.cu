@@ -36,6 +36,8 @@ struct BInst {
   const void* gauge64;
   const void* gauge_s;
   double c;  // 4 + m
+  double b;  // -1 / (4 c), the Schur hop's coefficient
+  double ab; // c / b = -4 c^2
   void* f[12];
   int64_t tile0;
 };
@@ -97,7 +99,8 @@ __global__ void __launch_bounds__(TILE) batch_hop_kernel(const BatchArgs A) {
     if (j < I.g.nsites) {
       EpiCoef c;
       c.a = I.c;
-      c.b = EPI == EPI_XPAY ? -1.0 / (4.0 * I.c) : 1.0;
+      c.b = EPI == EPI_XPAY ? I.b : 1.0;
+      c.ab = I.ab;
       c.m5d = 0.0;
       c.mf = 0.0;
       Spinor<T> res;
@@ -458,6 +461,8 @@ int lqcd_batch_cg_solve(int n, const lqcd_batch_item* items, int recon, const lq
     I.gauge64 = items[i].gauge;
     I.gauge_s = (prm->sloppy_prec == LQCD_F64 || !items[i].gauge_sloppy) ? items[i].gauge : items[i].gauge_sloppy;
     I.c = 4.0 + items[i].mass;
+    I.b = -1.0 / (4.0 * I.c);
+    I.ab = I.c / I.b;
     I.tile0 = tiles;
     tiles += (g.nsites + TILE - 1) / TILE;
     char* f = base + lay.fields_offset[i];
