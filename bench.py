@@ -35,19 +35,22 @@ FLOP_PER_SITE = 1320
 BC = (1.0, 1.0, 1.0, -1.0)
 WORKLOAD = "wilson_eo_cg_24x24x24x48_m0.01_exp0.3_tol1e-10"
 # Solver variants of the headline workload, key -> (inner storage precision, delta, delta_mid).
-# A reliable update recomputes r = b - A x with the FP64 operator, which on GB300 is bound by the
-# FP64 pipe and costs as much as ~10 FP32 iterations, so the largest drop per update that the inner
-# iteration sustains wins: sweeps on this workload gave delta = 1e-5 for FP32 storage (2 updates,
-# 61 iterations) and 0.003 for FP16 storage (4 updates, 62 iterations; smaller deltas add
-# iterations). Variant 3 keeps FP16 storage but puts FP32-arithmetic residual replacements
-# (delta_mid = 0.003) between FP64 updates at delta = 1e-5: 2 FP64 updates, 2 replacements,
-# 62 iterations, the fastest of the four (15.7 ms against 17.6 ms for FP32 storage, solve only).
-VARIANTS = {0: (0, 0.1, 0.0), 1: (1, 1e-5, 0.0), 2: (2, 0.003, 0.0), 3: (2, 1e-5, 0.003)}
+# Every variant is lqcd_eo_solve (even-odd CGNR: the exit test is the FP64 residual of the
+# even-odd system, ||b_hat - M_hat x|| / ||b_hat||). A reliable update recomputes it with two
+# FP64 hops, which on GB300 are bound by the FP64 pipe, so the largest drop per update that the
+# inner iteration sustains wins: delta = 3e-6 with FP32 storage (2 updates, 64 iterations;
+# 1e-5 needs 3 updates under this exit test) and 0.003 with FP16 storage alone (5 updates).
+# Variant 3 keeps FP16 storage and puts FP32-arithmetic residual replacements (delta_mid =
+# 0.003) between the FP64 updates at delta = 3e-6: 2 updates, 3 replacements, 66 iterations,
+# the fastest (16.7 ms against 17.6 ms for FP32 storage, whole even-odd solve).
+VARIANTS = {0: (0, 0.1, 0.0), 1: (1, 3e-6, 0.0), 2: (2, 0.003, 0.0), 3: (2, 3e-6, 0.003)}
 VARIANT_NAMES = {0: "fp64", 1: "mixed_fp32", 2: "mixed_fp16", 3: "mixed_fp16_three_level"}
 HEADLINE = 3
 HEADLINE_PREC = VARIANTS[HEADLINE][0]
 DELTA = {q: VARIANTS[q][1] for q in (0, 1, 2)}
 DELTA_3LVL, DELTA_MID = VARIANTS[3][1], VARIANTS[3][2]
+# lqcd_cg_solve (normal-equation exit test: multi-RHS, force, batch) keeps 1e-5 with FP32 storage
+DELTA_NORMAL_FP32 = 1e-5
 PREC_TAG = {1: "f32", 2: "f16"}
 PROFILE_JSON = {q: os.path.join(ROOT, "profiles", f"hop_{PREC_TAG[q]}r12_24x24x24x48.json") for q in (1, 2)}
 DSLASH_COMMON = ["dslash_kernels.cuh", "lqcd_common.cuh", "cg_site.cuh", "dslash_launch.cuh"]
@@ -255,14 +258,13 @@ def run_lqcd(args, world, rank, local):
     g64 = F.empty(L.lqcd_gauge_bytes(lat, L.LQCD_F64, 18))
     gs = {p: F.empty(L.lqcd_gauge_bytes(lat, p, 12)) for p in (L.LQCD_F32, L.LQCD_F16)}
     bfull = F.empty(L.lqcd_spinor_bytes(lat, L.LQCD_F64, L.LQCD_FULL))
-    bhat = F.empty(L.lqcd_spinor_bytes(lat, L.LQCD_F64, L.LQCD_EVEN))
     x = F.empty(L.lqcd_spinor_bytes(lat, L.LQCD_F64, L.LQCD_FULL))
     tmp = F.empty(L.lqcd_operator_workspace_bytes(lat, op64, L.LQCD_EVEN))
     prms = {k: L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=q, sloppy_recon=12 if q else 18,
                                delta=d, delta_mid=dm, check_interval=args.check_interval,
                                use_graph=0 if args.no_graph else 1)
             for k, (q, d, dm) in VARIANTS.items()}
-    ws = F.empty(max(L.lqcd_cg_workspace_bytes(lat, op64, prms[k], L.LQCD_EVEN) for k in prms))
+    ws = F.empty(max(L.lqcd_eo_solve_workspace_bytes(lat, op64, prms[k]) for k in prms))
     flush = L2Flush(dev)
 
     def step(key):
@@ -274,10 +276,10 @@ def run_lqcd(args, world, rank, local):
             gsl = gs[sloppy]
             L.lqcd_gauge_pack(gsl, sloppy, 12, U_dev, lat)
         L.lqcd_spinor_pack(bfull, L.LQCD_F64, L.LQCD_FULL, b_dev, lat)
-        L.lqcd_eo_prepare(bhat, bfull, g64, lat, op64, tmp)
-        info = L.lqcd_cgnr_solve(x, bhat, g64, gsl, lat, op64, prms[key], L.LQCD_EVEN, ws)
-        L.lqcd_eo_reconstruct(x, bfull, g64, lat, op64, tmp)
-        hops = 1 + 2 + 4 * (info.iterations + info.reliable_updates + info.residual_replacements) + 1
+        info = L.lqcd_eo_solve(x, bfull, g64, gsl, lat, op64, prms[key], ws)
+        # preparation, CGNR start, 4 per iteration, update and replacement; the odd half reuses the last
+        # update's hop
+        hops = 1 + 2 + 4 * (info.iterations + info.reliable_updates + info.residual_replacements)
         return hops, info
 
     def timed(fn, *a):
@@ -337,7 +339,7 @@ def run_lqcd(args, world, rank, local):
         ms, (hops, info) = runs[2]  # median of 5 after one warm-up
         cgcmp[name] = {"ms": round(ms, 3), "iterations": info.iterations,
                        "reliable_updates": info.reliable_updates, "delta": prms[p].delta,
-                       "true_rel_residual_normal_eq": info.true_rel_residual,
+                       "true_rel_residual_eo_system": info.true_rel_residual,
                        "dslash_gflops": round(hops * FLOP_PER_SITE * vh / (ms * 1e-3) / 1e9, 1)}
         if p == 3:
             cgcmp[name].update({"delta_mid": prms[p].delta_mid,
@@ -356,13 +358,13 @@ def run_lqcd(args, world, rank, local):
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(L, F, lat, op64, U, b, prms[HEADLINE], ws, tmp, x, gs[HEADLINE_PREC], g64, bfull, bhat,
+        e2e = run_e2e(L, F, lat, op64, U, b, prms[HEADLINE], ws, tmp, x, gs[HEADLINE_PREC], g64, bfull,
                       flush, stream, vh, args, world)
 
     # ---- the other hot-path workloads (domain wall, multi-RHS, uneven batch, force)
     extras = None
     if not args.no_extras:
-        del U_dev, g64, gs, ws, tmp, x, bfull, bhat
+        del U_dev, g64, gs, ws, tmp, x, bfull
         torch.cuda.empty_cache()
         extras = run_extras(L, F, flush, stream)
 
@@ -374,12 +376,12 @@ def run_lqcd(args, world, rank, local):
                  "f32-arithmetic residual replacements, f64 reliable updates and true residual",
         "data": "synthetic (seeded exp(0.3 i H) links, Gaussian source)",
         "config": {"workload": WORKLOAD, "lattice": list(dims), "mass": mass, "bc": list(BC),
-                   "solver": "even-odd CGNR (CG on M_hat^dag M_hat x = M_hat^dag b_hat), FP16-storage / 12-real "
-                             f"inner iteration, FP32-arithmetic residual replacements at delta_mid {DELTA_MID}, FP64 "
-                             f"reliable updates r = M_hat^dag (b_hat - M_hat x) at delta {DELTA_3LVL}",
-                   "tol": 1e-10, "tol_applies_to": "FP64 true residual of the normal equations, ||M_hat^dag (b_hat - "
-                                                   "M_hat x)|| / ||M_hat^dag b_hat|| (the full-system residual is "
-                                                   "reported beside it)",
+                   "solver": "lqcd_eo_solve: even-odd CGNR (CG on M_hat^dag M_hat x = M_hat^dag b_hat), "
+                             "FP16-storage / 12-real inner iteration, FP32-arithmetic residual replacements at "
+                             f"delta_mid {DELTA_MID}, FP64 reliable updates of b_hat - M_hat x at delta {DELTA_3LVL}",
+                   "tol": 1e-10, "tol_applies_to": "FP64 true residual of the even-odd system, ||b_hat - M_hat x_e|| / "
+                                                   "||b_hat|| (the full-system residual ||b - D x|| / ||b|| of the "
+                                                   "reconstructed x is reported beside it)",
                    "l2": "flushed before every timed step (512 MB write, then 256 MB read)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "full_system_rel_residual": res,
@@ -505,7 +507,7 @@ def measured_peak():
         return 6800.0, "fallback 6.8 TB/s (of fallback)"
 
 
-def run_e2e(L, F, lat, op64, U, b, prm, ws, tmp, x, gsl, g64, bfull, bhat, flush, stream, vh, args, world):
+def run_e2e(L, F, lat, op64, U, b, prm, ws, tmp, x, gsl, g64, bfull, flush, stream, vh, args, world):
     """Same solve through the C ABI from pinned host buffers: H2D of the FP64
     gauge field and source, pack, solve, reconstruct, D2H of the solution."""
     import torch
@@ -518,11 +520,9 @@ def run_e2e(L, F, lat, op64, U, b, prm, ws, tmp, x, gsl, g64, bfull, bhat, flush
         L.lqcd_gauge_upload(g64, L.LQCD_F64, 18, U_h, staging, lat)
         L.lqcd_gauge_pack(gsl, HEADLINE_PREC, 12, staging, lat)
         L.lqcd_spinor_upload(bfull, L.LQCD_F64, L.LQCD_FULL, b_h, staging, lat)
-        L.lqcd_eo_prepare(bhat, bfull, g64, lat, op64, tmp)
-        info = L.lqcd_cgnr_solve(x, bhat, g64, gsl, lat, op64, prm, L.LQCD_EVEN, ws)
-        L.lqcd_eo_reconstruct(x, bfull, g64, lat, op64, tmp)
+        info = L.lqcd_eo_solve(x, bfull, g64, gsl, lat, op64, prm, ws)
         L.lqcd_spinor_download(x_h, x, L.LQCD_F64, L.LQCD_FULL, staging, lat)
-        return 1 + 2 + 4 * (info.iterations + info.reliable_updates + info.residual_replacements) + 1
+        return 1 + 2 + 4 * (info.iterations + info.reliable_updates + info.residual_replacements)
 
     for _ in range(max(1, args.warmup // 2)):
         e2e_step()
@@ -608,9 +608,9 @@ def run_extras(L, F, flush, stream):
     be = F.spinor_to_device(F.checkerboard(rhs, 0), lat, 0, 0)
     del rhs
     x = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
-    prm = {q: L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=q, sloppy_recon=12, delta=DELTA[q],
-                              check_interval=64) for q in (1, 2)}
-    prm[3] = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=2, sloppy_recon=12, delta=DELTA_3LVL,
+    prm = {q: L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=q, sloppy_recon=12,
+                              delta=DELTA_NORMAL_FP32 if q == 1 else DELTA[q], check_interval=64) for q in (1, 2)}
+    prm[3] = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=2, sloppy_recon=12, delta=DELTA_NORMAL_FP32,
                              delta_mid=DELTA_MID, check_interval=64)
     ws = F.empty(max(L.lqcd_cg_workspace_bytes(lat, op, prm[q], 0) for q in prm))
     vh = 32 ** 4 // 2
@@ -654,7 +654,8 @@ def run_extras(L, F, flush, stream):
                             gauge_sloppy=F.gauge_to_device(U, lat, 1, 12),
                             x=F.empty(L.lqcd_spinor_bytes(lat, 0, 0)), b=F.spinor_to_device(bsrc, lat, 0, 0)))
     items = L.batch_items(entries)
-    prm = L.solver_params(tol=1e-10, maxiter=5000, sloppy_prec=1, sloppy_recon=12, delta=DELTA[1], check_interval=64)
+    prm = L.solver_params(tol=1e-10, maxiter=5000, sloppy_prec=1, sloppy_recon=12, delta=DELTA_NORMAL_FP32,
+                          check_interval=64)
     wsb = F.empty(L.lqcd_batch_cg_workspace_bytes(len(entries), items, 18, prm))
     L.lqcd_batch_cg_solve(len(entries), items, 18, prm, wsb)  # tunes the grid, captures the graph
     ms_b, infos = _events_time(lambda: L.lqcd_batch_cg_solve(len(entries), items, 18, prm, wsb), stream, flush)
@@ -691,7 +692,7 @@ def run_extras(L, F, flush, stream):
         X = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
         Y = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
         Fo = F.empty(L.lqcd_gauge_bytes(lat, 0, 18))
-        prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=18, delta=DELTA[1],
+        prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=18, delta=DELTA_NORMAL_FP32,
                               check_interval=64)
         ws = F.empty(L.lqcd_cg_workspace_bytes(lat, op, prm, 2))
 
@@ -738,21 +739,16 @@ def dwf_bench(L, F, flush, stream, use_graph=1, check_interval=64, three_level=T
     g32 = F.gauge_to_device(U, lat, 1, 12)
     bd = F.spinor_to_device(b, lat, 0, 2)
     del b
-    tmp = F.empty(L.lqcd_operator_workspace_bytes(lat, op, 0))
-    bhat = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
     x = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
     prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=12, delta=DELTA[1],
                           check_interval=check_interval, use_graph=use_graph)
     prm3 = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=2, sloppy_recon=12, delta=DELTA_3LVL,
                            delta_mid=DELTA_MID, check_interval=check_interval, use_graph=use_graph)
     g16 = F.gauge_to_device(U, lat, 2, 12)
-    ws = F.empty(max(L.lqcd_cg_workspace_bytes(lat, op, q, 0) for q in (prm, prm3)))
+    ws = F.empty(max(L.lqcd_eo_solve_workspace_bytes(lat, op, q) for q in (prm, prm3)))
 
     def dwf_solve(p=prm, gs=g32):
-        L.lqcd_eo_prepare(bhat, bd, g64, lat, op, tmp)
-        info = L.lqcd_cgnr_solve(x, bhat, g64, gs, lat, op, p, L.LQCD_EVEN, ws)
-        L.lqcd_eo_reconstruct(x, bd, g64, lat, op, tmp)
-        return info
+        return L.lqcd_eo_solve(x, bd, g64, gs, lat, op, p, ws)
 
     if three_level:
         dwf_solve(prm3, g16)
@@ -776,7 +772,7 @@ def dwf_bench(L, F, flush, stream, use_graph=1, check_interval=64, three_level=T
         "fp16_inner_three_level": {"ms": round(ms3, 3), "iterations": info3.iterations,
                                    "reliable_updates": info3.reliable_updates,
                                    "fp32_replacements": info3.residual_replacements,
-                                   "true_rel_residual_normal_eq": info3.true_rel_residual} if three_level else None}
+                                   "true_rel_residual_eo_system": info3.true_rel_residual} if three_level else None}
 
 
 def su3_sweep(L, F, flush, stream):
@@ -849,17 +845,12 @@ def gparity_bench(L, F, flush, stream):
     g32 = F.gauge_to_device(U, lat, 1, 12)
     bd = F.spinor_to_device(gaussian_spinor(dims, config_seed(60, 1), lead=(2,)), lat, 0, 2)
     del U
-    tmp = F.empty(L.lqcd_operator_workspace_bytes(lat, op, 0))
-    bhat = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
     x = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
     prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=12, delta=DELTA[1], check_interval=64)
-    ws = F.empty(L.lqcd_cg_workspace_bytes(lat, op, prm, 0))
+    ws = F.empty(L.lqcd_eo_solve_workspace_bytes(lat, op, prm))
 
     def solve():
-        L.lqcd_eo_prepare(bhat, bd, g64, lat, op, tmp)
-        info = L.lqcd_cgnr_solve(x, bhat, g64, g32, lat, op, prm, L.LQCD_EVEN, ws)
-        L.lqcd_eo_reconstruct(x, bd, g64, lat, op, tmp)
-        return info
+        return L.lqcd_eo_solve(x, bd, g64, g32, lat, op, prm, ws)
 
     solve()
     ms, info = _events_time(solve, stream, flush)
@@ -872,7 +863,7 @@ def gparity_bench(L, F, flush, stream):
     L.lqcd_spinor_unpack(bb, bd, 0, 2, lat)
     res = float(torch.linalg.vector_norm(a - bb) / torch.linalg.vector_norm(bb))
     vh = int(np.prod(dims)) // 2
-    hops = 1 + 2 + 4 * (info.iterations + info.reliable_updates) + 1
+    hops = 1 + 2 + 4 * (info.iterations + info.reliable_updates)  # the odd half reuses the last update's hop
     opg = L.operator(prec=1, recon=12, gparity=mask)
     fin = F.empty(L.lqcd_spinor_bytes(lat, 1, L.LQCD_ODD))
     fin.zero_()
@@ -931,7 +922,8 @@ def hmc_bench(L, F, stream):
     U = gauge_field(dims, "exp", config_seed(50, 0), eps=0.3)
     P = random_su3_algebra(make_rng(config_seed(50, 1)), U.size // 9).reshape(U.shape)
     eta = gaussian_spinor(dims, config_seed(50, 2)) / np.sqrt(2.0)
-    prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=12, delta=DELTA[1], check_interval=64)
+    prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=12, delta=DELTA_NORMAL_FP32,
+                          check_interval=64)
     hp = L.hmc_params(beta, 1.0, 10, L.LQCD_MINNORM2, 1)
     U0 = F.gauge_to_device(U, lat, 0, 18)
     P0 = F.gauge_to_device(P, lat, 0, 18)

@@ -269,20 +269,38 @@ int lqcd_cg_solve(void* x_dev, const void* b_dev, const void* gauge_dev,
                   void* stream);
 
 /* CGNR: solves M x = b (subset LQCD_FULL) or M_hat x = b (LQCD_EVEN, b = b_hat
- * of lqcd_eo_prepare) by CG on the normal equations M^dag M x = M^dag b,
- * without forming M^dag b in FP64: the starting residual M^dag b is applied in
- * the inner iteration's arithmetic (FP32 arithmetic on gauge_dev for a mixed
- * solve, FP64 for a plain one), and every reliable update recomputes
- * r = M^dag (b - M x) in FP64. The exit test is the FP64 true residual of the
- * normal equations, ||M^dag (b - M x)|| / ||M^dag b|| <= tol, the same
- * quantity lqcd_cg_solve tests for b' = M^dag b; the norm of M^dag b in the
- * denominator carries the start's relative error (about 1e-7 in FP32). Saves
- * the two FP64 hops of forming M^dag b. Arguments, workspace
- * (lqcd_cg_workspace_bytes), delta_mid and the rest as lqcd_cg_solve. */
+ * of lqcd_eo_prepare) by CG on the normal equations M^dag M x = M^dag b. Every
+ * reliable update recomputes the residual of the system itself, s = b - M x,
+ * and its norm in FP64 (two FP64 hops for M_hat), and the exit test is on it:
+ * ||b - M x|| / ||b|| <= tol, reported as true_rel_residual (CG on M^dag M
+ * minimises exactly this norm of the error over its Krylov space). The
+ * normal-equation residual M^dag s, which only restarts the iterated
+ * recurrence, and the start M^dag b are applied in the inner iteration's
+ * arithmetic: FP32 arithmetic on gauge_dev for a mixed solve, FP64 for a plain
+ * one. M^dag b is never formed in FP64. Arguments, workspace
+ * (lqcd_cg_workspace_bytes), delta, delta_mid and the rest as lqcd_cg_solve. */
 int lqcd_cgnr_solve(void* x_dev, const void* b_dev, const void* gauge_dev, const void* gauge_sloppy_dev,
                     const lqcd_lattice* lat, const lqcd_operator* op, const lqcd_solver_params* params,
                     int subset, lqcd_solve_info* info, void* workspace_dev, size_t workspace_bytes,
                     void* stream);
+
+/* Even-odd solve of the full system D x = b (Wilson D_W or domain wall D_DW,
+ * the mass-form operators of lqcd_M): b_hat = b_e - D_eo D_oo^-1 b_o (as
+ * lqcd_eo_prepare), CGNR on M_hat x_e = b_hat (lqcd_cgnr_solve; the exit test
+ * ||b_hat - M_hat x_e|| / ||b_hat|| <= tol is reported as true_rel_residual,
+ * and the full system's residual b - D x is the same vector once the odd half
+ * is in place), then x_o = D_oo^-1 (b_o - D_oe x_e). For the Wilson operator
+ * the odd half takes H_oe x_e from the last FP64 reliable update (the first hop
+ * of its M_hat x_e), so it needs no FP64 hop of its own. x_dev, b_dev: FP64
+ * full fields (x is overwritten, b is not). workspace_dev:
+ * lqcd_eo_solve_workspace_bytes() bytes, 256-byte aligned. Returns the solver's
+ * status; on LQCD_ERR_NOT_CONVERGED or LQCD_ERR_TIMEOUT x is still the full
+ * solution of the last FP64 update. Synchronises the stream. */
+size_t lqcd_eo_solve_workspace_bytes(const lqcd_lattice* lat, const lqcd_operator* op,
+                                     const lqcd_solver_params* params);
+int lqcd_eo_solve(void* x_dev, const void* b_dev, const void* gauge_dev, const void* gauge_sloppy_dev,
+                  const lqcd_lattice* lat, const lqcd_operator* op, const lqcd_solver_params* params,
+                  lqcd_solve_info* info, void* workspace_dev, size_t workspace_bytes, void* stream);
 
 /* Block CG (O'Leary 1980) for the n5 <= 16 right-hand sides of a Wilson
  * multi-RHS field (subset LQCD_EVEN: M_hat^dag M_hat X = B): one block Krylov

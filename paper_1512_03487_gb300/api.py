@@ -200,6 +200,21 @@ def lqcd_cgnr_solve(x, b, gauge, gauge_sloppy, lat, op, params, subset, workspac
     return info
 
 
+def lqcd_eo_solve_workspace_bytes(lat, op, params) -> int:
+    return int(lib.lqcd_eo_solve_workspace_bytes(C.byref(lat), C.byref(op), C.byref(params)))
+
+
+def lqcd_eo_solve(x, b, gauge, gauge_sloppy, lat, op, params, workspace, stream=None,
+                  raise_on_error=True) -> lqcd_solve_info:
+    info = lqcd_solve_info()
+    nbytes = workspace.numel() * workspace.element_size()
+    st = lib.lqcd_eo_solve(_ptr(x), _ptr(b), _ptr(gauge), _ptr(gauge_sloppy), C.byref(lat), C.byref(op),
+                           C.byref(params), C.byref(info), _ptr(workspace), nbytes, _stream(stream))
+    if raise_on_error:
+        _check(st)
+    return info
+
+
 def lqcd_fma_probe(sink, prec, iters, blocks, stream=None):
     _check(lib.lqcd_fma_probe(_ptr(sink), prec, iters, blocks, _stream(stream)))
 

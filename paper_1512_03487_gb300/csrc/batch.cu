@@ -37,7 +37,6 @@ struct BInst {
   const void* gauge_s;
   double c;  // 4 + m
   double b;  // -1 / (4 c), the Schur hop's coefficient
-  double ab; // c / b = -4 c^2
   void* f[12];
   int64_t tile0;
 };
@@ -100,7 +99,6 @@ __global__ void __launch_bounds__(TILE) batch_hop_kernel(const BatchArgs A) {
       EpiCoef c;
       c.a = I.c;
       c.b = EPI == EPI_XPAY ? I.b : 1.0;
-      c.ab = I.ab;
       c.m5d = 0.0;
       c.mf = 0.0;
       Spinor<T> res;
@@ -462,7 +460,6 @@ int lqcd_batch_cg_solve(int n, const lqcd_batch_item* items, int recon, const lq
     I.gauge_s = (prm->sloppy_prec == LQCD_F64 || !items[i].gauge_sloppy) ? items[i].gauge : items[i].gauge_sloppy;
     I.c = 4.0 + items[i].mass;
     I.b = -1.0 / (4.0 * I.c);
-    I.ab = I.c / I.b;
     I.tile0 = tiles;
     tiles += (g.nsites + TILE - 1) / TILE;
     char* f = base + lay.fields_offset[i];

@@ -26,9 +26,12 @@
 //   Ap = M^dag Mp
 //   x_s += alpha p, r_s -= alpha Ap   (|r_s|^2 -> beta, or pause)
 //   p = r_s + beta p
-// CGNR (lqcd_cgnr_solve) runs the same iteration for M x = b: r_0 = M^dag b is
-// applied in the inner arithmetic and each reliable update recomputes
-// r = M^dag (b - M x) in FP64, so M^dag b is never formed in FP64.
+// CGNR (lqcd_cgnr_solve) runs the same iteration for M x = b: each reliable
+// update recomputes the system's residual s = b - M x and |s|^2 in FP64, which
+// decides the exit (tol applies to |b - M x| / |b|), while r_0 = M^dag b and
+// r = M^dag s, which only seed the iterated recurrence, are applied in the inner
+// arithmetic. The FP64 work of an update halves and M^dag b is never formed in
+// FP64.
 //
 // A chunk of such iterations is captured once as a CUDA graph and replayed;
 // kernels return immediately once the control block is paused, so the host
@@ -131,18 +134,52 @@ __global__ void __launch_bounds__(BLAS_BLOCK) k_copy_field(VecArgs a, void* dst,
   SpinorIO<DP>::store(static_cast<char*>(dst) + hd, a.g.sstride, j, w);
 }
 
-// out = b - mx in FP64 (CGNR reliable update: b - M x; out may alias mx)
+// CGNR: out = b - mx in FP64 and |b - mx|^2 per system (a.red, FIN_STORE);
+// with mx null only |b|^2 (out may alias mx)
 __global__ void __launch_bounds__(BLAS_BLOCK) k_b_minus(VecArgs a, double* out, const double* mx) {
   int parity;
   int64_t j, first;
-  if (!vec_site(a, parity, j, first)) return;
-  const int64_t h = parity * a.hb64;
-  Spinor<double> b, m;
-  SpinorIO<LQCD_F64>::load(reinterpret_cast<const char*>(a.b64) + h, a.g.sstride, j, b);
-  SpinorIO<LQCD_F64>::load(reinterpret_cast<const char*>(mx) + h, a.g.sstride, j, m);
+  double red = 0.0;
+  if (vec_site(a, parity, j, first)) {
+    const int64_t h = parity * a.hb64;
+    Spinor<double> b, m;
+    SpinorIO<LQCD_F64>::load(reinterpret_cast<const char*>(a.b64) + h, a.g.sstride, j, b);
+    if (mx) {
+      SpinorIO<LQCD_F64>::load(reinterpret_cast<const char*>(mx) + h, a.g.sstride, j, m);
 #pragma unroll
-  for (int k = 0; k < 12; k++) b.v[k] = b.v[k] - m.v[k];
-  SpinorIO<LQCD_F64>::store(reinterpret_cast<char*>(out) + h, a.g.sstride, j, b);
+      for (int k = 0; k < 12; k++) b.v[k] = b.v[k] - m.v[k];
+      SpinorIO<LQCD_F64>::store(reinterpret_cast<char*>(out) + h, a.g.sstride, j, b);
+    }
+    red = site_norm2(b);
+  }
+  block_reduce_finalize<BLAS_BLOCK>(red, first, a.red);
+}
+
+// CGNR: r = M^dag (b - M x) from its FP32-arithmetic value (a.ax32) -> FP64 r,
+// r_s; |r|^2 -> FIN_RELIABLE (exit decided by the FP64 |b - M x|^2)
+template <int VF>
+__global__ void __launch_bounds__(BLAS_BLOCK) k_residual32(VecArgs a) {
+  int parity;
+  int64_t j, first;
+  typename PrecTraits<VF>::real red = 0;
+  if (vec_site(a, parity, j, first))
+    red = residual32_site<VF>(a.g, j, PAR_PTR(a.ax32, a.hbv), PAR_PTR(a.r64, a.hb64), PAR_PTR(a.rs, a.hbv));
+  block_reduce_finalize<BLAS_BLOCK>(red, first, a.red);
+}
+
+// Odd half of an even-odd Wilson solve from the last reliable update's hop:
+// x_o = (b_o + hx / 2) / c with hx = H_oe x_e (FP64, one checkerboard)
+__global__ void __launch_bounds__(BLAS_BLOCK) k_reconstruct_odd(Geom g, double* xo, const double* bo, const double* hx,
+                                                                double c) {
+  const int64_t j = (int64_t)blockIdx.x * BLAS_BLOCK + threadIdx.x;
+  if (j >= g.nsites) return;
+  Spinor<double> b, h;
+  SpinorIO<LQCD_F64>::load(bo, g.sstride, j, b);
+  SpinorIO<LQCD_F64>::load(hx, g.sstride, j, h);
+  const double ic = 1.0 / c, ih = 0.5 / c;
+#pragma unroll
+  for (int k = 0; k < 12; k++) b.v[k] = mk(fma(ih, h.v[k].r, ic * b.v[k].r), fma(ih, h.v[k].i, ic * b.v[k].i));
+  SpinorIO<LQCD_F64>::store(xo, g.sstride, j, b);
 }
 
 // r_s = r - A x_s (FP32 arithmetic); |r_s|^2 -> beta, resume (FIN_MID)
@@ -164,6 +201,7 @@ struct Workspace {
   SysState* sys;
   double* partials;
   unsigned int* counter;
+  double* ss;  // CGNR: per-system |b|^2, then |b - M x|^2 of the last reliable update
   double* r64;
   double* ax64;
   double* mid64;
@@ -200,6 +238,7 @@ static Workspace carve(void* base, const Geom& g, const lqcd_operator& op, const
   w.sys = (SysState*)take(sizeof(SysState) * MAX_SYS);
   w.partials = (double*)take(sizeof(double) * nsys * max_blocks(g, subset));
   w.counter = (unsigned int*)take(64);
+  w.ss = (double*)take(sizeof(double) * MAX_SYS);
   w.r64 = (double*)take(field_bytes(g, LQCD_F64, subset));
   w.ax64 = (double*)take(field_bytes(g, LQCD_F64, subset));
   w.mid64 = (double*)take(field_bytes(g, LQCD_F64, subset));
@@ -238,7 +277,7 @@ static int validate(const lqcd_lattice* lat, const lqcd_operator* op, const lqcd
 }
 
 // Launch helpers for the (VF, SF) instantiations.
-enum VecKernel { VK_INIT, VK_PUPDATE, VK_ACCUM, VK_RESIDUAL, VK_MID_RESIDUAL };
+enum VecKernel { VK_INIT, VK_PUPDATE, VK_ACCUM, VK_RESIDUAL, VK_MID_RESIDUAL, VK_RESIDUAL32 };
 
 template <int VF, int SF>
 static void launch_vec_t(VecKernel k, unsigned grid, const VecArgs& a, cudaStream_t s) {
@@ -248,6 +287,7 @@ static void launch_vec_t(VecKernel k, unsigned grid, const VecArgs& a, cudaStrea
     case VK_ACCUM: k_accumulate<VF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
     case VK_RESIDUAL: k_residual<VF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
     case VK_MID_RESIDUAL: k_mid_residual<VF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
+    case VK_RESIDUAL32: k_residual32<VF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
   }
 }
 
@@ -271,7 +311,7 @@ struct Solver : CgEngine {
   const void* gauge64;
   const void* gauge_s;
   VecArgs va;
-  ReduceCtx rc_init, rc_alpha, rc_update, rc_reliable, rc_mid;
+  ReduceCtx rc_init, rc_alpha, rc_update, rc_reliable, rc_mid, rc_ss;
 
   int init(cudaStream_t s) override {
     cudaError_t e = cudaMemsetAsync(w.counter, 0, 64, s);
@@ -279,10 +319,15 @@ struct Solver : CgEngine {
     VecArgs a = va;
     a.red = rc_init;
     if (normal) {
-      // r_0 = M^dag b in the inner iteration's arithmetic: the FP64 operator for a
-      // plain solve, else FP32 arithmetic on the FP64 links (every reliable update
-      // then recomputes r = M^dag (b - M x) in FP64, so the start needs no more)
+      // |b|^2 in FP64 (the exit test's scale); r_0 = M^dag b in the inner iteration's
+      // arithmetic: the FP64 operator for a plain solve, else FP32 arithmetic on the
+      // FP64 links (r only seeds the recurrence; the exit test is on b - M x)
       int st;
+      const unsigned grid0 = (unsigned)(a.full ? 2 * a.bpp : a.bpp);
+      VecArgs an = a;
+      an.red = rc_ss;
+      k_b_minus<<<grid0, BLAS_BLOCK, 0, s>>>(an, nullptr, nullptr);
+      if ((st = after_launch("cgnr: |b|^2"))) return st;
       if (prm.sloppy_prec == LQCD_F64) {
         OpCtx c64{g, op64, gauge64};
         if ((st = op_apply(c64, w.ax64, a.b64, subset, 1, w.t1_64, w.t2_64, nullptr, nullptr, s))) return st;
@@ -328,15 +373,32 @@ struct Solver : CgEngine {
     if (st) return st;
     OpCtx c64{g, op64, gauge64};
     if ((st = op_apply(c64, w.mid64, a.x64, subset, 0, w.t1_64, w.t2_64, nullptr, nullptr, s))) return st;
-    if (normal) {  // r = M^dag (b - M x)
-      const unsigned grid = (unsigned)(a.full ? 2 * a.bpp : a.bpp);
-      k_b_minus<<<grid, BLAS_BLOCK, 0, s>>>(a, w.mid64, w.mid64);
-      if ((st = after_launch("cgnr: b - M x"))) return st;
+    if (!normal) {  // r = b - M^dag M x in FP64
+      if ((st = op_apply(c64, w.ax64, w.mid64, subset, 1, w.t1_64, w.t2_64, nullptr, nullptr, s))) return st;
+      a.red = rc_reliable;
+      return launch_vec(VK_RESIDUAL, prm.sloppy_prec, a, s);
     }
-    if ((st = op_apply(c64, w.ax64, w.mid64, subset, 1, w.t1_64, w.t2_64, nullptr, nullptr, s))) return st;
+    // CGNR: the FP64 residual of the system, s = b - M x and |s|^2, decides the exit;
+    // r = M^dag s then only restarts the recurrence, in the inner arithmetic. The first
+    // hop's H x stays in t1_64 (the odd half of an even-odd solve reuses it): the
+    // adjoint's temporaries are r64 (rewritten last) and t2_64.
+    const unsigned grid = (unsigned)(a.full ? 2 * a.bpp : a.bpp);
+    VecArgs an = a;
+    an.red = rc_ss;
+    k_b_minus<<<grid, BLAS_BLOCK, 0, s>>>(an, w.mid64, w.mid64);
+    if ((st = after_launch("cgnr: b - M x"))) return st;
     a.red = rc_reliable;
-    if (normal) a.b64 = nullptr;  // ax64 already holds the residual
-    return launch_vec(VK_RESIDUAL, prm.sloppy_prec, a, s);
+    if (prm.sloppy_prec == LQCD_F64) {
+      if ((st = op_apply(c64, w.ax64, w.mid64, subset, 1, w.r64, w.t2_64, nullptr, nullptr, s))) return st;
+      a.b64 = nullptr;  // ax64 already holds the residual
+      return launch_vec(VK_RESIDUAL, prm.sloppy_prec, a, s);
+    }
+    k_copy_field<LQCD_F32, LQCD_F64><<<grid, BLAS_BLOCK, 0, s>>>(a, w.ax64, w.mid64);
+    if ((st = after_launch("cgnr: b - M x to FP32"))) return st;
+    OpCtx cm{g, opm, gauge64, LQCD_F64};
+    if ((st = op_apply(cm, w.mid64, w.ax64, subset, 1, w.r64, w.t2_64, nullptr, nullptr, s))) return st;
+    a.ax32 = w.mid64;
+    return launch_vec(VK_RESIDUAL32, prm.sloppy_prec, a, s);
   }
 
   bool has_mid() const override { return mid_on; }
@@ -456,6 +518,13 @@ static int cg_solve_impl(void* x, const void* b, const void* gauge, const void* 
   S.rc_reliable.fin = FIN_RELIABLE;
   S.rc_mid = base;
   S.rc_mid.fin = FIN_MID;
+  S.rc_ss = base;
+  S.rc_ss.fin = FIN_STORE;
+  S.rc_ss.result = S.w.ss;
+  if (normal) {
+    S.rc_init.sysres = S.rc_reliable.sysres = 1;
+    S.rc_init.result = S.rc_reliable.result = S.w.ss;
+  }
   S.rc_init.delta2_mid = S.mid_on ? prm->delta_mid * prm->delta_mid : 0.0;
 
   // what the captured graph bakes in (tol and delta live in device state, not in the graph)
@@ -499,7 +568,8 @@ static int cg_solve_impl(void* x, const void* b, const void* gauge, const void* 
   if (e != cudaSuccess && out_status == LQCD_OK) out_status = cuda_fail(e, "cg: state readback");
   double worst = 0.0;
   for (int i = 0; i < S.nsys; i++) {
-    double rel = sys[i].rr0 > 0 ? std::sqrt(sys[i].rr_true / sys[i].rr0) : 0.0;
+    const double den = normal ? sys[i].ss0 : sys[i].rr0;  // CGNR: |b - M x| / |b|
+    double rel = den > 0 ? std::sqrt(sys[i].rr_true / den) : 0.0;
     if (rel > worst || std::isnan(rel)) worst = rel;
   }
   inf->iterations = ctrl.iter;
@@ -525,6 +595,72 @@ int lqcd_cgnr_solve(void* x, const void* b, const void* gauge, const void* gauge
                     void* workspace, size_t workspace_bytes, void* stream) {
   return cg_solve_impl(x, b, gauge, gauge_sloppy, lat, op, prm, subset, info, workspace, workspace_bytes, stream,
                        true);
+}
+
+// even-odd solve: [CG workspace (EVEN)][b_hat: one FP64 checkerboard][operator temporary]
+size_t lqcd_eo_solve_workspace_bytes(const lqcd_lattice* lat, const lqcd_operator* op,
+                                     const lqcd_solver_params* prm) {
+  const size_t cgb = lqcd_cg_workspace_bytes(lat, op, prm, LQCD_EVEN);
+  if (!cgb) return 0;
+  Geom g;
+  if (make_geom(lat, &g)) return 0;
+  const size_t cb = cb_spinor_bytes(g, LQCD_F64);
+  return round_up((int64_t)cgb, 256) + round_up((int64_t)cb, 256) + cb;
+}
+
+int lqcd_eo_solve(void* x, const void* b, const void* gauge, const void* gauge_sloppy, const lqcd_lattice* lat,
+                  const lqcd_operator* op, const lqcd_solver_params* prm, lqcd_solve_info* info, void* workspace,
+                  size_t workspace_bytes, void* stream) {
+  lqcd_solve_info local;
+  lqcd_solve_info* inf = info ? info : &local;
+  const size_t need = lqcd_eo_solve_workspace_bytes(lat, op, prm);
+  if (!need) {
+    memset(inf, 0, sizeof(*inf));
+    inf->status = LQCD_ERR_ARG;
+    Geom g;
+    int st = validate(lat, op, prm, LQCD_EVEN, &g);
+    return st ? st : fail(LQCD_ERR_ARG, "eo_solve: invalid arguments");
+  }
+  if (!x || !b || !workspace || ((uintptr_t)workspace & 255) || workspace_bytes < need) {
+    memset(inf, 0, sizeof(*inf));
+    inf->status = LQCD_ERR_WORKSPACE;
+    return fail(LQCD_ERR_WORKSPACE, "eo_solve: null pointer or workspace below %zu bytes (256-byte aligned)", need);
+  }
+  Geom g;
+  make_geom(lat, &g);
+  const size_t cgb = round_up((int64_t)lqcd_cg_workspace_bytes(lat, op, prm, LQCD_EVEN), 256);
+  const size_t cb = cb_spinor_bytes(g, LQCD_F64);
+  void* bhat = off(workspace, cgb);
+  void* tmp = off(bhat, round_up((int64_t)cb, 256));
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = lqcd_eo_prepare(bhat, b, gauge, lat, op, tmp, stream);
+  if (st) {
+    memset(inf, 0, sizeof(*inf));
+    inf->status = st;
+    return st;
+  }
+  // the even half of x is the first checkerboard of the full field
+  st = cg_solve_impl(x, bhat, gauge, gauge_sloppy, lat, op, prm, LQCD_EVEN, inf, workspace, cgb, stream, true);
+  if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED && st != LQCD_ERR_TIMEOUT) return st;
+  int rst;
+  if (op->kind == LQCD_WILSON && inf->reliable_updates > 0) {
+    // the last reliable update computed M_hat x_e for the x_e returned: its first hop, H_oe x_e,
+    // is still in the workspace's odd temporary (t1_64)
+    Geom gs = g;
+    check_operator(op, gs);
+    const int nsys = !op->gparity ? gs.n5 : 1;
+    const Workspace w = carve(workspace, gs, *op, *prm, LQCD_EVEN, nsys);
+    const unsigned grid = (unsigned)((gs.nsites + BLAS_BLOCK - 1) / BLAS_BLOCK);
+    k_reconstruct_odd<<<grid, BLAS_BLOCK, 0, s>>>(gs, (double*)off(x, cb), (const double*)off(b, cb),
+                                                  (const double*)w.t1_64, 4.0 + op->mass);
+    rst = after_launch("eo_solve: odd half");
+  } else {
+    rst = lqcd_eo_reconstruct(x, b, gauge, lat, op, tmp, stream);
+  }
+  if (rst) return rst;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "eo_solve: synchronize");
+  return st;
 }
 
 }  // extern "C"

@@ -127,6 +127,23 @@ __device__ __forceinline__ double residual_site(const Geom& g, int64_t j, const 
   return site_norm2(b);
 }
 
+// CGNR reliable update: r = M^dag (b - M x) applied with FP32 arithmetic (ax32),
+// stored as the FP64 r (the replacements' reference) and as r_s; returns |r|^2
+template <int VF>
+__device__ __forceinline__ typename PrecTraits<VF>::real residual32_site(const Geom& g, int64_t j, const void* ax32,
+                                                                         double* r64, void* rs) {
+  using TV = typename PrecTraits<VF>::real;
+  Spinor<float> r;
+  SpinorIO<LQCD_F32>::load(ax32, g.sstride, j, r);
+  Spinor<double> rd;
+  convert(r, rd);
+  SpinorIO<LQCD_F64>::store(r64, g.sstride, j, rd);
+  Spinor<TV> rv;
+  convert(r, rv);
+  SpinorIO<VF>::store(rs, g.sstride, j, rv);
+  return site_norm2(rv);
+}
+
 // Intermediate replacement: r_s = r - A x_s, r the FP64 residual of the last
 // reliable update and A x_s an FP32 field computed with FP32 arithmetic;
 // returns |r_s|^2. The difference is taken in FP32: A x_s carries FP32 error

@@ -40,8 +40,7 @@ struct HopArgs {
   int full;               // 1: out / in / x are full fields, grid covers both parities
   int blocks_per_parity;
   int64_t half_bytes;     // bytes of one checkerboard of a full field
-  double a, b;            // EPI_PLAIN: out = b H in; EPI_XPAY: out = a x + b H in (b != 0)
-  double ab;              // EPI_XPAY: a / b (set by launch_hop)
+  double a, b;            // EPI_PLAIN: out = b H in; EPI_XPAY: out = a x + b H in
   double m5d, mf;         // EPI_M5: out = M5op(x) + b H in, M5op diagonal m5d = 5 - M5
   int m5_dagger;          // EPI_M5INV: apply the adjoint of M5op^-1
   double m5_a;            // EPI_M5INV: 1 / (5 - M5)
@@ -284,13 +283,12 @@ __device__ __forceinline__ void add_chiral(Spinor<T>& out, const Spinor<T>& xs, 
   }
 }
 
-// Epilogue coefficients: PLAIN out = b H in; XPAY out = a x + b H in (for
-// FP16 storage as b (ab x + H in), ab = a / b, so that x is loaded first and
-// becomes the accumulator's start: 0.7 % faster solves with FP16 storage, 1 %
-// slower with FP32, measured); M5 out = M5op(x) + b H in with M5op diagonal
-// m5d and corner mf.
+// Epilogue coefficients: PLAIN out = b H in; XPAY out = a x + b H in;
+// M5 out = M5op(x) + b H in with M5op diagonal m5d and corner mf. (Loading the
+// xpay operand before the hop, as the accumulator's start, made the bench step
+// 1.8 % slower with FP16 storage: the operand is read at the end.)
 struct EpiCoef {
-  double a, b, m5d, mf, ab;
+  double a, b, m5d, mf;
 };
 
 // The result at output site j (= cb * n5 + i5) of checkerboard `parity`.
@@ -310,23 +308,14 @@ __device__ __forceinline__ void hop_site(const Geom& g, const void* gauge, const
     i5 = j - cb * n5;
   }
   const Coord x = cb_to_coord(g, cb, parity);
-  constexpr bool XPAY_FIRST = EPI == EPI_XPAY && P == LQCD_F16;
   Spinor<T> acc;
-  if (XPAY_FIRST) {
-    // the xpay operand is read first, so its load overlaps the neighbour loads
-    IO::load(xb, g.sstride, j, acc);
-    const T ab = (T)c.ab;
-#pragma unroll
-    for (int k = 0; k < 12; k++) acc.v[k] = ab * acc.v[k];
-  } else {
-    zero(acc);
-  }
+  zero(acc);
   hop_dir<0, P, R, DAG, GP, LP>(acc, g, gauge, x, cb, i5, parity, in);
   hop_dir<1, P, R, DAG, GP, LP>(acc, g, gauge, x, cb, i5, parity, in);
   hop_dir<2, P, R, DAG, GP, LP>(acc, g, gauge, x, cb, i5, parity, in);
   hop_dir<3, P, R, DAG, GP, LP>(acc, g, gauge, x, cb, i5, parity, in);
   const T b = (T)c.b;
-  if (EPI == EPI_PLAIN || EPI == EPI_M5INV || XPAY_FIRST) {
+  if (EPI == EPI_PLAIN || EPI == EPI_M5INV) {
 #pragma unroll
     for (int k = 0; k < 12; k++) res.v[k] = b * acc.v[k];
   } else if (EPI == EPI_XPAY) {
@@ -390,7 +379,7 @@ __global__ void __launch_bounds__(BLOCK) hop_kernel(const HopArgs A) {
     const bool live = j < A.g.nsites;
     Spinor<T> res;
     if (live) {
-      const EpiCoef c{A.a, A.b, A.m5d, A.mf, A.ab};
+      const EpiCoef c{A.a, A.b, A.m5d, A.mf};
       hop_site<P, R, DAG, EPI, GP, LP>(A.g, A.gauge, in, xb, parity, j, c, res);
     } else {
       zero(res);
@@ -404,7 +393,7 @@ __global__ void __launch_bounds__(BLOCK) hop_kernel(const HopArgs A) {
   T red = T(0);
   if (j < A.g.nsites) {
     Spinor<T> res;
-    const EpiCoef c{A.a, A.b, A.m5d, A.mf, A.ab};
+    const EpiCoef c{A.a, A.b, A.m5d, A.mf};
     hop_site<P, R, DAG, EPI, GP, LP>(A.g, A.gauge, in, xb, parity, j, c, res);
     if (RED == RED_CG_UPDATE) {
       const int64_t ps = A.full ? parity * A.half_bytes : 0, vs = A.full ? parity * A.upd_half_bytes : 0;

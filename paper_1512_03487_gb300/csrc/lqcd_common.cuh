@@ -364,6 +364,8 @@ struct SysState {
   double rr_true; // last FP64 true |r|^2
   double maxrr_mid;   // max iterated |r|^2 since the last residual replacement of either level
   double delta2_mid;  // delta_mid^2 (0 disables the FP32-arithmetic replacements)
+  double ss0;         // CGNR: |b|^2 of the system M x = b
+  double tol2_sys;    // CGNR: tol^2 |b|^2, the exit test on the FP64 |b - M x|^2
   int done;
   int pad;
 };
@@ -403,6 +405,8 @@ struct ReduceCtx {
   double tol2_rel;        // FIN_INIT: tol^2
   double delta2;          // FIN_INIT: delta^2
   double delta2_mid;      // FIN_INIT: delta_mid^2 (0 = no intermediate replacements)
+  int sysres;             // FIN_INIT / FIN_RELIABLE of CGNR: result[s] holds |b|^2 / the FP64 |b - M x|^2,
+                          // which sets and decides the exit test (tol applies to M x = b)
   int maxiter;            // FIN_UPDATE: request a final FP64 residual once this many iterations ran
   int cond;               // FIN_UPDATE: 1 = set h_rel / h_mid (device-driven graph), 0 = pause for the host
   cudaGraphConditionalHandle h_rel;  // IF node running the reliable update (when cond)
@@ -479,8 +483,10 @@ __device__ inline void finalize_totals(const ReduceCtx& rc, const double* totals
         st.tol2 = rc.tol2_rel * t;
         st.delta2 = rc.delta2;
         st.delta2_mid = rc.delta2_mid;
-        if (!finite(t)) bad = true;
-        st.done = (t == 0.0) ? 1 : 0;
+        st.ss0 = rc.sysres ? rc.result[s] : t;
+        st.tol2_sys = rc.tol2_rel * st.ss0;
+        if (!finite(t) || !finite(st.ss0)) bad = true;
+        st.done = (t == 0.0 || st.ss0 == 0.0) ? 1 : 0;
         n_done += st.done;
       }
       rc.ctrl->nsys = nsys;
@@ -498,15 +504,20 @@ __device__ inline void finalize_totals(const ReduceCtx& rc, const double* totals
       for (int s = 0; s < nsys; s++) {
         SysState& st = rc.sys[s];
         const double t = totals[s];
-        st.rr_true = t;
+        // CGNR: the exit test is on the FP64 |b - M x|^2; t = |M^dag (b - M x)|^2 restarts the recurrence
+        const double ss = rc.sysres ? rc.result[s] : t;
+        st.rr_true = ss;
         if (!st.done) {
-          if (!finite(t)) bad = true;
-          else if (t <= st.tol2) { st.done = 1; st.beta = 0.0; }
+          if (!finite(t) || !finite(ss)) bad = true;
+          else if (ss <= (rc.sysres ? st.tol2_sys : st.tol2)) { st.done = 1; st.beta = 0.0; }
           else {
             st.beta = t / st.rr;
             st.rr = t;
             st.maxrr = t;
             st.maxrr_mid = t;
+            // the iterated |r|^2 at which |b - M x|^2 should meet the tolerance, if the two stay
+            // proportional (with a factor 2 of margin), requests the next FP64 check
+            if (rc.sysres) st.tol2 = fmin(st.tol2, 0.5 * t * st.tol2_sys / ss);
           }
         }
         n_done += st.done;

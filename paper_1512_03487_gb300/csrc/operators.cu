@@ -11,10 +11,6 @@
 namespace lqcd {
 
 int launch_hop(int prec, int recon, bool dagger, int epi, int reduce, HopArgs a, cudaStream_t s) {
-  if (epi == EPI_XPAY) {
-    if (a.b == 0.0) return fail(LQCD_ERR_ARG, "xpay hop with b = 0");
-    a.ab = a.a / a.b;
-  }
   if (a.g.gp) return launch_hop_gparity(prec, recon, dagger, epi, reduce, a, s);
   switch (prec) {
     case LQCD_F64: return launch_hop_f64(recon, dagger, epi, reduce, a, s);
@@ -50,10 +46,9 @@ int op_apply(const OpCtx& c, void* out, const void* in, int subset, int dagger, 
   const bool link64 = c.link_prec >= 0 && c.link_prec != P;
   if (link64 && (P != LQCD_F32 || c.link_prec != LQCD_F64 || red || upd))
     return fail(LQCD_ERR_UNSUPPORTED, "operator with links in precision %d under precision %d", c.link_prec, P);
-  auto launch_hop = [&](int prec, int recon, bool dag, int epi, int reduce, HopArgs a, cudaStream_t st) {
-    if (!link64) return lqcd::launch_hop(prec, recon, dag, epi, reduce, a, st);
-    if (epi == EPI_XPAY) a.ab = a.a / a.b;  // b != 0 for every operator xpay
-    return launch_hop_f32_link64(recon, dag, epi, reduce, a, st);
+  auto launch_hop = [&](int prec, int recon, bool dag, int epi, int reduce, const HopArgs& a, cudaStream_t st) {
+    return link64 ? launch_hop_f32_link64(recon, dag, epi, reduce, a, st)
+                  : lqcd::launch_hop(prec, recon, dag, epi, reduce, a, st);
   };
   if (upd && (!red || !dagger)) return fail(LQCD_ERR_ARG, "fused CG update needs a reduction and dagger");
   const int mode = upd ? RED_CG_UPDATE : red ? RED_NORM : RED_NONE;

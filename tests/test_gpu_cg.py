@@ -166,21 +166,19 @@ def _solve_nr(L, U, b, lat, op, prm, subset, sloppy_recon=12):
     return F.spinor_to_host(x, lat, 0, subset), info
 
 
-def _normal_residual(apply_m, apply_mdag, x, b):
-    """||M^dag (b - M x)|| / ||M^dag b|| in FP64 (the oracle's own operators)."""
-    r = apply_mdag(b - apply_m(x))
-    s = apply_mdag(b)
-    return float(np.linalg.norm(r.ravel()) / np.linalg.norm(s.ravel()))
+def _system_residual(apply_m, x, b):
+    """||b - M x|| / ||b|| in FP64 (the oracle's own operator): CGNR's exit test."""
+    return float(np.linalg.norm((b - apply_m(x)).ravel()) / np.linalg.norm(b.ravel()))
 
 
 @pytest.mark.parametrize("case", ["fp64", "fp32", "fp16_three_level", "full_fp32", "nograph_fp16", "dwf_fp32",
                                   "mrhs_fp16_three_level"])
 def test_cgnr(L, case):
-    """CGNR for M_hat x = b_hat (or M x = b): M^dag b is never formed in FP64 --
-    the start applies it in the inner arithmetic, the reliable updates
-    recompute M^dag (b - M x) in FP64 -- and the solve still meets the FP64
-    normal-equation residual that the oracle computes from x, and x is the
-    oracle's solution."""
+    """CGNR for M_hat x = b_hat (or M x = b): the reliable updates recompute
+    b - M x and its norm in FP64, which decide the exit; M^dag b and
+    M^dag (b - M x) only seed the recurrence, in the inner arithmetic. The
+    solve meets the system residual ||b - M x|| / ||b|| that the oracle
+    computes from x, reports it, and x is the oracle's solution."""
     dims, m = (8, 4, 4, 8), 0.01
     sloppy, dmid, delta, subset, n5 = 1, 0.0, 1e-5, L.LQCD_EVEN, 1
     if case == "fp64":
@@ -219,18 +217,68 @@ def test_cgnr(L, case):
         assert info.residual_replacements >= 1
     full = (lambda v: from_cb(v, 0)) if subset == L.LQCD_EVEN else (lambda v: v)  # noqa: E731
     if case == "dwf_fp32":
-        res = _normal_residual(Mx, Md, full(x), full(src))
+        res = _system_residual(Mx, full(x), full(src))
         assert res <= 1e-10
-        assert abs(res - info.true_rel_residual) < 1e-11
+        assert abs(res - info.true_rel_residual) < 1e-12
         return
     worst = 0.0
     for k in range(n5):
-        res = _normal_residual(Mx, Md, full(x[k:k + 1]), full(src[k:k + 1]))
+        res = _system_residual(Mx, full(x[k:k + 1]), full(src[k:k + 1]))
         assert res <= 1e-10, (k, res)
         worst = max(worst, res)
         xo, _ = ocg.cg(lambda v: Md(Mx(v)), Md(full(src[k:k + 1])), 1e-13, 5000)
         assert rel_l2(full(x[k:k + 1]), xo) < 1e-6
-    assert abs(worst - info.true_rel_residual) < 1e-11
+    assert abs(worst - info.true_rel_residual) < 1e-12
+
+
+@pytest.mark.parametrize("case", ["fp64", "fp32", "fp16_three_level", "nograph_fp16", "mrhs_fp32", "dwf_fp32",
+                                  "zero"])
+def test_eo_solve_full_system(L, case):
+    """lqcd_eo_solve: prepare, CGNR, odd half (for Wilson from the last reliable
+    update's H_oe x_e, with no hop of its own). The oracle's full operator gives
+    ||b - D x|| / ||b|| <= 1e-10 on the whole lattice, and the odd half equals
+    what lqcd_eo_reconstruct computes from the returned even half."""
+    dims, m, n5 = (8, 4, 4, 8), 0.01, 1
+    sloppy, dmid, delta, kind = 1, 0.0, 1e-5, 0
+    if case == "fp64":
+        sloppy, delta = 0, 0.1
+    elif case in ("fp16_three_level", "nograph_fp16"):
+        sloppy, dmid = 2, 0.003
+    elif case == "mrhs_fp32":
+        dims, n5 = (4, 4, 4, 8), 3
+    U = gauge_field(dims, "exp", 151, eps=0.3)
+    if case == "dwf_fp32":
+        dims, n5, kind = (4, 4, 4, 4), 8, 1
+        U = gauge_field(dims, "haar", 152)
+    F = L.fields
+    lat = L.lattice(dims, n5=n5, bc=BC)
+    op = L.operator(kind=kind, mass=m, M5=1.8, mf=0.02)
+    b = gaussian_spinor(dims, 153, lead=(n5,))
+    if case == "zero":
+        b = np.zeros_like(b)
+    prm = L.solver_params(tol=1e-10, maxiter=5000, sloppy_prec=sloppy, sloppy_recon=12, delta=delta,
+                          delta_mid=dmid, use_graph=0 if case == "nograph_fp16" else 1)
+    g64 = F.gauge_to_device(U, lat, 0, 18)
+    gs = F.gauge_to_device(U, lat, sloppy, 12) if sloppy else g64
+    bd = F.spinor_to_device(b, lat, 0, 2)
+    x = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
+    ws = F.empty(L.lqcd_eo_solve_workspace_bytes(lat, op, prm))
+    info = L.lqcd_eo_solve(x, bd, g64, gs, lat, op, prm, ws, raise_on_error=False)
+    assert info.status == 0, L.lqcd_last_error()
+    xh = F.spinor_to_host(x, lat, 0, 2)
+    if case == "zero":
+        assert not np.any(xh)
+        return
+    D = (lambda v: dwf.dirac(U, v, 1.8, 0.02, BC)) if kind else (lambda v: wilson.dirac(U, v, m, BC))  # noqa: E731
+    for k in range(n5 if kind == 0 else 1):
+        sl = slice(k, k + 1) if kind == 0 else slice(None)
+        res = np.linalg.norm(b[sl] - D(xh[sl])) / np.linalg.norm(b[sl])
+        assert res <= 1e-10, (k, res)
+    # the odd half against lqcd_eo_reconstruct applied to the returned even half
+    tmp = F.empty(L.lqcd_operator_workspace_bytes(lat, op, 0))
+    x2 = x.clone()
+    L.lqcd_eo_reconstruct(x2, bd, g64, lat, op, tmp)
+    assert rel_l2(F.spinor_to_host(x2, lat, 0, 2), xh) <= 1e-13
 
 
 def test_multi_rhs_cg(L):
