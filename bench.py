@@ -594,9 +594,10 @@ def run_extras(L, F, flush, stream):
     out["dwf_16x4_ls16_mixed_fp32"] = dwf_bench(L, F, flush, stream)
     torch.cuda.empty_cache()
 
-    # 32^4 with 12 right-hand sides sharing the links, m = 0.01, mixed CG per RHS to 1e-10:
-    # FP32 inner (delta 1e-5), FP16 inner (delta 0.003), FP16 inner with FP32-arithmetic replacements
-    # (three levels), and block CG with FP32 inner
+    # 32^4 with 12 right-hand sides sharing the links, m = 0.01, mixed CG per RHS to 1e-10 on
+    # M_hat^dag M_hat x = b_e: FP32 inner (delta 1e-5), FP16 inner (delta 0.003), FP16 inner with
+    # FP32-arithmetic replacements (three levels), block CG with FP32 inner; and the full systems
+    # D x = b by the even-odd solve
     dims, nr = (32, 32, 32, 32), 12
     U = gauge_field(dims, "haar", config_seed(3, 0))
     lat = L.lattice(dims, n5=nr, bc=BC)
@@ -606,6 +607,7 @@ def run_extras(L, F, flush, stream):
     del U
     rhs = gaussian_spinor(dims, config_seed(3, 1), lead=(nr,))
     be = F.spinor_to_device(F.checkerboard(rhs, 0), lat, 0, 0)
+    bfull = F.spinor_to_device(rhs, lat, 0, 2)
     del rhs
     x = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
     prm = {q: L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=q, sloppy_recon=12,
@@ -625,6 +627,21 @@ def run_extras(L, F, flush, stream):
             "fp32_replacements": info.residual_replacements, "delta": prm[q].delta, "delta_mid": prm[q].delta_mid,
             "max_true_rel_residual_normal_eq": info.true_rel_residual,
             "dslash_gflops_in_solve": round(4 * nop * FLOP_PER_SITE * vh * nr / (ms * 1e-3) / 1e9, 1)}
+    # the full systems D x = b of the 12 right-hand sides by lqcd_eo_solve (CGNR, tolerance on each
+    # even-odd system's FP64 residual, FP16 storage with three levels)
+    pe = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=2, sloppy_recon=12, delta=DELTA_3LVL,
+                         delta_mid=DELTA_MID, check_interval=64)
+    xf = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
+    wse = F.empty(L.lqcd_eo_solve_workspace_bytes(lat, op, pe))
+    L.lqcd_eo_solve(xf, bfull, g64, gsl[2], lat, op, pe, wse)
+    mse, infe = _events_time(lambda: L.lqcd_eo_solve(xf, bfull, g64, gsl[2], lat, op, pe, wse), stream, flush)
+    mr["eo_solve_full_systems_fp16_three_level"] = {
+        "ms": round(mse, 3), "iterations": infe.iterations, "reliable_updates": infe.reliable_updates,
+        "fp32_replacements": infe.residual_replacements, "delta": pe.delta, "delta_mid": pe.delta_mid,
+        "max_true_rel_residual_eo_system": infe.true_rel_residual,
+        "dslash_gflops_in_solve": round((3 + 4 * (infe.iterations + infe.reliable_updates + infe.residual_replacements))
+                                        * FLOP_PER_SITE * vh * nr / (mse * 1e-3) / 1e9, 1)}
+    del xf, wse, bfull
     wsb = F.empty(L.lqcd_block_cg_workspace_bytes(lat, op, prm[1]))
     L.lqcd_block_cg_solve(x, be, g64, gsl[1], lat, op, prm[1], wsb)
     msb, infb = _events_time(lambda: L.lqcd_block_cg_solve(x, be, g64, gsl[1], lat, op, prm[1], wsb), stream, flush)
