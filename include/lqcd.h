@@ -255,7 +255,8 @@ int lqcd_fma_probe(void* sink_dev, int prec, int64_t iters, int blocks, void* st
  * residual is replaced by r - A x_s whenever it falls below delta_mid times
  * its maximum since the last replacement, with r the residual of the last
  * FP64 update, x_s the sloppy solution since then, and A applied with FP32
- * arithmetic to gauge_dev (no extra field); FP64 updates then follow delta,
+ * arithmetic on an FP32 / 12-real copy of gauge_dev that the solve makes in
+ * its workspace; FP64 updates then follow delta,
  * which this allows down to about 1e-5. The solve's result and exit test are
  * unchanged (FP64 true residual); only the update schedule differs. Ignored
  * by the block and batched solvers.
@@ -276,7 +277,8 @@ int lqcd_cg_solve(void* x_dev, const void* b_dev, const void* gauge_dev,
  * minimises exactly this norm of the error over its Krylov space). The
  * normal-equation residual M^dag s, which only restarts the iterated
  * recurrence, and the start M^dag b are applied in the inner iteration's
- * arithmetic: FP32 arithmetic on gauge_dev for a mixed solve, FP64 for a plain
+ * arithmetic: FP32 on the workspace's FP32 / 12-real copy of gauge_dev for a
+ * mixed solve, FP64 for a plain
  * one. M^dag b is never formed in FP64. Arguments, workspace
  * (lqcd_cg_workspace_bytes), delta, delta_mid and the rest as lqcd_cg_solve. */
 int lqcd_cgnr_solve(void* x_dev, const void* b_dev, const void* gauge_dev, const void* gauge_sloppy_dev,

@@ -15,9 +15,10 @@
 // recomputation costs as much as ten FP32 iterations. So whenever |r_s| falls
 // below delta_mid times its maximum since the last replacement, the iterated
 // residual is replaced by r - A x_s, with r the residual of the last FP64
-// update and A x_s applied with FP32 arithmetic to the FP64 links (accurate
-// to about 1e-7 of |r|); the FP64 updates then only follow delta, which FP32
-// accuracy allows to be as small as about 1e-5.
+// update and A x_s applied in FP32 to an FP32 / 12-real copy of the FP64 links
+// made once per solve in the workspace (accurate to about 1e-7 of |r|); the
+// FP64 updates then only follow delta, which FP32 accuracy allows to be as
+// small as about 1e-5.
 //
 // Every scalar (alpha, beta, the convergence and update decisions) lives on
 // the device and is produced by the last block of the reducing kernel, so an
@@ -167,6 +168,23 @@ __global__ void __launch_bounds__(BLAS_BLOCK) k_residual32(VecArgs a) {
   block_reduce_finalize<BLAS_BLOCK>(red, first, a.red);
 }
 
+// FP32 / 12-real copy of the FP64 links (rows 0 and 1, rounded once): the operator
+// of the CGNR start, of the updates' M^dag and of the intermediate replacements,
+// whose FP32 arithmetic needs no more than FP32 links. One thread per (parity, mu, cb).
+__global__ void __launch_bounds__(BLAS_BLOCK) k_links_to_f32r12(float4* dst, const double2* src, Geom g, int nchunk64) {
+  const int64_t t = (int64_t)blockIdx.x * BLAS_BLOCK + threadIdx.x;
+  if (t >= 8 * (int64_t)g.Vh) return;
+  const int blk = (int)(t / g.Vh);
+  const int64_t cb = t - (int64_t)blk * g.Vh;
+  const double2* s = src + (int64_t)blk * nchunk64 * g.gstride + cb;
+  float4* d = dst + (int64_t)blk * 3 * g.gstride + cb;
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const double2 a = __ldg(s + (2 * c) * g.gstride), b = __ldg(s + (2 * c + 1) * g.gstride);
+    d[c * g.gstride] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+  }
+}
+
 // Odd half of an even-odd Wilson solve from the last reliable update's hop:
 // x_o = (b_o + hx / 2) / c with hx = H_oe x_e (FP64, one checkerboard)
 __global__ void __launch_bounds__(BLAS_BLOCK) k_reconstruct_odd(Geom g, double* xo, const double* bo, const double* hx,
@@ -202,6 +220,7 @@ struct Workspace {
   double* partials;
   unsigned int* counter;
   double* ss;  // CGNR: per-system |b|^2, then |b - M x|^2 of the last reliable update
+  void* g32;   // mixed solves: FP32 / 12-real copy of the FP64 links
   double* r64;
   double* ax64;
   double* mid64;
@@ -246,6 +265,7 @@ static Workspace carve(void* base, const Geom& g, const lqcd_operator& op, const
     w.t1_64 = take(cb_spinor_bytes(g, LQCD_F64));
     if (op.kind == LQCD_DWF) w.t2_64 = take(cb_spinor_bytes(g, LQCD_F64));
   }
+  if (p.sloppy_prec != LQCD_F64) w.g32 = take((size_t)8 * g.gstride * link_bytes(LQCD_F32, 12));
   w.rs = take(field_bytes(g, VF, subset));
   w.xs = take(field_bytes(g, VF, subset));
   w.p = take(field_bytes(g, SF, subset));
@@ -302,7 +322,7 @@ static int launch_vec(VecKernel k, int sloppy, const VecArgs& a, cudaStream_t s)
 
 struct Solver : CgEngine {
   Geom g;
-  lqcd_operator op64, ops, opm;  // FP64, sloppy, and FP32 arithmetic on the FP64 links (replacements)
+  lqcd_operator op64, ops, opm;  // FP64, sloppy, and FP32 on FP32 / 12-real links from the FP64 field
   lqcd_solver_params prm;
   int subset;
   bool mid_on = false;
@@ -316,12 +336,18 @@ struct Solver : CgEngine {
   int init(cudaStream_t s) override {
     cudaError_t e = cudaMemsetAsync(w.counter, 0, 64, s);
     if (e != cudaSuccess) return cuda_fail(e, "cg: memset");
+    if (w.g32 && (normal || mid_on)) {  // FP32 links for the FP32-arithmetic operator, from this call's FP64 field
+      const unsigned grid = (unsigned)((8 * (int64_t)g.Vh + BLAS_BLOCK - 1) / BLAS_BLOCK);
+      k_links_to_f32r12<<<grid, BLAS_BLOCK, 0, s>>>((float4*)w.g32, (const double2*)gauge64, g, op64.recon == 18 ? 9 : 6);
+      int st = after_launch("cg: FP32 links");
+      if (st) return st;
+    }
     VecArgs a = va;
     a.red = rc_init;
     if (normal) {
       // |b|^2 in FP64 (the exit test's scale); r_0 = M^dag b in the inner iteration's
-      // arithmetic: the FP64 operator for a plain solve, else FP32 arithmetic on the
-      // FP64 links (r only seeds the recurrence; the exit test is on b - M x)
+      // arithmetic: the FP64 operator for a plain solve, else the FP32 operator on the
+      // FP32 link copy (r only seeds the recurrence; the exit test is on b - M x)
       int st;
       const unsigned grid0 = (unsigned)(a.full ? 2 * a.bpp : a.bpp);
       VecArgs an = a;
@@ -336,7 +362,7 @@ struct Solver : CgEngine {
         const unsigned grid = (unsigned)(a.full ? 2 * a.bpp : a.bpp);
         k_copy_field<LQCD_F32, LQCD_F64><<<grid, BLAS_BLOCK, 0, s>>>(a, w.xs, a.b64);
         if ((st = after_launch("cgnr: b to FP32"))) return st;
-        OpCtx cm{g, opm, gauge64, LQCD_F64};
+        OpCtx cm{g, opm, w.g32};
         if ((st = op_apply(cm, w.ax64, w.xs, subset, 1, w.t1_64, w.t2_64, nullptr, nullptr, s))) return st;
         k_copy_field<LQCD_F64, LQCD_F32><<<grid, BLAS_BLOCK, 0, s>>>(a, w.mid64, w.ax64);
         if ((st = after_launch("cgnr: M^dag b to FP64"))) return st;
@@ -395,7 +421,7 @@ struct Solver : CgEngine {
     }
     k_copy_field<LQCD_F32, LQCD_F64><<<grid, BLAS_BLOCK, 0, s>>>(a, w.ax64, w.mid64);
     if ((st = after_launch("cgnr: b - M x to FP32"))) return st;
-    OpCtx cm{g, opm, gauge64, LQCD_F64};
+    OpCtx cm{g, opm, w.g32};
     if ((st = op_apply(cm, w.mid64, w.ax64, subset, 1, w.r64, w.t2_64, nullptr, nullptr, s))) return st;
     a.ax32 = w.mid64;
     return launch_vec(VK_RESIDUAL32, prm.sloppy_prec, a, s);
@@ -403,11 +429,11 @@ struct Solver : CgEngine {
 
   bool has_mid() const override { return mid_on; }
 
-  // r_s = r - M^dag M x_s with FP32 arithmetic on the FP64 links. The FP64
-  // update's buffers (mid64, ax64, t1_64, t2_64) are idle here and hold the
-  // FP32 intermediates.
+  // r_s = r - M^dag M x_s with the FP32 operator on the FP32 link copy. The
+  // FP64 update's buffers (mid64, ax64, t1_64, t2_64) are idle here and hold
+  // the FP32 intermediates.
   int mid(cudaStream_t s) override {
-    OpCtx cm{g, opm, gauge64, LQCD_F64};
+    OpCtx cm{g, opm, w.g32};
     int st = op_apply(cm, w.mid64, w.xs, subset, 0, w.t1_64, w.t2_64, nullptr, nullptr, s);
     if (st) return st;
     if ((st = op_apply(cm, w.ax64, w.mid64, subset, 1, w.t1_64, w.t2_64, nullptr, nullptr, s))) return st;
@@ -475,6 +501,7 @@ static int cg_solve_impl(void* x, const void* b, const void* gauge, const void* 
   S.ops.recon = prm->sloppy_prec == LQCD_F64 ? op->recon : prm->sloppy_recon;
   S.opm = *op;
   S.opm.prec = LQCD_F32;
+  S.opm.recon = 12;  // on the workspace's FP32 / 12-real copy of the FP64 links
   S.mid_on = prm->sloppy_prec == LQCD_F16 && prm->delta_mid > 0.0;
   S.gauge64 = gauge;
   S.gauge_s = gauge_sloppy;

@@ -18,8 +18,6 @@
 // the lower half is S B^dag h, so only h is multiplied by the link.
 #pragma once
 
-#include <type_traits>
-
 #include "cg_site.cuh"
 #include "lqcd_common.cuh"
 #include "m5_scan.cuh"
@@ -195,27 +193,6 @@ __device__ __forceinline__ typename PrecTraits<P>::real load_project(const void*
   return wrap ? bc_phase<T>(g, MU) * f : f;
 }
 
-// Link in the arithmetic type T from storage precision LP. Links stored at a
-// higher precision than the arithmetic (FP64 links under FP32 arithmetic, the
-// intermediate residual replacement) are rounded once per element; the third
-// row of a 12-real link is then rebuilt in T.
-template <int LP, int R, typename T>
-__device__ __forceinline__ void load_link(const void* gauge, int64_t gs, int blk, int64_t cb, Link<T>& u) {
-  using TS = typename LinkIO<LP, R>::T;
-  if constexpr (std::is_same<TS, T>::value) {
-    LinkIO<LP, R>::load(gauge, gs, blk, cb, u);
-  } else {
-    static_assert(LP == LQCD_F64, "only FP64 links are narrowed");
-    const double2* b = reinterpret_cast<const double2*>(gauge) + (int64_t)blk * LinkIO<LP, R>::NCHUNK * gs + cb;
-#pragma unroll
-    for (int c = 0; c < LinkIO<LP, R>::NCHUNK; c++) {
-      const double2 w = __ldg(b + c * gs);
-      u.v[c] = mk((T)w.x, (T)w.y);
-    }
-    if (R == 12) rebuild_row2(u);
-  }
-}
-
 template <typename T> __device__ __forceinline__ void conj_link(Link<T>& u) {
 #pragma unroll
   for (int k = 0; k < 9; k++) u.v[k].i = -u.v[k].i;
@@ -226,7 +203,7 @@ template <typename T> __device__ __forceinline__ void conj_link(Link<T>& u) {
 // (forward, f = 0 / 1) or -1 / +1 (backward) instead of the boundary phase,
 // and the link is conjugated when its owner -- the site for the forward hop,
 // the neighbour (flavour f') for the backward hop -- is flavour 1.
-template <int MU, int P, int R, bool DAG, bool GP = false, int LP = P>
+template <int MU, int P, int R, bool DAG, bool GP = false>
 __device__ __forceinline__ void hop_dir(Spinor<typename PrecTraits<P>::real>& acc, const Geom& g,
                                         const void* gauge, const Coord& x, int64_t cb, int64_t i5,
                                         int parity, const void* in) {
@@ -246,7 +223,7 @@ __device__ __forceinline__ void hop_dir(Spinor<typename PrecTraits<P>::real>& ac
     Half<T> h;
     const T f = sgn * load_project<P, MU, SF>(in, g, nb * n5 + f_nb, wrap, h);
     Link<T> u;
-    load_link<LP, R>(gauge, g.gstride, parity * 4 + MU, cb, u);
+    LinkIO<P, R>::load(gauge, g.gstride, parity * 4 + MU, cb, u);
     if (GP && i5 == 1) conj_link(u);
     Half<T> w;
     link_mul(u, h, w);
@@ -265,7 +242,7 @@ __device__ __forceinline__ void hop_dir(Spinor<typename PrecTraits<P>::real>& ac
     Half<T> h;
     const T f = sgn * load_project<P, MU, -SF>(in, g, nb * n5 + f_nb, wrap, h);
     Link<T> u;
-    load_link<LP, R>(gauge, g.gstride, (1 - parity) * 4 + MU, nb, u);
+    LinkIO<P, R>::load(gauge, g.gstride, (1 - parity) * 4 + MU, nb, u);
     if (GP && f_nb == 1) conj_link(u);
     Half<T> w;
     link_mul_dag(u, h, w);
@@ -292,7 +269,7 @@ struct EpiCoef {
 };
 
 // The result at output site j (= cb * n5 + i5) of checkerboard `parity`.
-template <int P, int R, bool DAG, int EPI, bool GP = false, int LP = P>
+template <int P, int R, bool DAG, int EPI, bool GP = false>
 __device__ __forceinline__ void hop_site(const Geom& g, const void* gauge, const void* in, const void* xb,
                                          int parity, int64_t j, const EpiCoef& c,
                                          Spinor<typename PrecTraits<P>::real>& res) {
@@ -310,10 +287,10 @@ __device__ __forceinline__ void hop_site(const Geom& g, const void* gauge, const
   const Coord x = cb_to_coord(g, cb, parity);
   Spinor<T> acc;
   zero(acc);
-  hop_dir<0, P, R, DAG, GP, LP>(acc, g, gauge, x, cb, i5, parity, in);
-  hop_dir<1, P, R, DAG, GP, LP>(acc, g, gauge, x, cb, i5, parity, in);
-  hop_dir<2, P, R, DAG, GP, LP>(acc, g, gauge, x, cb, i5, parity, in);
-  hop_dir<3, P, R, DAG, GP, LP>(acc, g, gauge, x, cb, i5, parity, in);
+  hop_dir<0, P, R, DAG, GP>(acc, g, gauge, x, cb, i5, parity, in);
+  hop_dir<1, P, R, DAG, GP>(acc, g, gauge, x, cb, i5, parity, in);
+  hop_dir<2, P, R, DAG, GP>(acc, g, gauge, x, cb, i5, parity, in);
+  hop_dir<3, P, R, DAG, GP>(acc, g, gauge, x, cb, i5, parity, in);
   const T b = (T)c.b;
   if (EPI == EPI_PLAIN || EPI == EPI_M5INV) {
 #pragma unroll
@@ -356,9 +333,7 @@ template <typename T> __device__ __forceinline__ T norm2_site(const Spinor<T>& r
   return s;
 }
 
-// LP: storage precision of the links (P except for the FP32-arithmetic
-// operator on FP64 links of the intermediate residual replacement).
-template <int P, int R, bool DAG, int EPI, int RED, int BLOCK, bool GP = false, int LP = P>
+template <int P, int R, bool DAG, int EPI, int RED, int BLOCK, bool GP = false>
 __global__ void __launch_bounds__(BLOCK) hop_kernel(const HopArgs A) {
   using T = typename PrecTraits<P>::real;
   if (gate_closed(A.gate)) return;
@@ -380,7 +355,7 @@ __global__ void __launch_bounds__(BLOCK) hop_kernel(const HopArgs A) {
     Spinor<T> res;
     if (live) {
       const EpiCoef c{A.a, A.b, A.m5d, A.mf};
-      hop_site<P, R, DAG, EPI, GP, LP>(A.g, A.gauge, in, xb, parity, j, c, res);
+      hop_site<P, R, DAG, EPI, GP>(A.g, A.gauge, in, xb, parity, j, c, res);
     } else {
       zero(res);
     }
@@ -394,7 +369,7 @@ __global__ void __launch_bounds__(BLOCK) hop_kernel(const HopArgs A) {
   if (j < A.g.nsites) {
     Spinor<T> res;
     const EpiCoef c{A.a, A.b, A.m5d, A.mf};
-    hop_site<P, R, DAG, EPI, GP, LP>(A.g, A.gauge, in, xb, parity, j, c, res);
+    hop_site<P, R, DAG, EPI, GP>(A.g, A.gauge, in, xb, parity, j, c, res);
     if (RED == RED_CG_UPDATE) {
       const int64_t ps = A.full ? parity * A.half_bytes : 0, vs = A.full ? parity * A.upd_half_bytes : 0;
       red = update_site_ap<vec_prec(P), P>(A.g, j, A.red.sys[sys_of(j, A.red.nsys)].alpha,

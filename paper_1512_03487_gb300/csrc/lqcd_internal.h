@@ -12,8 +12,6 @@ int launch_hop_f64(int recon, bool dagger, int epi, int reduce, HopArgs a, cudaS
 int launch_hop_f32(int recon, bool dagger, int epi, int reduce, HopArgs a, cudaStream_t s);
 int launch_hop_f16(int recon, bool dagger, int epi, int reduce, HopArgs a, cudaStream_t s);
 int launch_hop_gparity(int prec, int recon, bool dagger, int epi, int reduce, HopArgs a, cudaStream_t s);
-// FP32 spinors and arithmetic on FP64 links (recon 18 / 12), no reduction
-int launch_hop_f32_link64(int recon, bool dagger, int epi, int reduce, HopArgs a, cudaStream_t s);
 
 // Blocks of the hop kernel per checkerboard (the reduction buffers are sized from it).
 constexpr int HOP_BLOCK = 128;
@@ -37,7 +35,6 @@ struct OpCtx {
   Geom g;
   lqcd_operator op;   // kind, mass, M5, mf, prec, recon
   const void* gauge;
-  int link_prec = -1; // storage precision of gauge when it differs from op.prec (LQCD_F64 under LQCD_F32)
 };
 // out = M in (subset LQCD_FULL) or M_hat in (LQCD_EVEN), dagger; optional |out|^2
 // reduction and gate. t1, t2: odd checkerboard temporaries (EVEN subset).

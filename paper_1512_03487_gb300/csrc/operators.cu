@@ -43,13 +43,6 @@ static HopArgs base_args(const OpCtx& c, const ReduceCtx* red, const Control* ga
 int op_apply(const OpCtx& c, void* out, const void* in, int subset, int dagger, void* t1, void* t2,
              const ReduceCtx* red, const Control* gate, cudaStream_t s, const HopUpdate* upd) {
   const int P = c.op.prec, R = c.op.recon;
-  const bool link64 = c.link_prec >= 0 && c.link_prec != P;
-  if (link64 && (P != LQCD_F32 || c.link_prec != LQCD_F64 || red || upd))
-    return fail(LQCD_ERR_UNSUPPORTED, "operator with links in precision %d under precision %d", c.link_prec, P);
-  auto launch_hop = [&](int prec, int recon, bool dag, int epi, int reduce, const HopArgs& a, cudaStream_t st) {
-    return link64 ? launch_hop_f32_link64(recon, dag, epi, reduce, a, st)
-                  : lqcd::launch_hop(prec, recon, dag, epi, reduce, a, st);
-  };
   if (upd && (!red || !dagger)) return fail(LQCD_ERR_ARG, "fused CG update needs a reduction and dagger");
   const int mode = upd ? RED_CG_UPDATE : red ? RED_NORM : RED_NONE;
   auto set_upd = [&](HopArgs& a) {
