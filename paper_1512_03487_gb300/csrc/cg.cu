@@ -17,8 +17,8 @@
 // residual is replaced by r - A x_s, with r the residual of the last FP64
 // update and A x_s applied in FP32 to an FP32 / 12-real copy of the FP64 links
 // made once per solve in the workspace (accurate to about 1e-7 of |r|); the
-// FP64 updates then only follow delta, which FP32 accuracy allows to be as
-// small as about 1e-5.
+// FP64 updates then only follow delta, which FP32 accuracy allows down to a
+// few times 1e-6.
 //
 // Every scalar (alpha, beta, the convergence and update decisions) lives on
 // the device and is produced by the last block of the reducing kernel, so an
@@ -32,7 +32,9 @@
 // decides the exit (tol applies to |b - M x| / |b|), while r_0 = M^dag b and
 // r = M^dag s, which only seed the iterated recurrence, are applied in the inner
 // arithmetic. The FP64 work of an update halves and M^dag b is never formed in
-// FP64.
+// FP64. lqcd_eo_solve wraps it for the full system D x = b: preparation, CGNR
+// on the even checkerboard, and (Wilson) the odd half from the H_oe x_e that
+// the last update's M x left in the workspace.
 //
 // A chunk of such iterations is captured once as a CUDA graph and replayed;
 // kernels return immediately once the control block is paused, so the host
