@@ -112,3 +112,35 @@ def test_cgnr_nan_zero_and_cap(L, sloppy, delta_mid, use_graph):
     res = np.linalg.norm(be - wilson.schur(U, xe, m, BC)) / np.linalg.norm(be)
     assert abs(res - info.true_rel_residual) <= 1e-9 * res
     _healthy(L, U, b, dims, m)
+
+
+def test_eo_solve_iteration_cap_returns_full_solution(L):
+    """lqcd_eo_solve stopped by the iteration cap still returns the full
+    solution of its last FP64 update: the odd half is what lqcd_eo_reconstruct
+    gives for the returned even half, and the reported residual is that of the
+    even-odd system for the returned x_e."""
+    from tests.layout import rel_l2
+    dims, m = (4, 4, 4, 8), 0.05
+    U = gauge_field(dims, "haar", 841)
+    b = gaussian_spinor(dims, 842, lead=(1,))
+    F = L.fields
+    lat = L.lattice(dims, bc=BC)
+    op = L.operator(mass=m)
+    prm = L.solver_params(tol=1e-12, maxiter=10, sloppy_prec=1, sloppy_recon=12, delta=3e-6, check_interval=4)
+    g64 = F.gauge_to_device(U, lat, 0, 18)
+    gs = F.gauge_to_device(U, lat, 1, 12)
+    bd = F.spinor_to_device(b, lat, 0, 2)
+    x = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
+    ws = F.empty(L.lqcd_eo_solve_workspace_bytes(lat, op, prm))
+    info = L.lqcd_eo_solve(x, bd, g64, gs, lat, op, prm, ws, raise_on_error=False)
+    assert info.status == ERR_NOT_CONVERGED
+    xh = F.spinor_to_host(x, lat, 0, 2)
+    tmp = F.empty(L.lqcd_operator_workspace_bytes(lat, op, 0))
+    x2 = x.clone()
+    L.lqcd_eo_reconstruct(x2, bd, g64, lat, op, tmp)
+    assert rel_l2(F.spinor_to_host(x2, lat, 0, 2), xh) <= 1e-13
+    xe = wilson.restrict(xh, 0)
+    bh = wilson.prepare_source(U, b, m, BC)
+    res = np.linalg.norm(bh - wilson.schur(U, xe, m, BC)) / np.linalg.norm(bh)
+    assert abs(res - info.true_rel_residual) <= 1e-9 * res
+    _healthy(L, U, to_cb(b, 0), dims, m)

@@ -114,3 +114,27 @@ def test_even_odd_solve_full_residual(L, sloppy, mask, solver):
     xh = F.spinor_to_host(x, lat, 0, 2)
     res = np.linalg.norm(b - gparity.dirac(U, xh, m, BC, gd)) / np.linalg.norm(b)
     assert info.status == 0 and res <= 1e-9, (info.iterations, res)
+
+
+@pytest.mark.parametrize("sloppy", [0, 1])
+def test_eo_solve_gparity(L, sloppy):
+    """lqcd_eo_solve with G-parity: the odd half comes from the last update's
+    G-parity hop H_oe x_e; the oracle's two-flavour operator gives the full
+    system's residual <= 1e-10."""
+    dims, m, mask = (4, 4, 4, 8), 0.05, 6
+    gd = MASKS[mask]
+    U = gauge_field(dims, "haar", 1931)
+    b = gaussian_spinor(dims, 1932, lead=(2,))
+    F = L.fields
+    lat = L.lattice(dims, n5=2, bc=BC)
+    op = L.operator(mass=m, gparity=mask)
+    prm = L.solver_params(tol=1e-10, maxiter=5000, sloppy_prec=sloppy, sloppy_recon=12 if sloppy else 18,
+                          delta=3e-6 if sloppy else 0.1)
+    g64 = F.gauge_to_device(U, lat, 0, 18)
+    gs = F.gauge_to_device(U, lat, 1, 12) if sloppy else g64
+    x = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
+    ws = F.empty(L.lqcd_eo_solve_workspace_bytes(lat, op, prm))
+    info = L.lqcd_eo_solve(x, F.spinor_to_device(b, lat, 0, 2), g64, gs, lat, op, prm, ws)
+    xh = F.spinor_to_host(x, lat, 0, 2)
+    res = np.linalg.norm(b - gparity.dirac(U, xh, m, BC, gd)) / np.linalg.norm(b)
+    assert info.status == 0 and res <= 1e-10, (info.iterations, res)
