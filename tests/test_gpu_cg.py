@@ -232,7 +232,7 @@ def test_cgnr(L, case):
 
 
 @pytest.mark.parametrize("case", ["fp64", "fp32", "fp16_three_level", "nograph_fp16", "mrhs_fp32", "dwf_fp32",
-                                  "zero"])
+                                  "dwf6_fp16_three_level", "zero"])
 def test_eo_solve_full_system(L, case):
     """lqcd_eo_solve: prepare, CGNR, odd half (for Wilson from the last reliable
     update's H_oe x_e, with no hop of its own). The oracle's full operator gives
@@ -247,9 +247,12 @@ def test_eo_solve_full_system(L, case):
     elif case == "mrhs_fp32":
         dims, n5 = (4, 4, 4, 8), 3
     U = gauge_field(dims, "exp", 151, eps=0.3)
-    if case == "dwf_fp32":
-        dims, n5, kind = (4, 4, 4, 4), 8, 1
+    if case.startswith("dwf"):
+        # L_s = 8 runs M5op^-1 in the hop's epilogue, L_s = 6 the closed-form kernel
+        dims, n5, kind = (4, 4, 4, 4), (6 if case.startswith("dwf6") else 8), 1
         U = gauge_field(dims, "haar", 152)
+        if case == "dwf6_fp16_three_level":
+            sloppy, dmid = 2, 0.003
     F = L.fields
     lat = L.lattice(dims, n5=n5, bc=BC)
     op = L.operator(kind=kind, mass=m, M5=1.8, mf=0.02)
