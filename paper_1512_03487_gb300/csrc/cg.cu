@@ -10,7 +10,9 @@
 // its maximum since the last update (or below the tolerance) the residual
 // r = b - A x is recomputed with the FP64 operator.
 //
-// With FP16 storage a third level sits between the two (delta_mid > 0): FP16
+// With FP16 storage the iterated residual r_s is stored in FP16 as well (its
+// rounding is relative to the current residual; x_s stays FP32), and a third
+// level sits between the two (delta_mid > 0): FP16
 // needs a fresh residual every two to three decades, and on GB300 an FP64
 // recomputation costs as much as ten FP32 iterations. So whenever |r_s| falls
 // below delta_mid times its maximum since the last replacement, the iterated
@@ -59,9 +61,9 @@ struct VecArgs {
   const double* ax64; // FP64 A x
   const void* ax32;   // FP32 A x_s of the intermediate replacement (FP32 field)
   void* xs;           // sloppy-vector solution increment (VF)
-  void* rs;           // sloppy-vector residual (VF)
+  void* rs;           // sloppy-vector residual (rs_prec)
   void* p;            // search direction (SF)
-  int64_t hb64, hbv, hbs;  // bytes of one checkerboard per format
+  int64_t hb64, hbv, hbs, hbr;  // bytes of one checkerboard per format (FP64, VF, SF, r_s)
   SysState* sys;
   ReduceCtx red;
   const Control* gate;
@@ -88,8 +90,9 @@ __global__ void __launch_bounds__(BLAS_BLOCK) k_init(VecArgs a) {
   int64_t j, first;
   double red = 0.0;
   if (vec_site(a, parity, j, first))
-    red = init_site<VF, SF>(a.g, j, PAR_PTR(a.b64, a.hb64), PAR_PTR(a.r64, a.hb64), PAR_PTR(a.x64, a.hb64),
-                            PAR_PTR(a.rs, a.hbv), PAR_PTR(a.xs, a.hbv), PAR_PTR(a.p, a.hbs));
+    red = init_site<VF, SF, rs_prec(SF)>(a.g, j, PAR_PTR(a.b64, a.hb64), PAR_PTR(a.r64, a.hb64),
+                                         PAR_PTR(a.x64, a.hb64), PAR_PTR(a.rs, a.hbr), PAR_PTR(a.xs, a.hbv),
+                                         PAR_PTR(a.p, a.hbs));
   block_reduce_finalize<BLAS_BLOCK>(red, first, a.red);
 }
 
@@ -100,7 +103,8 @@ __global__ void __launch_bounds__(BLAS_BLOCK) k_pupdate(VecArgs a) {
   int parity;
   int64_t j, first;
   if (!vec_site(a, parity, j, first)) return;
-  pupdate_site<VF, SF>(a.g, j, a.sys[sys_of(j, a.red.nsys)].beta, PAR_PTR(a.rs, a.hbv), PAR_PTR(a.p, a.hbs));
+  pupdate_site<VF, SF, rs_prec(SF)>(a.g, j, a.sys[sys_of(j, a.red.nsys)].beta, PAR_PTR(a.rs, a.hbr),
+                                    PAR_PTR(a.p, a.hbs));
 }
 
 // x += x_s (FP64); x_s = 0
@@ -113,14 +117,14 @@ __global__ void __launch_bounds__(BLAS_BLOCK) k_accumulate(VecArgs a) {
 }
 
 // r = b - A x (FP64), r_s = r; |r|^2 -> done flags, beta, resume
-template <int VF>
+template <int VF, int RF>
 __global__ void __launch_bounds__(BLAS_BLOCK) k_residual(VecArgs a) {
   int parity;
   int64_t j, first;
   double red = 0.0;
   if (vec_site(a, parity, j, first))
-    red = residual_site<VF>(a.g, j, PAR_PTR(a.b64, a.hb64), PAR_PTR(a.ax64, a.hb64), PAR_PTR(a.r64, a.hb64),
-                            PAR_PTR(a.rs, a.hbv));
+    red = residual_site<VF, RF>(a.g, j, PAR_PTR(a.b64, a.hb64), PAR_PTR(a.ax64, a.hb64), PAR_PTR(a.r64, a.hb64),
+                                PAR_PTR(a.rs, a.hbr));
   block_reduce_finalize<BLAS_BLOCK>(red, first, a.red);
 }
 // dst = src between formats (the CGNR start: M^dag b in FP32 arithmetic)
@@ -160,13 +164,13 @@ __global__ void __launch_bounds__(BLAS_BLOCK) k_b_minus(VecArgs a, double* out, 
 
 // CGNR: r = M^dag (b - M x) from its FP32-arithmetic value (a.ax32) -> FP64 r,
 // r_s; |r|^2 -> FIN_RELIABLE (exit decided by the FP64 |b - M x|^2)
-template <int VF>
+template <int VF, int RF>
 __global__ void __launch_bounds__(BLAS_BLOCK) k_residual32(VecArgs a) {
   int parity;
   int64_t j, first;
   typename PrecTraits<VF>::real red = 0;
   if (vec_site(a, parity, j, first))
-    red = residual32_site<VF>(a.g, j, PAR_PTR(a.ax32, a.hbv), PAR_PTR(a.r64, a.hb64), PAR_PTR(a.rs, a.hbv));
+    red = residual32_site<VF, RF>(a.g, j, PAR_PTR(a.ax32, a.hbv), PAR_PTR(a.r64, a.hb64), PAR_PTR(a.rs, a.hbr));
   block_reduce_finalize<BLAS_BLOCK>(red, first, a.red);
 }
 
@@ -203,13 +207,13 @@ __global__ void __launch_bounds__(BLAS_BLOCK) k_reconstruct_odd(Geom g, double* 
 }
 
 // r_s = r - A x_s (FP32 arithmetic); |r_s|^2 -> beta, resume (FIN_MID)
-template <int VF>
+template <int VF, int RF>
 __global__ void __launch_bounds__(BLAS_BLOCK) k_mid_residual(VecArgs a) {
   int parity;
   int64_t j, first;
   double red = 0.0;
   if (vec_site(a, parity, j, first))
-    red = mid_residual_site<VF>(a.g, j, PAR_PTR(a.r64, a.hb64), PAR_PTR(a.ax32, a.hbv), PAR_PTR(a.rs, a.hbv));
+    red = mid_residual_site<VF, RF>(a.g, j, PAR_PTR(a.r64, a.hb64), PAR_PTR(a.ax32, a.hbv), PAR_PTR(a.rs, a.hbr));
   block_reduce_finalize<BLAS_BLOCK>(red, first, a.red);
 }
 #undef PAR_PTR
@@ -268,7 +272,7 @@ static Workspace carve(void* base, const Geom& g, const lqcd_operator& op, const
     if (op.kind == LQCD_DWF) w.t2_64 = take(cb_spinor_bytes(g, LQCD_F64));
   }
   if (p.sloppy_prec != LQCD_F64) w.g32 = take((size_t)8 * g.gstride * link_bytes(LQCD_F32, 12));
-  w.rs = take(field_bytes(g, VF, subset));
+  w.rs = take(field_bytes(g, rs_prec(SF), subset));
   w.xs = take(field_bytes(g, VF, subset));
   w.p = take(field_bytes(g, SF, subset));
   w.mp = take(field_bytes(g, SF, subset));
@@ -307,9 +311,9 @@ static void launch_vec_t(VecKernel k, unsigned grid, const VecArgs& a, cudaStrea
     case VK_INIT: k_init<VF, SF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
     case VK_PUPDATE: k_pupdate<VF, SF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
     case VK_ACCUM: k_accumulate<VF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
-    case VK_RESIDUAL: k_residual<VF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
-    case VK_MID_RESIDUAL: k_mid_residual<VF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
-    case VK_RESIDUAL32: k_residual32<VF><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
+    case VK_RESIDUAL: k_residual<VF, rs_prec(SF)><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
+    case VK_MID_RESIDUAL: k_mid_residual<VF, rs_prec(SF)><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
+    case VK_RESIDUAL32: k_residual32<VF, rs_prec(SF)><<<grid, BLAS_BLOCK, 0, s>>>(a); break;
   }
 }
 
@@ -385,7 +389,7 @@ struct Solver : CgEngine {
     ru.cond = cond;
     ru.h_rel = h_rel;
     ru.h_mid = h_mid;
-    const HopUpdate upd{w.p, w.xs, w.rs, va.hbv};
+    const HopUpdate upd{w.p, w.xs, w.rs, va.hbv, va.hbr};
     return op_apply(cs, nullptr, w.mp, subset, 1, w.t1_s, w.t2_s, &ru, w.ctrl, s, &upd);
   }
 
@@ -525,6 +529,7 @@ static int cg_solve_impl(void* x, const void* b, const void* gauge, const void* 
   a.hb64 = (int64_t)cb_spinor_bytes(S.g, LQCD_F64);
   a.hbv = (int64_t)cb_spinor_bytes(S.g, VF);
   a.hbs = (int64_t)cb_spinor_bytes(S.g, SF);
+  a.hbr = (int64_t)cb_spinor_bytes(S.g, rs_prec(SF));
   a.sys = S.w.sys;
   ReduceCtx base;
   memset(&base, 0, sizeof(base));

@@ -1,8 +1,10 @@
 // Per-site bodies of the conjugate-gradient vector kernels, shared by the
 // single-lattice solver (cg.cu) and the batched solver (batch.cu). VF is the
-// format of the iterated vectors x_s, r_s (FP64 or FP32); SF the format of the
-// vectors the Dslash reads and writes, p and Ap (FP64, FP32 or FP16). Each
-// returning function gives the site's contribution to the next reduction.
+// format of the iterated solution x_s (FP64 or FP32) and the arithmetic of the
+// iterated vectors, RF the storage of the iterated residual r_s (VF, or FP16
+// with FP16 storage); SF the format of the vectors the Dslash reads and writes,
+// p and Ap (FP64, FP32 or FP16). Each returning function gives the site's
+// contribution to the next reduction.
 #pragma once
 
 #include "lqcd_common.cuh"
@@ -23,7 +25,7 @@ template <typename TD, typename TS> __device__ __forceinline__ void convert(cons
 }
 
 // r = b, r_s = b, p = b, x_s = 0, x = 0; returns |b|^2
-template <int VF, int SF>
+template <int VF, int SF, int RF = VF>
 __device__ __forceinline__ double init_site(const Geom& g, int64_t j, const double* b64, double* r64, double* x64,
                                             void* rs, void* xs, void* p) {
   using TV = typename PrecTraits<VF>::real;
@@ -36,7 +38,7 @@ __device__ __forceinline__ double init_site(const Geom& g, int64_t j, const doub
   Spinor<TV> bv, zv;
   convert(b, bv);
   zero(zv);
-  SpinorIO<VF>::store(rs, g.sstride, j, bv);
+  SpinorIO<RF>::store(rs, g.sstride, j, bv);
   SpinorIO<VF>::store(xs, g.sstride, j, zv);
   Spinor<TS> bs;
   convert(b, bs);
@@ -45,7 +47,7 @@ __device__ __forceinline__ double init_site(const Geom& g, int64_t j, const doub
 }
 
 // x_s += alpha p; r_s -= alpha Ap with Ap given in registers; returns |r_s|^2 (in VF's type)
-template <int VF, int SF, typename TA>
+template <int VF, int SF, int RF = VF, typename TA>
 __device__ __forceinline__ typename PrecTraits<VF>::real update_site_ap(const Geom& g, int64_t j, double alpha_d, const void* p_,
                                                  const Spinor<TA>& ap, void* xs, void* rs) {
   using TV = typename PrecTraits<VF>::real;
@@ -55,34 +57,34 @@ __device__ __forceinline__ typename PrecTraits<VF>::real update_site_ap(const Ge
   SpinorIO<SF>::load(p_, g.sstride, j, p);
   Spinor<TV> x, r;
   SpinorIO<VF>::load(xs, g.sstride, j, x);
-  SpinorIO<VF>::load(rs, g.sstride, j, r);
+  SpinorIO<RF>::load(rs, g.sstride, j, r);
 #pragma unroll
   for (int k = 0; k < 12; k++) {
     x.v[k] = mk(fma(alpha, (TV)p.v[k].r, x.v[k].r), fma(alpha, (TV)p.v[k].i, x.v[k].i));
     r.v[k] = mk(fma(-alpha, (TV)ap.v[k].r, r.v[k].r), fma(-alpha, (TV)ap.v[k].i, r.v[k].i));
   }
   SpinorIO<VF>::store(xs, g.sstride, j, x);
-  SpinorIO<VF>::store(rs, g.sstride, j, r);
+  SpinorIO<RF>::store(rs, g.sstride, j, r);
   return site_norm2(r);
 }
 
 // x_s += alpha p; r_s -= alpha Ap; returns |r_s|^2 (in VF's type)
-template <int VF, int SF>
+template <int VF, int SF, int RF = VF>
 __device__ __forceinline__ typename PrecTraits<VF>::real update_site(const Geom& g, int64_t j, double alpha_d, const void* p_,
                                               const void* ap_, void* xs, void* rs) {
   Spinor<typename PrecTraits<SF>::real> ap;
   SpinorIO<SF>::load(ap_, g.sstride, j, ap);
-  return update_site_ap<VF, SF>(g, j, alpha_d, p_, ap, xs, rs);
+  return update_site_ap<VF, SF, RF>(g, j, alpha_d, p_, ap, xs, rs);
 }
 
 // p = r_s + beta p
-template <int VF, int SF>
+template <int VF, int SF, int RF = VF>
 __device__ __forceinline__ void pupdate_site(const Geom& g, int64_t j, double beta_d, const void* rs, void* pp) {
   using TV = typename PrecTraits<VF>::real;
   using TS = typename PrecTraits<SF>::real;
   const TS beta = (TS)beta_d;
   Spinor<TV> r;
-  SpinorIO<VF>::load(rs, g.sstride, j, r);
+  SpinorIO<RF>::load(rs, g.sstride, j, r);
   Spinor<TS> p;
   SpinorIO<SF>::load(pp, g.sstride, j, p);
 #pragma unroll
@@ -107,7 +109,7 @@ __device__ __forceinline__ void accumulate_site(const Geom& g, int64_t j, double
 
 // r = b - A x (FP64), r_s = r; returns |r|^2 in FP64. With b64 null, ax64
 // already holds the residual (CGNR: M^dag (b - M x)) and r = ax.
-template <int VF>
+template <int VF, int RF = VF>
 __device__ __forceinline__ double residual_site(const Geom& g, int64_t j, const double* b64, const double* ax64,
                                                 double* r64, void* rs) {
   using TV = typename PrecTraits<VF>::real;
@@ -123,13 +125,13 @@ __device__ __forceinline__ double residual_site(const Geom& g, int64_t j, const 
   SpinorIO<LQCD_F64>::store(r64, g.sstride, j, b);
   Spinor<TV> rv;
   convert(b, rv);
-  SpinorIO<VF>::store(rs, g.sstride, j, rv);
+  SpinorIO<RF>::store(rs, g.sstride, j, rv);
   return site_norm2(b);
 }
 
 // CGNR reliable update: r = M^dag (b - M x) applied with FP32 arithmetic (ax32),
 // stored as the FP64 r (the replacements' reference) and as r_s; returns |r|^2
-template <int VF>
+template <int VF, int RF = VF>
 __device__ __forceinline__ typename PrecTraits<VF>::real residual32_site(const Geom& g, int64_t j, const void* ax32,
                                                                          double* r64, void* rs) {
   using TV = typename PrecTraits<VF>::real;
@@ -140,7 +142,7 @@ __device__ __forceinline__ typename PrecTraits<VF>::real residual32_site(const G
   SpinorIO<LQCD_F64>::store(r64, g.sstride, j, rd);
   Spinor<TV> rv;
   convert(r, rv);
-  SpinorIO<VF>::store(rs, g.sstride, j, rv);
+  SpinorIO<RF>::store(rs, g.sstride, j, rv);
   return site_norm2(rv);
 }
 
@@ -148,7 +150,7 @@ __device__ __forceinline__ typename PrecTraits<VF>::real residual32_site(const G
 // reliable update and A x_s an FP32 field computed with FP32 arithmetic;
 // returns |r_s|^2. The difference is taken in FP32: A x_s carries FP32 error
 // already, and the subtraction adds at most one rounding of r_s itself.
-template <int VF>
+template <int VF, int RF = VF>
 __device__ __forceinline__ typename PrecTraits<VF>::real mid_residual_site(const Geom& g, int64_t j, const double* r64, const void* ax32,
                                                     void* rs) {
   using TV = typename PrecTraits<VF>::real;
@@ -160,7 +162,7 @@ __device__ __forceinline__ typename PrecTraits<VF>::real mid_residual_site(const
 #pragma unroll
   for (int k = 0; k < 12; k++)
     rv.v[k] = mk((TV)((float)r.v[k].r - ax.v[k].r), (TV)((float)r.v[k].i - ax.v[k].i));
-  SpinorIO<VF>::store(rs, g.sstride, j, rv);
+  SpinorIO<RF>::store(rs, g.sstride, j, rv);
   return site_norm2(rv);
 }
 

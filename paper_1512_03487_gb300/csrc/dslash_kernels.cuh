@@ -50,8 +50,9 @@ struct HopArgs {
   // out; x_s and r_s in vec_prec of it (upd_half_bytes: one checkerboard).
   const void* upd_p;
   void* upd_xs;
-  void* upd_rs;
+  void* upd_rs;             // in rs_prec of out's format
   int64_t upd_half_bytes;
+  int64_t upd_rs_half_bytes;
 };
 
 // Reduction / epilogue modes of the hop kernel.
@@ -372,9 +373,11 @@ __global__ void __launch_bounds__(BLOCK) hop_kernel(const HopArgs A) {
     hop_site<P, R, DAG, EPI, GP>(A.g, A.gauge, in, xb, parity, j, c, res);
     if (RED == RED_CG_UPDATE) {
       const int64_t ps = A.full ? parity * A.half_bytes : 0, vs = A.full ? parity * A.upd_half_bytes : 0;
-      red = update_site_ap<vec_prec(P), P>(A.g, j, A.red.sys[sys_of(j, A.red.nsys)].alpha,
-                                           static_cast<const char*>(A.upd_p) + ps,
-                                           res, static_cast<char*>(A.upd_xs) + vs, static_cast<char*>(A.upd_rs) + vs);
+      const int64_t rs = A.full ? parity * A.upd_rs_half_bytes : 0;
+      red = update_site_ap<vec_prec(P), P, rs_prec(P)>(A.g, j, A.red.sys[sys_of(j, A.red.nsys)].alpha,
+                                                       static_cast<const char*>(A.upd_p) + ps, res,
+                                                       static_cast<char*>(A.upd_xs) + vs,
+                                                       static_cast<char*>(A.upd_rs) + rs);
     } else {
       SpinorIO<P>::store(out, A.g.sstride, j, res);
       if (RED == RED_NORM) red = norm2_site(res);

@@ -70,6 +70,10 @@ template <> struct PrecTraits<LQCD_F16> { using real = float; static constexpr i
 // Format of the iterated CG vectors x_s, r_s for a given sloppy storage format:
 // FP64 stays FP64, FP32 and FP16 storage iterate in FP32.
 __host__ __device__ constexpr int vec_prec(int sloppy) { return sloppy == LQCD_F64 ? LQCD_F64 : LQCD_F32; }
+// Storage of the iterated residual r_s: FP16 with FP16 storage (its rounding is
+// relative to the current residual, and the FP32 replacements bound its drift),
+// else the vector precision.
+__host__ __device__ constexpr int rs_prec(int sloppy) { return sloppy == LQCD_F16 ? LQCD_F16 : vec_prec(sloppy); }
 
 __host__ __device__ inline int spinor_site_bytes(int prec) {
   return prec == LQCD_F64 ? 192 : prec == LQCD_F32 ? 96 : prec == LQCD_F16 ? 52 : 0;

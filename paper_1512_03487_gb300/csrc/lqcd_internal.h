@@ -44,7 +44,8 @@ struct HopUpdate {
   const void* p;
   void* xs;
   void* rs;
-  int64_t half_bytes;  // one checkerboard of x_s / r_s
+  int64_t half_bytes;     // one checkerboard of x_s
+  int64_t rs_half_bytes;  // one checkerboard of r_s
 };
 int op_apply(const OpCtx& c, void* out, const void* in, int subset, int dagger,
              void* t1, void* t2, const ReduceCtx* red, const Control* gate, cudaStream_t s,

@@ -51,6 +51,7 @@ int op_apply(const OpCtx& c, void* out, const void* in, int subset, int dagger, 
     a.upd_xs = upd->xs;
     a.upd_rs = upd->rs;
     a.upd_half_bytes = upd->half_bytes;
+    a.upd_rs_half_bytes = upd->rs_half_bytes;
   };
   const bool wilson = c.op.kind == LQCD_WILSON;
   const double cw = 4.0 + c.op.mass;
