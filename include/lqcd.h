@@ -269,8 +269,10 @@ int lqcd_cg_solve(void* x_dev, const void* b_dev, const void* gauge_dev,
                   lqcd_solve_info* info, void* workspace_dev, size_t workspace_bytes,
                   void* stream);
 
-/* CGNR: solves M x = b (subset LQCD_FULL) or M_hat x = b (LQCD_EVEN, b = b_hat
- * of lqcd_eo_prepare) by CG on the normal equations M^dag M x = M^dag b. Every
+/* CGNR (CG on the normal equations; the Grid paper lists CG, Sec. 4, for the
+ * Wilson and domain-wall operators of Sec. 3): solves M x = b (subset
+ * LQCD_FULL) or M_hat x = b (LQCD_EVEN, b = b_hat of lqcd_eo_prepare) by CG on
+ * M^dag M x = M^dag b. Every
  * reliable update recomputes the residual of the system itself, s = b - M x,
  * and its norm in FP64 (two FP64 hops for M_hat), and the exit test is on it:
  * ||b - M x|| / ||b|| <= tol, reported as true_rel_residual (CG on M^dag M
@@ -287,7 +289,8 @@ int lqcd_cgnr_solve(void* x_dev, const void* b_dev, const void* gauge_dev, const
                     void* stream);
 
 /* Even-odd solve of the full system D x = b (Wilson D_W or domain wall D_DW,
- * the mass-form operators of lqcd_M): b_hat = b_e - D_eo D_oo^-1 b_o (as
+ * the mass-form operators of lqcd_M; single-checkerboard fields as the paper's
+ * grids allow them, Sec. 2.4, with CG, Sec. 4): b_hat = b_e - D_eo D_oo^-1 b_o (as
  * lqcd_eo_prepare), CGNR on M_hat x_e = b_hat (lqcd_cgnr_solve; the exit test
  * ||b_hat - M_hat x_e|| / ||b_hat|| <= tol is reported as true_rel_residual,
  * and the full system's residual b - D x is the same vector once the odd half
