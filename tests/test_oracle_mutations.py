@@ -204,3 +204,106 @@ def test_mixed_chirality_aggregation_is_caught(monkeypatch):
     monkeypatch.setattr(mg, "CHIRAL_SPINS", ((0, 2), (1, 3)))
     with pytest.raises(AssertionError):
         test_coarse_gamma5_hermiticity()
+
+
+# ------------------------------------------------------------ source mutants
+# A one-token change planted in a copy of an oracle function's source: the copy
+# is compiled against the module's own globals and swapped in for the test.
+# Each mutant lists the pins (existing pin tests) of which at least one must
+# fail; they run in order and stop at the first failure.
+
+def _plant(monkeypatch, module, fname, old, new):
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(getattr(module, fname)))
+    assert src.count(old) == 1, (fname, old)
+    scope = {}
+    exec(compile(src.replace(old, new), f"<mutant of {module.__name__}.{fname}>", "exec"), module.__dict__, scope)
+    monkeypatch.setattr(module, fname, scope[fname])
+
+
+def _some_pin_fails(pins):
+    for pin in pins:
+        try:
+            with np.errstate(all="ignore"):
+                pin()
+        except AssertionError:
+            return True
+    return False
+
+
+def _eo_pins():
+    from tests import test_oracle_eo as t
+    return [t.test_schur_adjoint, t.test_schur_determinant_identity, t.test_schur_solve_gives_full_solution]
+
+
+@pytest.mark.parametrize("fname,old,new", [
+    ("schur", "/ (4.0 * c)", "/ (2.0 * c)"),                                   # Schur term without the 1/2 of each hop
+    ("schur", "hop_eo(U, tmp, bc, 0, dagger)", "hop_eo(U, tmp, bc, 0)"),       # adjoint forgets the second hop
+    ("prepare_source", "restrict(b, 0) + hop_eo", "restrict(b, 0) - hop_eo"),  # source sign
+    ("prepare_source", "(2.0 * c)", "(4.0 * c)"),                              # source factor
+    ("reconstruct", "0.5 * hop_eo", "-0.5 * hop_eo"),                          # odd-half sign
+])
+def test_wilson_even_odd_mutants_are_caught(monkeypatch, fname, old, new):
+    assert not _some_pin_fails(_eo_pins())
+    _plant(monkeypatch, wilson, fname, old, new)
+    assert _some_pin_fails(_eo_pins())
+
+
+def _dwf_pins():
+    from tests import test_oracle_dwf as t
+    return [lambda: t.test_m5_inverse(False), lambda: t.test_m5_inverse(True), t.test_ls1_reduces_to_wilson,
+            lambda: t.test_dense_brute_force(False), lambda: t.test_dense_brute_force(True),
+            t.test_gamma5_reflection_hermiticity, t.test_eo_solve_gives_full_solution]
+
+
+@pytest.mark.parametrize("fname,old,new", [
+    ("s_up", "out[-1] *= -mf", "out[-1] *= mf"),                               # wall coupling sign
+    ("s_down", "out[0] *= -mf", "out[0] *= 0.0 * mf"),                         # wall coupling dropped on one side
+    ("m5op", "(5.0 - M5)", "(4.0 - M5)"),                                      # diagonal of D_W(-M5) without the +1
+    ("m5op_matrix", "up[s, 0] = -mf", "up[s, 0] = mf"),                        # inverse built with the wrong twist
+    ("m5op_inv", "m5op_matrix(Ls, M5, mf, chir, dagger)", "m5op_matrix(Ls, M5, mf, chir)"),  # adjoint inverse
+    ("schur", "0.25 *", "0.5 *"),                                              # Schur term factor
+    ("reconstruct", "0.5 * wilson.hop_eo", "0.25 * wilson.hop_eo"),            # odd-half factor
+])
+def test_dwf_mutants_are_caught(monkeypatch, fname, old, new):
+    _plant(monkeypatch, dwf, fname, old, new)
+    assert _some_pin_fails(_dwf_pins())
+
+
+def _cg_pins():
+    from tests import test_oracle_cg as t
+    return [t.test_cg_on_hermitian_matrix_exact_termination, t.test_cg_matches_dense_solve]
+
+
+@pytest.mark.parametrize("fname,old,new", [
+    ("cg", "p = r + (rr_new / rr) * p", "p = r + (rr / rr_new) * p"),          # beta inverted
+    ("cg", "alpha = rr / _dot(p, ap).real", "alpha = rr / _dot(ap, ap).real"), # alpha of the wrong inner product
+    ("cg", "r -= alpha * ap", "r += alpha * ap"),                              # residual update sign
+    ("cg", "x += alpha * p", "x += alpha * r"),                                # solution updated along r
+    ("true_residual", "b - apply_a(x)", "b - x"),                              # exit check without the operator
+])
+def test_cg_mutants_are_caught(monkeypatch, fname, old, new):
+    from oracle import cg
+    assert not _some_pin_fails(_cg_pins())
+    _plant(monkeypatch, cg, fname, old, new)
+    assert _some_pin_fails(_cg_pins())
+
+
+@pytest.mark.parametrize("fname,old,new,integrator", [
+    ("trajectory", "kick(eps / 2)", "kick(eps)", 0),                           # leapfrog opens with a full kick
+    ("trajectory", "drift(eps)", "drift(eps / 2)", 0),                         # leapfrog drift of half a step
+    ("trajectory", "kick(2 * lam * eps if", "kick(lam * eps if", 1),           # merged kicks of neighbouring steps
+    ("trajectory", "kick((1 - 2 * lam) * eps)", "kick((1 - lam) * eps)", 1),   # middle kick weight
+    ("total_force", "F = gauge.force(U, beta)", "F = 2.0 * gauge.force(U, beta)", 0),  # force of another action
+    ("hamiltonian", "K + Sg + Sf", "K + 0.5 * Sg + Sf", 0),                    # energy without the full action
+])
+def test_hmc_mutants_are_caught(monkeypatch, fname, old, new, integrator):
+    """Gauge-only trajectories (the fermion force has its own pins above)."""
+    from oracle import hmc
+    from tests import test_oracle_hmc as t
+    pins = [lambda: t.test_energy_violation_is_second_order(integrator, False),
+            lambda: t.test_reversibility(integrator, False)]
+    assert not _some_pin_fails(pins)
+    _plant(monkeypatch, hmc, fname, old, new)
+    assert _some_pin_fails(pins)
