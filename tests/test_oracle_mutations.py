@@ -307,3 +307,61 @@ def test_hmc_mutants_are_caught(monkeypatch, fname, old, new, integrator):
     assert not _some_pin_fails(pins)
     _plant(monkeypatch, hmc, fname, old, new)
     assert _some_pin_fails(pins)
+
+
+def _mg_pins():
+    from tests import test_oracle_mg as t
+    return [lambda: t.test_restriction_and_prolongation((4, 2, 2, 4), 2, 2),
+            lambda: t.test_coarse_operator_is_galerkin_product((4, 2, 2, 4), 2, 2),
+            t.test_coarse_gamma5_hermiticity]
+
+
+@pytest.mark.parametrize("fname,old,new", [
+    ("restrict", "np.conj(Gp[..., sp, :])", "Gp[..., sp, :]"),                 # restriction without P^dag
+    ("prolong", "c[..., s * Nv:(s + 1) * Nv]", "c[..., (1 - s) * Nv:(2 - s) * Nv]"),  # chiral halves swapped
+    ("orthonormalize", "Q = Q * (d / np.abs(d))[..., None, :]", "Q = Q"),      # QR sign convention left to LAPACK
+    ("_blocked", "n + 1, n + 3, n + 5, n + 7", "n + 3, n + 1, n + 5, n + 7"),  # in-block axes out of order
+    ("coarse_operator", "fwd_out = (coord % b) == b - 1", "fwd_out = (coord % b) == 0"),  # aggregate edge
+    ("coarse_operator", "(4.0 + mass) * B", "(4.0 - mass) * B"),              # site term
+    ("coarse_apply", "ym = np.roll(Y[2 + 2 * mu], -1, axis=ax - 1)", "ym = Y[2 + 2 * mu]"),  # adjoint stencil
+    ("coarse_apply", 'np.einsum("...ji,...j->...i", np.conj(yp), cm)',
+     'np.einsum("...ij,...j->...i", np.conj(yp), cm)'),                        # adjoint without the transpose
+])
+def test_mg_mutants_are_caught(monkeypatch, fname, old, new):
+    from oracle import mg
+    assert not _some_pin_fails(_mg_pins())
+    _plant(monkeypatch, mg, fname, old, new)
+    assert _some_pin_fails(_mg_pins())
+
+
+def _gauge_pins():
+    from tests import test_oracle_gauge as t
+    return [t.test_unit_links, lambda: t.test_single_twisted_link_closed_form(0, 0.3),
+            t.test_staple_counts_every_plaquette_four_times, t.test_gauge_invariance,
+            t.test_force_matches_central_finite_difference, t.test_exponential_against_series,
+            t.test_kinetic_energy]
+
+
+@pytest.mark.parametrize("fname,old,new", [
+    ("plaquette_field", "dag(_fwd(u_mu, nu)) @ dag(u_nu)", "dag(u_nu) @ dag(_fwd(u_mu, nu))"),  # path order
+    ("mean_plaquette", "/ 3.0", "/ 2.0"),                                      # colour normalisation
+    ("action", "n_plaq = 6 *", "n_plaq = 4 *"),                                # plaquette count
+    ("expm_i", "np.exp(1j * eps * w)", "np.exp(-1j * eps * w)"),               # exponent sign
+    ("expm_i", "v.conj())", "v)"),                                             # eigenvectors not conjugated
+    ("update_links", "expm_i(P, eps) @ U", "U @ expm_i(P, eps)"),              # update from the right
+    ("kinetic", "0.5 *", "1.0 *"),                                             # kinetic normalisation
+])
+def test_gauge_mutants_are_caught(monkeypatch, fname, old, new):
+    from oracle import gauge
+    assert not _some_pin_fails(_gauge_pins())
+    _plant(monkeypatch, gauge, fname, old, new)
+    assert _some_pin_fails(_gauge_pins())
+
+
+def test_su3_operand_swap_is_caught(monkeypatch):
+    from oracle import su3
+    from tests import test_oracle_su3 as t
+    pins = [t.test_explicit_loop, t.test_identity_and_order]
+    assert not _some_pin_fails(pins)
+    _plant(monkeypatch, su3, "su3_mul", "np.matmul(x, y)", "np.matmul(y, x)")
+    assert _some_pin_fails(pins)
