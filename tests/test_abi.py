@@ -167,3 +167,25 @@ def test_gparity_rejected_on_host(api):
         with pytest.raises(api.LqcdError) as ei:
             api.lqcd_dslash(buf, buf + 8192, buf + 16384, lat, op, api.LQCD_EVEN, 0, stream=0)
         assert ei.value.status in (-1, -6)
+
+
+def test_tune_table_file_format_on_host(api, tmp_path):
+    """The autotuner's table (shape key -> resident blocks per SM) is host state:
+    load keeps entries in 1..64 with a tab separator (CRLF tolerated, the last
+    value of a repeated key wins) and save writes them back one per line."""
+    n0 = api.lqcd_tune_entries()
+    src = tmp_path / "tune_in.txt"
+    src.write_bytes(b"4\thost-test-a\n0\thost-test-zero\n65\thost-test-big\nno separator here\n"
+                    b"8\thost-test-b\r\n\n3\thost-test-a\n")
+    api.lqcd_tune_load(str(src))
+    assert api.lqcd_tune_entries() == n0 + 2
+    out = tmp_path / "tune_out.txt"
+    api.lqcd_tune_save(str(out))
+    lines = out.read_text().splitlines()
+    assert len(lines) == n0 + 2
+    assert "3\thost-test-a" in lines and "8\thost-test-b" in lines
+    assert not any("host-test-zero" in ln or "host-test-big" in ln for ln in lines)
+    with pytest.raises(api.LqcdError):
+        api.lqcd_tune_load(str(tmp_path / "missing.txt"))
+    with pytest.raises(api.LqcdError):
+        api.lqcd_tune_save(str(tmp_path))  # a directory cannot be opened for writing
