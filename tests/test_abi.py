@@ -189,3 +189,15 @@ def test_tune_table_file_format_on_host(api, tmp_path):
         api.lqcd_tune_load(str(tmp_path / "missing.txt"))
     with pytest.raises(api.LqcdError):
         api.lqcd_tune_save(str(tmp_path))  # a directory cannot be opened for writing
+
+
+def test_autograd_rejects_host_tensors(api):
+    """FermionAction wants complex128 CUDA tensors; CPU or real inputs fail before any library call."""
+    import torch
+    from paper_1512_03487_gb300 import autograd
+    U = torch.zeros((4, 2, 2, 2, 4, 3, 3), dtype=torch.complex128)
+    phi = torch.zeros((4, 2, 2, 2, 4, 3), dtype=torch.complex128)
+    with pytest.raises(TypeError):
+        autograd.fermion_action(U, phi, 0.1)
+    with pytest.raises(TypeError):
+        autograd.fermion_action(U.real, phi.real, 0.1)
