@@ -24,7 +24,8 @@ odd-odd block:
 
 M5op^-1 is applied by a dense LU solve of the L_s x L_s matrix of each
 chirality. Pins: Gamma_5 R hermiticity, the L_s = 1 reduction to Wilson with
-mass 1 - M5 + mf, an explicit-loop dense matrix on a small 5D lattice, and the
+mass 1 - M5 + mf, the closed-form free-field determinant on a periodic 2^4
+lattice, an explicit-loop dense matrix on a small 5D lattice, and the
 full-system residual of the even-odd solve (tests/test_oracle_dwf.py).
 """
 from __future__ import annotations

@@ -77,3 +77,34 @@ def test_eo_solve_gives_full_solution():
     lhs = np.vdot(a.ravel(), dwf.schur(U, c, M5, mf, BC_AP).ravel())
     rhs = np.vdot(dwf.schur(U, a, M5, mf, BC_AP, dagger=True).ravel(), c.ravel())
     assert abs(lhs - rhs) < 1e-11 * abs(lhs)
+
+
+@pytest.mark.parametrize("Ls,M5,mf", [(5, 1.8, 0.02), (4, 1.3, 0.1), (3, 0.5, -0.3)])
+def test_free_field_determinant_closed_form(Ls, M5, mf):
+    """Free field on a periodic 2^4 lattice: every momentum p has components in {0, pi},
+    so sin p = 0 and the hop is diagonal, H = 2 sum_mu cos p_mu = 2 (4 - 2k) with k the
+    number of pi components. The operator is then block-diagonal in chirality with
+    blocks d_k - T, d_k = 1 - M5 + 2k, T a cyclic shift in s whose weights multiply to
+    -mf, and det(d - T) = d^Ls + mf (characteristic polynomial of a weighted cycle).
+    Each chirality carries 2 spins x 3 colours, and C(4, k) momenta have k pi components:
+    det D_DW = prod_k ((1 - M5 + 2k)^Ls + mf)^(12 C(4, k))."""
+    from math import comb
+
+    from synthetic import unit_gauge
+    dims = (2, 2, 2, 2)
+    U = unit_gauge(dims)
+    shape = (Ls, 2, 2, 2, 2, 4, 3)
+    n = int(np.prod(shape))
+    D = np.empty((n, n), dtype=np.complex128)
+    e = np.zeros(n, dtype=np.complex128)
+    for j in range(n):
+        e[j] = 1.0
+        D[:, j] = dwf.dirac(U, e.reshape(shape), M5, mf, (1.0, 1.0, 1.0, 1.0)).reshape(-1)
+        e[j] = 0.0
+    sign, logabs = np.linalg.slogdet(D)
+    factors = [(1 - M5 + 2 * k) ** Ls + mf for k in range(5)]
+    mult = [12 * comb(4, k) for k in range(5)]
+    want_log = sum(m * np.log(abs(f)) for f, m in zip(factors, mult))
+    want_sign = np.prod([np.sign(f) ** m for f, m in zip(factors, mult)])
+    assert logabs == pytest.approx(want_log, rel=1e-12, abs=1e-9)
+    assert abs(sign - want_sign) < 1e-9

@@ -253,6 +253,7 @@ def test_wilson_even_odd_mutants_are_caught(monkeypatch, fname, old, new):
 def _dwf_pins():
     from tests import test_oracle_dwf as t
     return [lambda: t.test_m5_inverse(False), lambda: t.test_m5_inverse(True), t.test_ls1_reduces_to_wilson,
+            lambda: t.test_free_field_determinant_closed_form(3, 0.5, -0.3),
             lambda: t.test_dense_brute_force(False), lambda: t.test_dense_brute_force(True),
             t.test_gamma5_reflection_hermiticity, t.test_eo_solve_gives_full_solution]
 
