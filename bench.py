@@ -260,9 +260,11 @@ def run_lqcd(args, world, rank, local):
     bfull = F.empty(L.lqcd_spinor_bytes(lat, L.LQCD_F64, L.LQCD_FULL))
     x = F.empty(L.lqcd_spinor_bytes(lat, L.LQCD_F64, L.LQCD_FULL))
     tmp = F.empty(L.lqcd_operator_workspace_bytes(lat, op64, L.LQCD_EVEN))
+    # mixed solves run their reliable updates and source preparation in double-float arithmetic
     prms = {k: L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=q, sloppy_recon=12 if q else 18,
                                delta=d, delta_mid=dm, check_interval=args.check_interval,
-                               use_graph=0 if args.no_graph else 1)
+                               use_graph=0 if args.no_graph else 1,
+                               update_prec=L.LQCD_F64_DF if q else L.LQCD_F64)
             for k, (q, d, dm) in VARIANTS.items()}
     ws = F.empty(max(L.lqcd_eo_solve_workspace_bytes(lat, op64, prms[k]) for k in prms))
     flush = L2Flush(dev)
@@ -283,8 +285,10 @@ def run_lqcd(args, world, rank, local):
         return hops, info
 
     def timed(fn, *a):
-        flush()
+        # the flush is queued, not waited for: while the GPU runs it the host queues the
+        # events and the step's first kernels, so no host latency lands between e0 and them
         torch.cuda.synchronize()
+        flush()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -432,6 +436,9 @@ def _cold_hop_seconds(L, F, lat, g, prec, recon, flush, stream, launches):
         L.lqcd_dslash(out, fin, g, lat, op, L.LQCD_EVEN, 0)
     times = []
     for _ in range(launches):
+        # flush queued behind a synchronize, events and launch queued while it runs: e0 -> e1
+        # spans the kernel on the device, not the host's launch latency
+        torch.cuda.synchronize()
         flush()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -548,9 +555,9 @@ def _events_time(fn, stream, flush=None, reps=1):
     best = None
     out = None
     for _ in range(reps):
-        if flush is not None:
-            flush()
         torch.cuda.synchronize()
+        if flush is not None:
+            flush()  # queued: the host queues e0 and fn's first launches while it runs
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)

@@ -71,6 +71,11 @@ extern "C" {
 #define LQCD_F64 0   /* storage precision: FP64, FP64 arithmetic */
 #define LQCD_F32 1   /* FP32 storage, FP32 arithmetic */
 #define LQCD_F16 2   /* FP16 storage (+ FP32 norm per spinor site), FP32 arithmetic */
+#define LQCD_F64_DF 3  /* FP64 storage (the LQCD_F64 layout) with double-float arithmetic: each
+                          real a pair of FP32 numbers (about 48 bits; results within a few 1e-15
+                          of the FP64 arithmetic), for GPUs whose FP64 units are few. An operator
+                          precision only (op->prec; Wilson, no G-parity: lqcd_dslash, lqcd_M,
+                          lqcd_MdagM, lqcd_eo_prepare, lqcd_eo_reconstruct); fields are LQCD_F64 */
 
 #define LQCD_EVEN 0  /* field subset: even checkerboard */
 #define LQCD_ODD  1  /* odd checkerboard */
@@ -124,6 +129,11 @@ typedef struct {
     double timeout_ms;     /* wall-clock limit; 0 = none */
     double delta_mid;      /* lqcd_cg_solve with sloppy_prec LQCD_F16 only (0 = off): threshold of the
                               intermediate FP32-arithmetic residual replacement (e.g. 0.003); see below */
+    int update_prec;       /* mixed Wilson solves: arithmetic of the FP64-field operator of the reliable
+                              updates and of lqcd_eo_solve's source preparation, LQCD_F64 (0, the
+                              default) or LQCD_F64_DF (double-float: the true residual b - A x within a
+                              few 1e-15 |b| of the FP64 one, several times faster on GB300) */
+    int reserved;          /* 0 */
 } lqcd_solver_params;
 
 typedef struct {
@@ -349,12 +359,38 @@ size_t lqcd_batch_cg_workspace_bytes(int n, const lqcd_batch_item* items, int re
 int lqcd_batch_cg_solve(int n, const lqcd_batch_item* items, int recon, const lqcd_solver_params* params,
                         lqcd_solve_info* infos, void* workspace_dev, size_t workspace_bytes, void* stream);
 
-/* The autotuner's table (batch shape -> resident blocks per SM): write it to
- * a text file, read it back (entries found in the file replace the current
- * ones), and count its entries. */
+/* The autotuner (the paper tunes its layout to the SIMD width at compile time,
+ * Sec. 2.4 "Nsimd"; here launch parameters are timed on the GPU at run time).
+ * Its table maps a text key to the integer choice made for it:
+ *  - "batch_hop sms=... prec=... recon=... : <dims of every instance>" ->
+ *    resident blocks per SM of the persistent batch launch (timed on the
+ *    first lqcd_batch_cg_solve of each batch shape);
+ *  - "hop prec=P recon=R dagger=D epi=E red=Q full=F lat=XxYxZxT n5=N" ->
+ *    launch-shape index of an FP32 / FP16 hop kernel (one site per thread
+ *    with 0: 128, 1: 64, 2: 256 threads per block, 3: 128 threads and at
+ *    least 6 resident blocks per SM; 4: 128 threads, two sites per thread in
+ *    packed FP32x2 arithmetic, 3 blocks per SM). All shapes give
+ *    bit-identical hop results. A hop key is
+ *    timed (one warm-up and three launches of every shape, back to back on
+ *    the caller's stream, which is synchronised) on its first launch outside
+ *    a stream capture when running it again cannot change what it leaves
+ *    behind (no reduction, output not aliasing an input); the solvers time
+ *    their in-iteration hops (which reduce and are captured in graphs) once
+ *    per configuration in a tuning pass on their own workspace before the
+ *    first iteration. Untimed keys use shape 0.
+ * lqcd_tune_save writes the table to a text file (one "value<TAB>key" line
+ * per entry); lqcd_tune_load reads one back (its entries replace current
+ * ones; loaded hop keys are never re-timed); lqcd_tune_entries counts the
+ * entries; lqcd_tune_get returns the value stored for key, or -1;
+ * lqcd_tune_clear forgets every entry (hops are timed again on next use);
+ * lqcd_tune_set_enabled(0) stops all timing (untimed keys then keep their
+ * default), 1 (the default) allows it. */
 int lqcd_tune_save(const char* path);
 int lqcd_tune_load(const char* path);
 int lqcd_tune_entries(void);
+int lqcd_tune_get(const char* key);
+void lqcd_tune_clear(void);
+void lqcd_tune_set_enabled(int on);
 
 /* ---------------------------------------------------------------- no-allocation operator */
 
@@ -377,7 +413,10 @@ int lqcd_tune_entries(void);
  *    larger requests return LQCD_ERR_ARG with a message saying so.
  *  - Set-up: the first call on each device, made with that device current,
  *    looks up the array's device address (cudaGetSymbolAddress) once; make
- *    that first call before any stream capture.
+ *    that first call before any stream capture. After a device reset, call
+ *    lqcd_release_caches() before the next call: the array may have moved.
+ *  - No timing: this call never runs the launch-shape autotuner (which would
+ *    synchronise the stream); it uses the table's shapes or the defaults.
  *  - Sharing: every call on a device uses the same array and the array keeps
  *    the last call's contents. The operator writes its temporaries before
  *    reading them, so nothing has to start at zero, but calls whose work

@@ -21,7 +21,7 @@ LQCD_ERR_TIMEOUT = -5
 LQCD_ERR_UNSUPPORTED = -6
 LQCD_ERR_WORKSPACE = -7
 # enums
-LQCD_F64, LQCD_F32, LQCD_F16 = 0, 1, 2
+LQCD_F64, LQCD_F32, LQCD_F16, LQCD_F64_DF = 0, 1, 2, 3
 LQCD_EVEN, LQCD_ODD, LQCD_FULL = 0, 1, 2
 LQCD_WILSON, LQCD_DWF = 0, 1
 LQCD_FORCE_TA, LQCD_FORCE_GRAD = 0, 1
@@ -40,7 +40,8 @@ class lqcd_operator(C.Structure):
 class lqcd_solver_params(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxiter", C.c_int), ("sloppy_prec", C.c_int),
                 ("sloppy_recon", C.c_int), ("delta", C.c_double), ("check_interval", C.c_int),
-                ("use_graph", C.c_int), ("timeout_ms", C.c_double), ("delta_mid", C.c_double)]
+                ("use_graph", C.c_int), ("timeout_ms", C.c_double), ("delta_mid", C.c_double),
+                ("update_prec", C.c_int), ("reserved", C.c_int)]
 
 
 class lqcd_solve_info(C.Structure):
@@ -135,6 +136,9 @@ SIGNATURES = {
     "lqcd_tune_save": (_I, [C.c_char_p]),
     "lqcd_tune_load": (_I, [C.c_char_p]),
     "lqcd_tune_entries": (_I, []),
+    "lqcd_tune_get": (_I, [C.c_char_p]),
+    "lqcd_tune_clear": (None, []),
+    "lqcd_tune_set_enabled": (None, [C.c_int]),
 }
 
 

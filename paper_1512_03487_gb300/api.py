@@ -15,7 +15,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (  # noqa: F401  (re-exported constants and structs)
-    LQCD_DWF, LQCD_EVEN, LQCD_F16, LQCD_F32, LQCD_F64, LQCD_FORCE_GRAD, LQCD_FORCE_TA, LQCD_FULL,
+    LQCD_DWF, LQCD_EVEN, LQCD_F16, LQCD_F32, LQCD_F64, LQCD_F64_DF, LQCD_FORCE_GRAD, LQCD_FORCE_TA, LQCD_FULL,
     LQCD_LEAPFROG, LQCD_MINNORM2, LQCD_ODD, LQCD_WILSON, lqcd_hmc_info, lqcd_hmc_params, lqcd_lattice,
     lqcd_mg_params, lqcd_operator, lqcd_solve_info, lqcd_solver_params,
 )
@@ -71,10 +71,11 @@ def operator(kind: int = LQCD_WILSON, mass: float = 0.0, M5: float = 1.8, mf: fl
 
 def solver_params(tol: float = 1e-10, maxiter: int = 10000, sloppy_prec: int = LQCD_F64,
                   sloppy_recon: int = 18, delta: float = 0.1, check_interval: int = 16,
-                  use_graph: int = 1, timeout_ms: float = 0.0, delta_mid: float = 0.0) -> lqcd_solver_params:
+                  use_graph: int = 1, timeout_ms: float = 0.0, delta_mid: float = 0.0,
+                  update_prec: int = LQCD_F64) -> lqcd_solver_params:
     return lqcd_solver_params(tol=tol, maxiter=maxiter, sloppy_prec=sloppy_prec, sloppy_recon=sloppy_recon,
                               delta=delta, check_interval=check_interval, use_graph=use_graph,
-                              timeout_ms=timeout_ms, delta_mid=delta_mid)
+                              timeout_ms=timeout_ms, delta_mid=delta_mid, update_prec=update_prec)
 
 
 # ------------------------------------------------------------------ library
@@ -272,6 +273,18 @@ def lqcd_tune_load(path: str) -> None:
 
 def lqcd_tune_entries() -> int:
     return int(lib.lqcd_tune_entries())
+
+
+def lqcd_tune_get(key: str) -> int:
+    return int(lib.lqcd_tune_get(key.encode()))
+
+
+def lqcd_tune_clear() -> None:
+    lib.lqcd_tune_clear()
+
+
+def lqcd_tune_set_enabled(on: bool) -> None:
+    lib.lqcd_tune_set_enabled(1 if on else 0)
 
 
 def lqcd_colour_matrix_bytes(lat, prec) -> int:

@@ -22,6 +22,7 @@
 
 #include "cg_engine.h"
 #include "cg_site.cuh"
+#include "tune.h"
 
 namespace lqcd {
 
@@ -216,9 +217,6 @@ static int launch_bvec(int kind, int sloppy, unsigned grid, const BatchArgs& a, 
 }
 
 // ------------------------------------------------------------------ autotuned grid size
-
-static std::mutex g_tune_mutex;
-static std::map<std::string, int> g_tune;  // shape key -> resident blocks per SM
 
 static std::string shape_key(int n, const Geom* geoms, int sloppy, int recon, int sms) {
   std::string k = "batch_hop sms=" + std::to_string(sms) + " prec=" + std::to_string(sloppy) +
@@ -524,17 +522,12 @@ int lqcd_batch_cg_solve(int n, const lqcd_batch_item* items, int recon, const lq
   if ((st = sm_count(&sms))) return finish(st, 0, 0);
   const std::string skey = shape_key(n, geoms, S.sloppy, S.sloppy_recon, sms);
   int bps = 0;
-  {
-    std::lock_guard<std::mutex> lock(g_tune_mutex);
-    auto it = g_tune.find(skey);
-    if (it != g_tune.end()) bps = it->second;
-  }
-  if (bps == 0) {
+  if (!tune_lookup(skey, &bps) || bps <= 0) {
+    bps = 0;
     S.grid = (unsigned)std::min<int64_t>(std::min<int64_t>((int64_t)4 * sms, tiles), MAX_GRID);
     if ((st = S.init(s))) return finish(st, 0, 0);  // gives p a defined value to time the hop on
     if ((st = autotune_grid(S, sms, &bps, s))) return finish(st, 0, 0);
-    std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune[skey] = bps;
+    tune_store(skey, bps);
   }
   S.grid = (unsigned)std::min<int64_t>(std::min<int64_t>((int64_t)bps * sms, tiles), MAX_GRID);
 
@@ -567,40 +560,6 @@ int lqcd_batch_cg_solve(int n, const lqcd_batch_item* items, int recon, const lq
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return finish(status ? status : cuda_fail(e, "batch: state readback"), &ctrl, nullptr);
   return finish(status, &ctrl, sys);
-}
-
-int lqcd_tune_save(const char* path) {
-  if (!path) return fail(LQCD_ERR_ARG, "lqcd_tune_save: null path");
-  FILE* f = fopen(path, "w");
-  if (!f) return fail(LQCD_ERR_ARG, "lqcd_tune_save: cannot open %s", path);
-  std::lock_guard<std::mutex> lock(g_tune_mutex);
-  for (auto& kv : g_tune) fprintf(f, "%d\t%s\n", kv.second, kv.first.c_str());
-  fclose(f);
-  return LQCD_OK;
-}
-
-int lqcd_tune_load(const char* path) {
-  if (!path) return fail(LQCD_ERR_ARG, "lqcd_tune_load: null path");
-  FILE* f = fopen(path, "r");
-  if (!f) return fail(LQCD_ERR_ARG, "lqcd_tune_load: cannot open %s", path);
-  char line[4096];
-  std::lock_guard<std::mutex> lock(g_tune_mutex);
-  while (fgets(line, sizeof(line), f)) {
-    char* tab = strchr(line, '\t');
-    if (!tab) continue;
-    *tab = 0;
-    const int v = atoi(line);
-    std::string k(tab + 1);
-    while (!k.empty() && (k.back() == '\n' || k.back() == '\r')) k.pop_back();
-    if (v > 0 && v <= 64) g_tune[k] = v;
-  }
-  fclose(f);
-  return LQCD_OK;
-}
-
-int lqcd_tune_entries(void) {
-  std::lock_guard<std::mutex> lock(g_tune_mutex);
-  return (int)g_tune.size();
 }
 
 }  // extern "C"

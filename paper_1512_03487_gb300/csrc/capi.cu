@@ -89,8 +89,10 @@ size_t field_bytes(const Geom& g, int prec, int subset) {
 int check_operator(const lqcd_operator* op, Geom& g) {
   if (!op) return fail(LQCD_ERR_ARG, "null operator");
   if (op->kind != LQCD_WILSON && op->kind != LQCD_DWF) return fail(LQCD_ERR_ARG, "bad operator kind %d", op->kind);
-  if (op->prec != LQCD_F64 && op->prec != LQCD_F32 && op->prec != LQCD_F16)
+  if (op->prec != LQCD_F64 && op->prec != LQCD_F32 && op->prec != LQCD_F16 && op->prec != LQCD_F64_DF)
     return fail(LQCD_ERR_ARG, "bad precision %d", op->prec);
+  if (op->prec == LQCD_F64_DF && (op->kind != LQCD_WILSON || op->gparity))
+    return fail(LQCD_ERR_UNSUPPORTED, "double-float arithmetic: Wilson operator without G-parity only");
   if (op->recon != 18 && op->recon != 12) return fail(LQCD_ERR_ARG, "bad recon %d", op->recon);
   if (op->kind == LQCD_DWF) {
     if (g.n5 > MAX_SYS * 4) return fail(LQCD_ERR_ARG, "L_s = %d too large", g.n5);

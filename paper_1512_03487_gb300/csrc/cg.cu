@@ -43,6 +43,7 @@
 // only looks at the control block between chunks.
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -284,6 +285,11 @@ static Workspace carve(void* base, const Geom& g, const lqcd_operator& op, const
   return w;
 }
 
+// Whether a solve runs its FP64-field operator (reliable updates, even-odd source) in double-float arithmetic.
+static bool update_df(const lqcd_operator& op, const lqcd_solver_params& p) {
+  return p.sloppy_prec != LQCD_F64 && p.update_prec == LQCD_F64_DF && op.kind == LQCD_WILSON && !op.gparity;
+}
+
 static int validate(const lqcd_lattice* lat, const lqcd_operator* op, const lqcd_solver_params* p, int subset,
                     Geom* g) {
   int st = make_geom(lat, g);
@@ -298,6 +304,8 @@ static int validate(const lqcd_lattice* lat, const lqcd_operator* op, const lqcd
   if (!(p->tol > 0.0) || p->maxiter < 1) return fail(LQCD_ERR_ARG, "cg: tol must be > 0 and maxiter >= 1");
   if (p->delta < 0.0 || p->delta >= 1.0) return fail(LQCD_ERR_ARG, "cg: delta must be in [0, 1)");
   if (!(p->delta_mid >= 0.0 && p->delta_mid < 1.0)) return fail(LQCD_ERR_ARG, "cg: delta_mid must be in [0, 1)");
+  if (p->update_prec != LQCD_F64 && p->update_prec != LQCD_F64_DF)
+    return fail(LQCD_ERR_ARG, "cg: update_prec must be LQCD_F64 or LQCD_F64_DF");
   if (subset != LQCD_EVEN && subset != LQCD_FULL) return fail(LQCD_ERR_ARG, "cg: subset must be EVEN or FULL");
   return LQCD_OK;
 }
@@ -435,6 +443,35 @@ struct Solver : CgEngine {
 
   bool has_mid() const override { return mid_on; }
 
+  // Tuning pass, before init: the operator applications of an iteration (M_hat p with
+  // its norm, M_hat^dag with the fused update) and of the FP32 level, run once with
+  // every reduction sent to scratch (FIN_STORE into ss) and alpha = 0, so that each
+  // hop instantiation the captured graph will replay gets its launch shape timed
+  // (inside a capture nothing can be timed). The fields it touches are rewritten by
+  // init afterwards.
+  int tune(cudaStream_t s) {
+    TuningPass pass;
+    cudaError_t e = cudaMemsetAsync(w.counter, 0, 64, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.sys, 0, sizeof(SysState) * MAX_SYS, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.p, 0, field_bytes(g, prm.sloppy_prec, subset), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.xs, 0, field_bytes(g, vec_prec(prm.sloppy_prec), subset), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.rs, 0, field_bytes(g, rs_prec(prm.sloppy_prec), subset), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cg: tuning pass memset");
+    ReduceCtx r = rc_ss;  // FIN_STORE into ss
+    OpCtx cs{g, ops, gauge_s};
+    int st = op_apply(cs, w.mp, w.p, subset, 0, w.t1_s, w.t2_s, &r, nullptr, s);
+    const HopUpdate upd{w.p, w.xs, w.rs, va.hbv, va.hbr};
+    if (!st) st = op_apply(cs, nullptr, w.mp, subset, 1, w.t1_s, w.t2_s, &r, nullptr, s, &upd);
+    if (!st && w.g32 && (normal || mid_on)) {
+      e = cudaMemsetAsync(w.g32, 0, (size_t)8 * g.gstride * link_bytes(LQCD_F32, 12), s);
+      if (e != cudaSuccess) return cuda_fail(e, "cg: tuning pass memset");
+      OpCtx cm{g, opm, w.g32};
+      st = op_apply(cm, w.mid64, w.xs, subset, 0, w.t1_64, w.t2_64, nullptr, nullptr, s);
+      if (!st) st = op_apply(cm, w.ax64, w.mid64, subset, 1, w.t1_64, w.t2_64, nullptr, nullptr, s);
+    }
+    return st;
+  }
+
   // r_s = r - M^dag M x_s with the FP32 operator on the FP32 link copy. The
   // FP64 update's buffers (mid64, ax64, t1_64, t2_64) are idle here and hold
   // the FP32 intermediates.
@@ -456,7 +493,10 @@ using namespace lqcd;
 
 extern "C" {
 
-void lqcd_release_caches(void) { release_graph_cache(); }
+void lqcd_release_caches(void) {
+  release_graph_cache();
+  release_noalloc_addresses();
+}
 
 size_t lqcd_cg_workspace_bytes(const lqcd_lattice* lat, const lqcd_operator* op, const lqcd_solver_params* p,
                                int subset) {
@@ -501,6 +541,8 @@ static int cg_solve_impl(void* x, const void* b, const void* gauge, const void* 
   S.ctrl = S.w.ctrl;
   S.sys = S.w.sys;
   S.op64 = *op;
+  // mixed Wilson solves may run the reliable updates' FP64-field operator in double-float arithmetic
+  if (update_df(*op, *prm)) S.op64.prec = LQCD_F64_DF;
   S.ops = *op;
   S.ops.prec = prm->sloppy_prec;
   // the FP64 inner operator runs on the FP64 field itself, in that field's format
@@ -590,6 +632,18 @@ static int cg_solve_impl(void* x, const void* b, const void* gauge, const void* 
   key_append(key, subset);
   key_append(key, S.mid_on);
   key_append(key, S.normal);
+  key_append(key, S.op64.prec);
+
+  // one tuning pass per solver configuration (lattice, operator, inner formats), outside any capture
+  if (S.ops.prec != LQCD_F64 && !op->gparity && hop_autotune_ready(s)) {
+    char tk[200];
+    snprintf(tk, sizeof(tk), "%dx%dx%dx%d n5=%d kind=%d prec=%d recon=%d subset=%d mid=%d normal=%d",
+             lat->dims[0], lat->dims[1], lat->dims[2], lat->dims[3], lat->n5, op->kind, S.ops.prec, S.ops.recon,
+             subset, (int)S.mid_on, (int)normal);
+    if (solver_tuning_due(tk)) {
+      if ((st = S.tune(s))) return finish(st);
+    }
+  }
 
   Control ctrl;
   memset(&ctrl, 0, sizeof(ctrl));
@@ -667,7 +721,9 @@ int lqcd_eo_solve(void* x, const void* b, const void* gauge, const void* gauge_s
   void* bhat = off(workspace, cgb);
   void* tmp = off(bhat, round_up((int64_t)cb, 256));
   cudaStream_t s = (cudaStream_t)stream;
-  int st = lqcd_eo_prepare(bhat, b, gauge, lat, op, tmp, stream);
+  lqcd_operator opp = *op;
+  if (update_df(*op, *prm)) opp.prec = LQCD_F64_DF;  // same FP64 fields, double-float arithmetic
+  int st = lqcd_eo_prepare(bhat, b, gauge, lat, &opp, tmp, stream);
   if (st) {
     memset(inf, 0, sizeof(*inf));
     inf->status = st;

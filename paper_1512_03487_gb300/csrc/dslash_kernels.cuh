@@ -19,6 +19,7 @@
 #pragma once
 
 #include "cg_site.cuh"
+#include "hop_pair.cuh"
 #include "lqcd_common.cuh"
 #include "m5_scan.cuh"
 
@@ -171,6 +172,7 @@ __device__ __forceinline__ void link_mul_dag(const Link<T>& u, const Half<T>& h,
 template <typename T> __device__ __forceinline__ T bc_phase(const Geom& g, int mu);
 template <> __device__ __forceinline__ double bc_phase<double>(const Geom& g, int mu) { return g.bcd[mu]; }
 template <> __device__ __forceinline__ float bc_phase<float>(const Geom& g, int mu) { return g.bcf[mu]; }
+template <> __device__ __forceinline__ dfl bc_phase<dfl>(const Geom& g, int mu) { return dfl(g.bcf[mu], 0.f); }
 
 // Load the neighbour spinor and spin-project it with (1 + S gamma_mu). The
 // linear factor the half spinor still needs -- the boundary phase of a
@@ -269,13 +271,53 @@ struct EpiCoef {
   double a, b, m5d, mf;
 };
 
-// The result at output site j (= cb * n5 + i5) of checkerboard `parity`.
-template <int P, int R, bool DAG, int EPI, bool GP = false>
-__device__ __forceinline__ void hop_site(const Geom& g, const void* gauge, const void* in, const void* xb,
-                                         int parity, int64_t j, const EpiCoef& c,
-                                         Spinor<typename PrecTraits<P>::real>& res) {
+// ---- the hop with its eight directions in a rolled loop (runtime mu): one copy
+// of the per-direction code instead of eight. For the double-float arithmetic a
+// fully unrolled hop is about 19,000 instructions long and stalls on
+// instruction fetch; this form keeps the loop body in the instruction cache.
+
+// z times c, c = +-1 or +-i: imag selects i, neg the sign
+template <typename T> __device__ __forceinline__ cpx<T> times_unit(cpx<T> z, bool imag, bool neg) {
+  const cpx<T> r = imag ? mk(-z.i, z.r) : z;
+  return neg ? mk(-r.r, -r.i) : r;
+}
+
+// The link of direction mu into w: U (forward hop, block blk at checkerboard site
+// cb) or U^dag (backward), as the matrix U' with w = U' h. 18-real links are read
+// in the transposed order for U^dag; 12-real ones are rebuilt, then transposed.
+template <int P, int R>
+__device__ __forceinline__ void load_link_rolled(const void* gauge, int64_t gs, int blk, int64_t cb, bool fwd,
+                                                 Link<typename PrecTraits<P>::real>& u) {
   using T = typename PrecTraits<P>::real;
-  using IO = SpinorIO<P>;
+  if constexpr (R == 18) {
+    const double2* b = reinterpret_cast<const double2*>(gauge) + (int64_t)blk * 9 * gs + cb;
+    static_assert(P == LQCD_F64 || P == LQCD_F64_DF, "rolled hop: FP64 fields");
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const double2 w = __ldg(b + (fwd ? 3 * r + c : 3 * c + r) * gs);
+        const double im = fwd ? w.y : -w.y;
+        if constexpr (P == LQCD_F64_DF) u.v[3 * r + c] = mk(df_split(w.x), df_split(im));
+        else u.v[3 * r + c] = mk(w.x, im);
+      }
+  } else {
+    Link<T> v;
+    LinkIO<P, 12>::load(gauge, gs, blk, cb, v);
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const cpx<T> a = v.v[3 * r + c], t = conj(v.v[3 * c + r]);
+        u.v[3 * r + c] = fwd ? a : t;
+      }
+  }
+}
+
+template <int P, int R, bool DAG>
+__device__ __forceinline__ void hop_acc_rolled(const Geom& g, const void* gauge, const void* in, int parity,
+                                               int64_t j, Spinor<typename PrecTraits<P>::real>& acc) {
+  using T = typename PrecTraits<P>::real;
   const int64_t n5 = g.n5;
   int64_t cb, i5;
   if (n5 == 1) {
@@ -286,12 +328,89 @@ __device__ __forceinline__ void hop_site(const Geom& g, const void* gauge, const
     i5 = j - cb * n5;
   }
   const Coord x = cb_to_coord(g, cb, parity);
-  Spinor<T> acc;
+  zero(acc);
+  constexpr int SF = DAG ? +1 : -1;  // forward hop carries (1 + SF gamma_mu)
+#pragma unroll 1
+  for (int dir = 0; dir < 8; dir++) {
+    const int mu = dir >> 1;
+    const bool fwd = (dir & 1) == 0;
+    const bool sneg = (fwd ? SF : -SF) < 0;  // the projector's sign S is -1
+    // neighbour along +-mu
+    const int L = mu == 0 ? g.X : mu == 1 ? g.Y : mu == 2 ? g.Z : g.T;
+    const int xm = mu == 0 ? x.c[0] : mu == 1 ? x.c[1] : mu == 2 ? x.c[2] : x.c[3];
+    const uint32_t st = mu == 0 ? 1u : mu == 1 ? (uint32_t)g.st[1] : mu == 2 ? (uint32_t)g.st[2] : (uint32_t)g.st[3];
+    const bool wrap = fwd ? xm == L - 1 : xm == 0;
+    const uint32_t lex = fwd ? (wrap ? x.lex - (uint32_t)(L - 1) * st : x.lex + st)
+                             : (wrap ? x.lex + (uint32_t)(L - 1) * st : x.lex - st);
+    const int64_t nb = (int64_t)(lex >> 1);
+    Spinor<T> p;
+    SpinorIO<P>::load(in, g.sstride, nb * n5 + i5, p);
+    // (1 + S gamma_mu) in the chiral basis: h0 = p0 + c0 p_k0, h1 = p1 + c1 p_k1 with
+    // c = sc S (i if mu is even), and the lower spins S B^dag w: spin 2 += d2 w_m2,
+    // spin 3 += d3 w_m3 with d = sd S (i if mu is even)
+    const bool imag = (mu & 1) == 0;
+    const bool k0_is3 = mu < 2;
+    const bool c0neg = (mu != 3) != sneg, c1neg = (mu == 0) != sneg;
+    const bool d2neg = sneg, d3neg = (mu == 1 || mu == 2) != sneg;
+    Half<T> h;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      const cpx<T> a0 = k0_is3 ? p.v[9 + c] : p.v[6 + c];
+      const cpx<T> a1 = k0_is3 ? p.v[6 + c] : p.v[9 + c];
+      h.v[c] = p.v[c] + times_unit(a0, imag, c0neg);
+      h.v[3 + c] = p.v[3 + c] + times_unit(a1, imag, c1neg);
+    }
+    Link<T> u;
+    load_link_rolled<P, R>(gauge, g.gstride, fwd ? parity * 4 + mu : (1 - parity) * 4 + mu, fwd ? cb : nb, fwd, u);
+    Half<T> w;
+    link_mul(u, h, w);
+    // a wrapping hop's boundary phase (+-1) flips the signs of its whole contribution
+    const float bcm = mu == 0 ? g.bcf[0] : mu == 1 ? g.bcf[1] : mu == 2 ? g.bcf[2] : g.bcf[3];
+    const bool pneg = wrap && bcm < 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      const cpx<T> w0 = w.v[c], w1 = w.v[3 + c];
+      acc.v[c] = acc.v[c] + times_unit(w0, false, pneg);
+      acc.v[3 + c] = acc.v[3 + c] + times_unit(w1, false, pneg);
+      acc.v[6 + c] = acc.v[6 + c] + times_unit(k0_is3 ? w1 : w0, imag, d2neg != pneg);
+      acc.v[9 + c] = acc.v[9 + c] + times_unit(k0_is3 ? w0 : w1, imag, d3neg != pneg);
+    }
+  }
+}
+
+// H in at output site j (= cb * n5 + i5) of checkerboard `parity`.
+template <int P, int R, bool DAG, bool GP = false>
+__device__ __forceinline__ void hop_acc(const Geom& g, const void* gauge, const void* in, int parity, int64_t j,
+                                        Spinor<typename PrecTraits<P>::real>& acc) {
+  const int64_t n5 = g.n5;
+  int64_t cb, i5;
+  if (n5 == 1) {
+    cb = j;
+    i5 = 0;
+  } else {
+    cb = fdiv((uint32_t)j, g.fn5);
+    i5 = j - cb * n5;
+  }
+  if constexpr (P == LQCD_F64_DF) {
+    hop_acc_rolled<P, R, DAG>(g, gauge, in, parity, j, acc);
+    return;
+  }
+  const Coord x = cb_to_coord(g, cb, parity);
   zero(acc);
   hop_dir<0, P, R, DAG, GP>(acc, g, gauge, x, cb, i5, parity, in);
   hop_dir<1, P, R, DAG, GP>(acc, g, gauge, x, cb, i5, parity, in);
   hop_dir<2, P, R, DAG, GP>(acc, g, gauge, x, cb, i5, parity, in);
   hop_dir<3, P, R, DAG, GP>(acc, g, gauge, x, cb, i5, parity, in);
+}
+
+// The epilogue at output site j of the hop result acc = H in (see EpiCoef).
+template <int P, bool DAG, int EPI>
+__device__ __forceinline__ void hop_epilogue(const Geom& g, const void* xb, int64_t j, const EpiCoef& c,
+                                             const Spinor<typename PrecTraits<P>::real>& acc,
+                                             Spinor<typename PrecTraits<P>::real>& res) {
+  using T = typename PrecTraits<P>::real;
+  using IO = SpinorIO<P>;
+  const int64_t n5 = g.n5;
   const T b = (T)c.b;
   if (EPI == EPI_PLAIN || EPI == EPI_M5INV) {
 #pragma unroll
@@ -304,6 +423,7 @@ __device__ __forceinline__ void hop_site(const Geom& g, const void* gauge, const
     for (int k = 0; k < 12; k++) res.v[k] = mk(fma(a, xv.v[k].r, b * acc.v[k].r), fma(a, xv.v[k].i, b * acc.v[k].i));
   } else {
     // M5op(x)(s) = d x(s) - P_- x(s+1) - P_+ x(s-1), mf corners (dagger swaps directions)
+    const int64_t i5 = n5 == 1 ? 0 : j - (int64_t)fdiv((uint32_t)j, g.fn5) * n5;
     Spinor<T> xv;
     IO::load(xb, g.sstride, j, xv);
     const T d = (T)c.m5d;
@@ -327,6 +447,16 @@ __device__ __forceinline__ void hop_site(const Geom& g, const void* gauge, const
   }
 }
 
+// The result at output site j (= cb * n5 + i5) of checkerboard `parity`.
+template <int P, int R, bool DAG, int EPI, bool GP = false>
+__device__ __forceinline__ void hop_site(const Geom& g, const void* gauge, const void* in, const void* xb,
+                                         int parity, int64_t j, const EpiCoef& c,
+                                         Spinor<typename PrecTraits<P>::real>& res) {
+  Spinor<typename PrecTraits<P>::real> acc;
+  hop_acc<P, R, DAG, GP>(g, gauge, in, parity, j, acc);
+  hop_epilogue<P, DAG, EPI>(g, xb, j, c, acc, res);
+}
+
 template <typename T> __device__ __forceinline__ T norm2_site(const Spinor<T>& res) {
   T s = T(0);
 #pragma unroll
@@ -334,9 +464,16 @@ template <typename T> __device__ __forceinline__ T norm2_site(const Spinor<T>& r
   return s;
 }
 
-template <int P, int R, bool DAG, int EPI, int RED, int BLOCK, bool GP = false>
-__global__ void __launch_bounds__(BLOCK) hop_kernel(const HopArgs A) {
+// One launch computes BLOCK * SPT output sites per block. SPT = 1: one site
+// per thread, any precision. SPT = 2 (FP32 and FP16 storage, not G-parity):
+// thread t of block blk computes sites j0 = blk BLOCK 2 + t and j1 = j0 +
+// BLOCK together in packed FP32x2 arithmetic (hop_pair.cuh), so that every
+// load instruction of a warp stays one coalesced access and the two sites
+// share each FP32 instruction of the hop.
+template <int P, int R, bool DAG, int EPI, int RED, int BLOCK, bool GP, int SPT>
+__device__ __forceinline__ void hop_body(const HopArgs& A) {
   using T = typename PrecTraits<P>::real;
+  static_assert(SPT == 1 || (SPT == 2 && P != LQCD_F64 && !GP), "two sites per thread: FP32 / FP16, no G-parity");
   if (gate_closed(A.gate)) return;
   int parity = A.out_parity;
   int blk = blockIdx.x;
@@ -347,43 +484,103 @@ __global__ void __launch_bounds__(BLOCK) hop_kernel(const HopArgs A) {
   const char* in = static_cast<const char*>(A.in) + (A.full ? (1 - parity) * A.half_bytes : 0);
   char* out = static_cast<char*>(A.out) + (A.full ? parity * A.half_bytes : 0);
   const char* xb = A.x ? static_cast<const char*>(A.x) + (A.full ? parity * A.half_bytes : 0) : nullptr;
-  const int64_t j = (int64_t)blk * BLOCK + threadIdx.x;
-  if constexpr (EPI == EPI_M5INV) {
-    // every lane takes part in the fifth-dimension scan; lanes past the end
-    // (whole 4D sites, since L_s divides the block) carry zeros and store nothing
-    static_assert(RED == RED_NONE, "M5op^-1 epilogue without reduction");
-    const bool live = j < A.g.nsites;
-    Spinor<T> res;
-    if (live) {
-      const EpiCoef c{A.a, A.b, A.m5d, A.mf};
+  const EpiCoef c{A.a, A.b, A.m5d, A.mf};
+  const int64_t first = (int64_t)blk * (BLOCK * SPT);
+  if constexpr (SPT == 1) {
+    const int64_t j = first + threadIdx.x;
+    if constexpr (EPI == EPI_M5INV) {
+      // every lane takes part in the fifth-dimension scan; lanes past the end
+      // (whole 4D sites, since L_s divides the block) carry zeros and store nothing
+      static_assert(RED == RED_NONE, "M5op^-1 epilogue without reduction");
+      const bool live = j < A.g.nsites;
+      Spinor<T> res;
+      if (live) hop_site<P, R, DAG, EPI, GP>(A.g, A.gauge, in, xb, parity, j, c, res);
+      else zero(res);
+      const int Ls = A.g.n5;
+      m5inv_lanes(res, (int)(threadIdx.x & (unsigned)(Ls - 1)), Ls, A.m5_dagger != 0, (T)A.m5_a, (T)A.mf,
+                  (T)A.m5_den_inv);
+      if (live) SpinorIO<P>::store(out, A.g.sstride, j, res);
+      return;
+    }
+    T red = T(0);
+    if (j < A.g.nsites) {
+      Spinor<T> res;
       hop_site<P, R, DAG, EPI, GP>(A.g, A.gauge, in, xb, parity, j, c, res);
-    } else {
-      zero(res);
+      if constexpr (RED == RED_CG_UPDATE) {
+        const int64_t ps = A.full ? parity * A.half_bytes : 0, vs = A.full ? parity * A.upd_half_bytes : 0;
+        const int64_t rs = A.full ? parity * A.upd_rs_half_bytes : 0;
+        red = update_site_ap<vec_prec(P), P, rs_prec(P)>(A.g, j, A.red.sys[sys_of(j, A.red.nsys)].alpha,
+                                                         static_cast<const char*>(A.upd_p) + ps, res,
+                                                         static_cast<char*>(A.upd_xs) + vs,
+                                                         static_cast<char*>(A.upd_rs) + rs);
+      } else {
+        SpinorIO<P>::store(out, A.g.sstride, j, res);
+        if constexpr (RED == RED_NORM) red = norm2_site(res);
+      }
     }
-    const int Ls = A.g.n5;
-    m5inv_lanes(res, (int)(threadIdx.x & (unsigned)(Ls - 1)), Ls, A.m5_dagger != 0, (T)A.m5_a, (T)A.mf,
-                (T)A.m5_den_inv);
-    if (live) SpinorIO<P>::store(out, A.g.sstride, j, res);
-    return;
-  }
-  T red = T(0);
-  if (j < A.g.nsites) {
-    Spinor<T> res;
-    const EpiCoef c{A.a, A.b, A.m5d, A.mf};
-    hop_site<P, R, DAG, EPI, GP>(A.g, A.gauge, in, xb, parity, j, c, res);
-    if (RED == RED_CG_UPDATE) {
-      const int64_t ps = A.full ? parity * A.half_bytes : 0, vs = A.full ? parity * A.upd_half_bytes : 0;
-      const int64_t rs = A.full ? parity * A.upd_rs_half_bytes : 0;
-      red = update_site_ap<vec_prec(P), P, rs_prec(P)>(A.g, j, A.red.sys[sys_of(j, A.red.nsys)].alpha,
-                                                       static_cast<const char*>(A.upd_p) + ps, res,
-                                                       static_cast<char*>(A.upd_xs) + vs,
-                                                       static_cast<char*>(A.upd_rs) + rs);
-    } else {
-      SpinorIO<P>::store(out, A.g.sstride, j, res);
-      if (RED == RED_NORM) red = norm2_site(res);
+    if constexpr (RED != RED_NONE) block_reduce_finalize<BLOCK>(red, first, A.red);
+  } else {
+    int64_t j[SPT];
+    bool live[SPT];
+#pragma unroll
+    for (int s = 0; s < SPT; s++) {
+      j[s] = first + s * BLOCK + threadIdx.x;
+      live[s] = j[s] < A.g.nsites;
     }
+    Spinor<T> acc[SPT];
+    if (live[0]) {
+      // a second site past the end repeats the first one's loads and is not stored
+      PSpinor pa;
+      hop_acc_pair<P, R, DAG>(A.g, A.gauge, in, parity, j[0], live[1] ? j[1] : j[0], pa);
+#pragma unroll
+      for (int k = 0; k < 12; k++) {
+        acc[0].v[k] = pick(pa.v[k], 0);
+        acc[1].v[k] = pick(pa.v[k], 1);
+      }
+    }
+    if constexpr (EPI == EPI_M5INV) {
+      static_assert(RED == RED_NONE, "M5op^-1 epilogue without reduction");
+      const int Ls = A.g.n5;
+#pragma unroll
+      for (int s = 0; s < SPT; s++) {
+        Spinor<T> res;
+        if (live[s]) hop_epilogue<P, DAG, EPI>(A.g, xb, j[s], c, acc[s], res);
+        else zero(res);
+        m5inv_lanes(res, (int)(threadIdx.x & (unsigned)(Ls - 1)), Ls, A.m5_dagger != 0, (T)A.m5_a, (T)A.mf,
+                    (T)A.m5_den_inv);
+        if (live[s]) SpinorIO<P>::store(out, A.g.sstride, j[s], res);
+      }
+      return;
+    }
+    T red[SPT];
+#pragma unroll
+    for (int s = 0; s < SPT; s++) {
+      red[s] = T(0);
+      if (!live[s]) continue;
+      Spinor<T> res;
+      hop_epilogue<P, DAG, EPI>(A.g, xb, j[s], c, acc[s], res);
+      if constexpr (RED == RED_CG_UPDATE) {
+        const int64_t ps = A.full ? parity * A.half_bytes : 0, vs = A.full ? parity * A.upd_half_bytes : 0;
+        const int64_t rs = A.full ? parity * A.upd_rs_half_bytes : 0;
+        red[s] = update_site_ap<vec_prec(P), P, rs_prec(P)>(A.g, j[s], A.red.sys[sys_of(j[s], A.red.nsys)].alpha,
+                                                            static_cast<const char*>(A.upd_p) + ps, res,
+                                                            static_cast<char*>(A.upd_xs) + vs,
+                                                            static_cast<char*>(A.upd_rs) + rs);
+      } else {
+        SpinorIO<P>::store(out, A.g.sstride, j[s], res);
+        if constexpr (RED == RED_NORM) red[s] = norm2_site(res);
+      }
+    }
+    if constexpr (RED != RED_NONE) block_reduce_finalize_n<BLOCK, SPT>(red, first, A.red);
   }
-  if (RED) block_reduce_finalize<BLOCK>(red, (int64_t)blk * BLOCK, A.red);
+}
+
+// MINB: minimum resident blocks per SM the register allocation must allow
+// (__launch_bounds__; 0 leaves the choice to the compiler), one of the knobs
+// of the launch shapes the tuner times.
+template <int P, int R, bool DAG, int EPI, int RED, int BLOCK, bool GP = false, int SPT = 1, int MINB = 0>
+__global__ void __launch_bounds__(BLOCK, MINB) hop_kernel(const HopArgs A) {
+  hop_body<P, R, DAG, EPI, RED, BLOCK, GP, SPT>(A);
 }
 
 }  // namespace lqcd

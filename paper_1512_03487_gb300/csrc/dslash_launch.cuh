@@ -6,13 +6,49 @@
 
 namespace lqcd {
 
-template <int P, int R, bool DAG, int EPI, int RED, bool GP>
-static int launch_hop_inst(const HopArgs& a, cudaStream_t s) {
-  const int64_t nb = (a.g.nsites + HOP_BLOCK - 1) / HOP_BLOCK;
+template <int P, int R, bool DAG, int EPI, int RED, bool GP, int BLOCK, int SPT, int MINB>
+static int launch_hop_shape(HopArgs a, cudaStream_t s) {
+  const int64_t nb = (a.g.nsites + BLOCK * SPT - 1) / (BLOCK * SPT);
+  a.blocks_per_parity = (int)nb;
   const int64_t grid = a.full ? 2 * nb : nb;
   if (grid == 0) return LQCD_OK;
-  hop_kernel<P, R, DAG, EPI, RED, HOP_BLOCK, GP><<<(unsigned)grid, HOP_BLOCK, 0, s>>>(a);
+  hop_kernel<P, R, DAG, EPI, RED, BLOCK, GP, SPT, MINB><<<(unsigned)grid, BLOCK, 0, s>>>(a);
   return after_launch("hop_kernel");
+}
+
+template <int P, int R, bool DAG, int EPI, int RED, bool GP>
+static int launch_hop_index(int idx, const HopArgs& a, cudaStream_t s) {
+  switch (idx) {
+#define LQCD_HOP_CASE(I, B, S, M) \
+  case I: return launch_hop_shape<P, R, DAG, EPI, RED, GP, B, S, M>(a, s);
+    LQCD_HOP_SHAPES(LQCD_HOP_CASE)
+#undef LQCD_HOP_CASE
+  }
+  return fail(LQCD_ERR_ARG, "hop launch shape %d out of range", idx);
+}
+
+// FP64 and G-parity hops have one launch shape; FP32 and FP16 hops take the
+// tuner table's shape for their key, timing every shape on the first launch
+// that may be timed (see TuningPass), else the default shape.
+template <int P, int R, bool DAG, int EPI, int RED, bool GP>
+static int launch_hop_inst(const HopArgs& a, cudaStream_t s) {
+  if constexpr (P == LQCD_F64 || P == LQCD_F64_DF || GP) {
+    return launch_hop_shape<P, R, DAG, EPI, RED, GP, HOP_BLOCK, 1, 0>(a, s);
+  } else {
+    const HopKey k{P, R, DAG ? 1 : 0, EPI, RED, a.full, a.g.X, a.g.Y, a.g.Z, a.g.T, a.g.n5};
+    int idx = HOP_SHAPE_DEFAULT;
+    if (!hop_shape_lookup(k, &idx)) {
+      idx = HOP_SHAPE_DEFAULT;
+      const bool repeatable = RED == RED_NONE ? (a.gate == nullptr && a.out != a.in && a.out != a.x)
+                                              : hop_tuning_pass();
+      if (repeatable && a.g.nsites > 0 && hop_autotune_ready(s)) {
+        const int st = tune_hop_shapes(
+            k, [&](int i) { return launch_hop_index<P, R, DAG, EPI, RED, GP>(i, a, s); }, s, &idx);
+        if (st) return st;
+      }
+    }
+    return launch_hop_index<P, R, DAG, EPI, RED, GP>(idx, a, s);
+  }
 }
 
 template <int P, int R, bool DAG, int EPI, bool GP>
@@ -36,15 +72,17 @@ static int launch_hop_epi(int epi, int red, const HopArgs& a, cudaStream_t s) {
   return fail(LQCD_ERR_ARG, "bad epilogue %d", epi);
 }
 
-template <int P, bool GP = false>
-static int launch_hop_prec(int recon, bool dagger, int epi, int red, HopArgs a, cudaStream_t s) {
-  a.blocks_per_parity = (int)((a.g.nsites + HOP_BLOCK - 1) / HOP_BLOCK);
+template <int P, bool DAG, bool GP = false>
+static int launch_hop_dag(int recon, int epi, int red, const HopArgs& a, cudaStream_t s) {
   if (epi == EPI_PLAIN && red) return fail(LQCD_ERR_UNSUPPORTED, "plain hop with reduction");
-  if (recon == 18)
-    return dagger ? launch_hop_epi<P, 18, true, GP>(epi, red, a, s) : launch_hop_epi<P, 18, false, GP>(epi, red, a, s);
-  if (recon == 12)
-    return dagger ? launch_hop_epi<P, 12, true, GP>(epi, red, a, s) : launch_hop_epi<P, 12, false, GP>(epi, red, a, s);
+  if (recon == 18) return launch_hop_epi<P, 18, DAG, GP>(epi, red, a, s);
+  if (recon == 12) return launch_hop_epi<P, 12, DAG, GP>(epi, red, a, s);
   return fail(LQCD_ERR_ARG, "bad recon %d", recon);
+}
+
+template <int P, bool GP = false>
+static int launch_hop_prec(int recon, bool dagger, int epi, int red, const HopArgs& a, cudaStream_t s) {
+  return dagger ? launch_hop_dag<P, true, GP>(recon, epi, red, a, s) : launch_hop_dag<P, false, GP>(recon, epi, red, a, s);
 }
 
 }  // namespace lqcd

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df.cuh"
 #include "lqcd.h"
 
 namespace lqcd {
@@ -66,6 +67,8 @@ template <int P> struct PrecTraits;
 template <> struct PrecTraits<LQCD_F64> { using real = double; static constexpr int site_bytes = 192; };
 template <> struct PrecTraits<LQCD_F32> { using real = float; static constexpr int site_bytes = 96; };
 template <> struct PrecTraits<LQCD_F16> { using real = float; static constexpr int site_bytes = 52; };
+// FP64 fields, double-float arithmetic
+template <> struct PrecTraits<LQCD_F64_DF> { using real = dfl; static constexpr int site_bytes = 192; };
 
 // Format of the iterated CG vectors x_s, r_s for a given sloppy storage format:
 // FP64 stays FP64, FP32 and FP16 storage iterate in FP32.
@@ -76,11 +79,11 @@ __host__ __device__ constexpr int vec_prec(int sloppy) { return sloppy == LQCD_F
 __host__ __device__ constexpr int rs_prec(int sloppy) { return sloppy == LQCD_F16 ? LQCD_F16 : vec_prec(sloppy); }
 
 __host__ __device__ inline int spinor_site_bytes(int prec) {
-  return prec == LQCD_F64 ? 192 : prec == LQCD_F32 ? 96 : prec == LQCD_F16 ? 52 : 0;
+  return prec == LQCD_F64 || prec == LQCD_F64_DF ? 192 : prec == LQCD_F32 ? 96 : prec == LQCD_F16 ? 52 : 0;
 }
 inline int link_bytes(int prec, int recon) {
   int reals = recon == 12 ? 12 : 18;
-  return reals * (prec == LQCD_F64 ? 8 : prec == LQCD_F32 ? 4 : 2);
+  return reals * (prec == LQCD_F64 || prec == LQCD_F64_DF ? 8 : prec == LQCD_F32 ? 4 : 2);
 }
 // bytes of one checkerboard of a spinor field
 __host__ __device__ inline size_t cb_spinor_bytes(const Geom& g, int prec) {
@@ -173,6 +176,25 @@ template <> struct SpinorIO<LQCD_F32> {
   }
 };
 
+// FP64 fields read into / written from double-float arithmetic (the split and
+// the recombination of df.cuh; the layout is the FP64 one).
+template <> struct SpinorIO<LQCD_F64_DF> {
+  using T = dfl;
+  static __device__ __forceinline__ void load(const void* base, int64_t stride, int64_t j, Spinor<T>& s) {
+    const double2* b = reinterpret_cast<const double2*>(base);
+#pragma unroll
+    for (int c = 0; c < 12; c++) {
+      const double2 w = __ldg(b + c * stride + j);
+      s.v[c] = mk(df_split(w.x), df_split(w.y));
+    }
+  }
+  static __device__ __forceinline__ void store(void* base, int64_t stride, int64_t j, const Spinor<T>& s) {
+    double2* b = reinterpret_cast<double2*>(base);
+#pragma unroll
+    for (int c = 0; c < 12; c++) __stcs(b + c * stride + j, make_double2(df_to_double(s.v[c].r), df_to_double(s.v[c].i)));
+  }
+};
+
 // FP16: 3 chunks of 8 halves (4 complexes), then a float norm per site.
 template <> struct SpinorIO<LQCD_F16> {
   using T = float;
@@ -259,6 +281,25 @@ template <> struct LinkIO<LQCD_F64, 12> {
     const double2* b = reinterpret_cast<const double2*>(g) + (int64_t)blk * NCHUNK * gs + cb;
 #pragma unroll
     for (int c = 0; c < 6; c++) { double2 w = __ldg(b + c * gs); u.v[c] = mk(w.x, w.y); }
+    rebuild_row2(u);
+  }
+};
+template <> struct LinkIO<LQCD_F64_DF, 18> {
+  using T = dfl;
+  static constexpr int NCHUNK = 9;
+  static __device__ __forceinline__ void load(const void* g, int64_t gs, int blk, int64_t cb, Link<T>& u) {
+    const double2* b = reinterpret_cast<const double2*>(g) + (int64_t)blk * NCHUNK * gs + cb;
+#pragma unroll
+    for (int c = 0; c < 9; c++) { double2 w = __ldg(b + c * gs); u.v[c] = mk(df_split(w.x), df_split(w.y)); }
+  }
+};
+template <> struct LinkIO<LQCD_F64_DF, 12> {
+  using T = dfl;
+  static constexpr int NCHUNK = 6;
+  static __device__ __forceinline__ void load(const void* g, int64_t gs, int blk, int64_t cb, Link<T>& u) {
+    const double2* b = reinterpret_cast<const double2*>(g) + (int64_t)blk * NCHUNK * gs + cb;
+#pragma unroll
+    for (int c = 0; c < 6; c++) { double2 w = __ldg(b + c * gs); u.v[c] = mk(df_split(w.x), df_split(w.y)); }
     rebuild_row2(u);
   }
 };
@@ -630,6 +671,38 @@ __device__ __forceinline__ void block_reduce_finalize(V v, int64_t block_first_g
     }
   }
   last_block_finalize<BLOCK>(rc, sh);
+}
+
+// block_reduce_finalize for SPT values per thread: value s of thread t belongs to
+// global index block_first_gid + s BLOCK + t (the layout of the two-site hop).
+template <int BLOCK, int SPT, typename V>
+__device__ __forceinline__ void block_reduce_finalize_n(const V (&v)[SPT], int64_t block_first_gid,
+                                                        const ReduceCtx& rc) {
+  if constexpr (SPT == 1) {
+    block_reduce_finalize<BLOCK>(v[0], block_first_gid, rc);
+  } else {
+    const int nsys = rc.nsys;
+    if (nsys == 1) {
+      V sum = v[0];
+#pragma unroll
+      for (int s = 1; s < SPT; s++) sum += v[s];
+      block_reduce_finalize<BLOCK>(sum, block_first_gid, rc);
+      return;
+    }
+    __shared__ double sh[BLOCK];
+    __shared__ V shv[BLOCK * SPT];
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int s = 0; s < SPT; s++) shv[s * BLOCK + tid] = v[s];
+    __syncthreads();
+    if (tid < nsys) {
+      const int first = (int)((tid - block_first_gid % nsys + nsys) % nsys);
+      double acc = 0.0;
+      for (int k = first; k < BLOCK * SPT; k += nsys) acc += (double)shv[k];
+      rc.partials[(int64_t)tid * gridDim.x + blockIdx.x] = acc;
+    }
+    last_block_finalize<BLOCK>(rc, sh);
+  }
 }
 
 // System index of a site index j = cb * n5 + i5.

@@ -1,6 +1,9 @@
 // Host-side internal interfaces shared by the library's translation units.
 #pragma once
 
+#include <functional>
+#include <string>
+
 #include "dslash_kernels.cuh"
 #include "lqcd_common.cuh"
 
@@ -12,9 +15,61 @@ int launch_hop_f64(int recon, bool dagger, int epi, int reduce, HopArgs a, cudaS
 int launch_hop_f32(int recon, bool dagger, int epi, int reduce, HopArgs a, cudaStream_t s);
 int launch_hop_f16(int recon, bool dagger, int epi, int reduce, HopArgs a, cudaStream_t s);
 int launch_hop_gparity(int prec, int recon, bool dagger, int epi, int reduce, HopArgs a, cudaStream_t s);
+int launch_hop_df(int recon, bool dagger, int epi, int reduce, HopArgs a, cudaStream_t s);
 
-// Blocks of the hop kernel per checkerboard (the reduction buffers are sized from it).
+// Threads per block of the one-site hop (FP64, G-parity, the batch solver's tiles).
+// Every hop launch shape covers at least 64 sites per block: the solvers size
+// their reduction partials for that.
 constexpr int HOP_BLOCK = 128;
+
+// Launch shapes of the FP32 / FP16 hop that the autotuner chooses among:
+// X(index, threads per block, sites per thread, minimum resident blocks per SM;
+// 0 leaves the register count to the compiler). Measured on GB300 at 24^3 x 48:
+// one site per thread is fastest for the plain FP16 / 12-real hop (27 us
+// against 31-33 us for two sites per thread, whose packed FP32x2 arithmetic
+// needs 32 % fewer instructions but 168-222 registers), so it is the default.
+#define LQCD_HOP_SHAPES(X) X(0, 128, 1, 0) X(1, 64, 1, 0) X(2, 256, 1, 0) X(3, 128, 1, 6) X(4, 128, 2, 3)
+constexpr int HOP_SHAPES = 5;
+// The shape used when the table holds no choice for a hop.
+constexpr int HOP_SHAPE_DEFAULT = 0;
+
+// What identifies one tunable hop launch: the kernel instantiation and the lattice.
+struct HopKey {
+  int prec, recon, dagger, epi, red, full, X, Y, Z, T, n5;
+};
+// Text form of k, the autotuner table's key.
+std::string hop_key_string(const HopKey& k);
+// The table's shape index for k, if it holds one.
+bool hop_shape_lookup(const HopKey& k, int* idx);
+// Whether an untuned hop launch on stream s may be timed now: autotuning is
+// on (lqcd_tune_set_enabled) and s is not capturing a graph.
+bool hop_autotune_ready(cudaStream_t s);
+// Launches launch(i) for every shape i (one warm-up, three timed launches
+// each, back to back on s), stores the fastest under k and returns it in *best.
+int tune_hop_shapes(const HopKey& k, const std::function<int(int)>& launch, cudaStream_t s, int* best);
+// A hop launch is timed in place only if running it again cannot change what
+// it leaves behind: no reduction, no gate, out not aliasing in or x. Inside a
+// tuning pass (an object of this type alive on the thread) the caller
+// guarantees that a reducing hop's partials, counter, result and update
+// fields are scratch, so reducing hops are tuned too.
+struct TuningPass {
+  TuningPass();
+  ~TuningPass();
+  bool prev;
+};
+bool hop_tuning_pass();
+// While an object of this type is alive on the thread, no hop launch is timed
+// (hop_autotune_ready is false): for entry points that must not synchronise.
+struct NoTuning {
+  NoTuning();
+  ~NoTuning();
+  bool prev;
+};
+// True the first time it is called for a solver configuration key (its tuning
+// pass is then due), false afterwards.
+bool solver_tuning_due(const std::string& key);
+// Forgets which configurations had their tuning pass (lqcd_tune_clear).
+void solver_tuning_reset();
 constexpr int BLAS_BLOCK = 128;
 constexpr int M5_BLOCK = 128;
 
@@ -61,6 +116,9 @@ int check_operator(const lqcd_operator* op, Geom& g);
 // Hermitian force of lqcd_force, kind LQCD_FORCE_TA); FP64 fields, gauge in recon.
 int force_accumulate(double2* mom, const void* gauge, const void* X, const void* Y, const Geom& g, int recon,
                      double coef, cudaStream_t s);
+
+// Forgets the cached device addresses of the allocation-free operator's array.
+void release_noalloc_addresses();
 
 // Host pointer offset helper.
 inline void* off(void* p, size_t bytes) { return static_cast<char*>(p) + bytes; }

@@ -44,6 +44,13 @@ static int scratch_address(void** out) {
   return LQCD_OK;
 }
 
+// Forgets the looked-up addresses (lqcd_release_caches): after a device reset
+// the module is loaded again and the array may move.
+void release_noalloc_addresses() {
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  for (int d = 0; d < MAX_DEVICES; d++) g_scratch_addr[d] = nullptr;
+}
+
 }  // namespace lqcd
 
 using namespace lqcd;
@@ -73,5 +80,6 @@ extern "C" int lqcd_M_noalloc(void* out, const void* in, const void* gauge, cons
     t2 = off(base, cb_spinor_bytes(g, op->prec));
   }
   OpCtx c{g, *op, gauge};
+  NoTuning quiet;  // never time launch shapes here: that would synchronise the stream
   return op_apply(c, out, in, subset, dagger != 0, t1, t2, nullptr, nullptr, (cudaStream_t)stream);
 }

@@ -16,6 +16,7 @@ int launch_hop(int prec, int recon, bool dagger, int epi, int reduce, HopArgs a,
     case LQCD_F64: return launch_hop_f64(recon, dagger, epi, reduce, a, s);
     case LQCD_F32: return launch_hop_f32(recon, dagger, epi, reduce, a, s);
     case LQCD_F16: return launch_hop_f16(recon, dagger, epi, reduce, a, s);
+    case LQCD_F64_DF: return launch_hop_df(recon, dagger, epi, reduce, a, s);
   }
   return fail(LQCD_ERR_ARG, "bad precision %d", prec);
 }

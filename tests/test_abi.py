@@ -88,12 +88,13 @@ def test_fma_probe_rejects_bad_arguments(api):
 
 def test_struct_layouts_match_the_header(api):
     """The ctypes mirrors of the C structs end where the header's do: the
-    fields appended last (delta_mid, residual_replacements) sit at their C
-    offsets, so older callers that zero the struct keep working."""
+    fields appended last (delta_mid, update_prec, residual_replacements) sit
+    at their C offsets, so older callers that zero the struct keep working."""
     import ctypes as C
     from paper_1512_03487_gb300 import _lib
     P = _lib.lqcd_solver_params
-    assert P.delta_mid.offset == P.timeout_ms.offset + 8 and C.sizeof(P) == P.delta_mid.offset + 8
+    assert P.delta_mid.offset == P.timeout_ms.offset + 8 and P.update_prec.offset == P.delta_mid.offset + 8
+    assert P.reserved.offset == P.update_prec.offset + 4 and C.sizeof(P) == P.reserved.offset + 4
     I = _lib.lqcd_solve_info
     assert I.residual_replacements.offset == I.status.offset + 4
 
@@ -170,21 +171,25 @@ def test_gparity_rejected_on_host(api):
 
 
 def test_tune_table_file_format_on_host(api, tmp_path):
-    """The autotuner's table (shape key -> resident blocks per SM) is host state:
-    load keeps entries in 1..64 with a tab separator (CRLF tolerated, the last
-    value of a repeated key wins) and save writes them back one per line."""
+    """The autotuner's table (text key -> choice) is host state: load keeps
+    values in 0..64 with a tab separator (CRLF tolerated, the last value of a
+    repeated key wins; 0 is a hop launch-shape index), save writes them back
+    one per line and lqcd_tune_get reads one entry (-1 when absent)."""
     n0 = api.lqcd_tune_entries()
     src = tmp_path / "tune_in.txt"
-    src.write_bytes(b"4\thost-test-a\n0\thost-test-zero\n65\thost-test-big\nno separator here\n"
-                    b"8\thost-test-b\r\n\n3\thost-test-a\n")
+    src.write_bytes(b"4\thost-test-a\n0\thost-test-zero\n65\thost-test-big\n-1\thost-test-neg\n"
+                    b"no separator here\nx\thost-test-nan\n8\thost-test-b\r\n\n3\thost-test-a\n")
     api.lqcd_tune_load(str(src))
-    assert api.lqcd_tune_entries() == n0 + 2
+    assert api.lqcd_tune_entries() == n0 + 3
+    assert api.lqcd_tune_get("host-test-a") == 3
+    assert api.lqcd_tune_get("host-test-zero") == 0
+    assert api.lqcd_tune_get("host-test-big") == -1
     out = tmp_path / "tune_out.txt"
     api.lqcd_tune_save(str(out))
     lines = out.read_text().splitlines()
-    assert len(lines) == n0 + 2
-    assert "3\thost-test-a" in lines and "8\thost-test-b" in lines
-    assert not any("host-test-zero" in ln or "host-test-big" in ln for ln in lines)
+    assert len(lines) == n0 + 3
+    assert "3\thost-test-a" in lines and "8\thost-test-b" in lines and "0\thost-test-zero" in lines
+    assert not any(k in ln for ln in lines for k in ("host-test-big", "host-test-neg", "host-test-nan"))
     with pytest.raises(api.LqcdError):
         api.lqcd_tune_load(str(tmp_path / "missing.txt"))
     with pytest.raises(api.LqcdError):
@@ -201,3 +206,28 @@ def test_autograd_rejects_host_tensors(api):
         autograd.fermion_action(U, phi, 0.1)
     with pytest.raises(TypeError):
         autograd.fermion_action(U.real, phi.real, 0.1)
+
+
+def test_double_float_operator_rejections_on_host(api):
+    """LQCD_F64_DF is a Wilson-only operator precision: domain wall and
+    G-parity are refused before any CUDA call, and a solver's update_prec
+    accepts only LQCD_F64 and LQCD_F64_DF."""
+    buf = 4096
+    lat4 = api.lattice((4, 4, 4, 4), n5=4)
+    with pytest.raises(api.LqcdError) as ei:
+        api.lqcd_dslash(buf, buf + 8192, buf + 16384, lat4, api.operator(kind=api.LQCD_DWF, prec=api.LQCD_F64_DF),
+                        api.LQCD_EVEN, 0, stream=0)
+    assert ei.value.status == -6
+    lat2 = api.lattice((4, 4, 4, 4), n5=2)
+    with pytest.raises(api.LqcdError) as ei:
+        api.lqcd_dslash(buf, buf + 8192, buf + 16384, lat2, api.operator(prec=api.LQCD_F64_DF, gparity=1),
+                        api.LQCD_EVEN, 0, stream=0)
+    assert ei.value.status == -6
+    lat = api.lattice((4, 4, 4, 4))
+    op = api.operator()
+    assert api.lqcd_cg_workspace_bytes(lat, op, api.solver_params(sloppy_prec=1, update_prec=api.LQCD_F64_DF),
+                                       api.LQCD_EVEN) > 0
+    assert api.lqcd_cg_workspace_bytes(lat, op, api.solver_params(sloppy_prec=1, update_prec=2), api.LQCD_EVEN) == 0
+    # the layout of a double-float operator's fields is the FP64 one
+    assert api.lqcd_operator_workspace_bytes(lat, api.operator(prec=api.LQCD_F64_DF), api.LQCD_EVEN) == \
+        api.lqcd_operator_workspace_bytes(lat, api.operator(prec=api.LQCD_F64), api.LQCD_EVEN)
