@@ -1,16 +1,18 @@
 #!/usr/bin/env python
 """Benchmark: even-odd preconditioned Wilson CG to a 1e-10 FP64 true residual
-on a 24^3 x 48 lattice (links exp(0.3 i H), m = 0.01), FP32 inner Dslash
-(12-real links) with FP64 reliable updates, on one GB300.
+on a 24^3 x 48 lattice (links exp(0.3 i H), m = 0.01) on one GB300.
 
-One step = one full solve of D_W x = b from resident FP64 inputs: link
-preparation (FP64 and FP16 / 12-real device layouts), source preparation
-b_hat = b_e + H_eo b_o / 2c, CG on M_hat^dag M_hat with source M_hat^dag b_hat,
-reconstruction of x_o. The headline value is the Dslash throughput sustained
-inside the step: (hops in the step) x 1320 flop x Vh / step time. The JSON
-line also carries the FP64 and FP16-inner solve times (the mixed vs FP64
-comparison), the roofline of the dominant kernel (the FP32 hop), the oracle
-CPU baseline and the end-to-end number through host buffers.
+One step = one full solve of D_W x = b from resident FP64 inputs with
+lqcd_eo_solve: link preparation (FP64 and FP16 / 12-real device layouts),
+source preparation b_hat = b_e + H_eo b_o / 2c, CGNR on M_hat^dag M_hat with
+FP16-storage / 12-real inner iteration, FP32-arithmetic residual replacements
+and reliable updates of b_hat - M_hat x in double-float arithmetic on the FP64
+fields, and the odd half. The headline value is the Dslash throughput
+sustained inside the step: (hops in the step) x 1320 flop x Vh / step time.
+The JSON line also carries the FP64 and other mixed solves (the mixed vs FP64
+comparison), the roofline of the dominant kernel (the FP16 / 12-real hop), the
+oracle CPU baseline on the host cores and the end-to-end number through host
+buffers.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lqcd|reference]
 """
@@ -178,19 +180,100 @@ class L2Flush:
         torch.sum(self.r)
 
 
-# ------------------------------------------------------------------ oracle timing
+# ------------------------------------------------------------------ oracle timing (CPU baseline)
 
-def oracle_gflops(U, b, mass, napply=1):
-    """FP64 oracle M_hat^dag M_hat (4 even-odd hops) on the bench's own fields."""
+def host_info():
+    """Core count, CPU model and memory of the host the oracle runs on."""
+    info = {"nproc": os.cpu_count() or 1}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            k, _, v = ln.partition(":")
+            if k.strip() in ("Model name", "Architecture", "CPU(s)", "L3 cache"):
+                info[k.strip()] = v.strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/meminfo") as fh:
+            for ln in fh:
+                if ln.startswith("MemAvailable:"):
+                    info["mem_available_gb"] = round(int(ln.split()[1]) / 1e6, 1)
+    except OSError:
+        pass
+    return info
+
+
+def _time_oracle_hops(path, reps):
     from oracle import wilson
-    dims = (U.shape[3], U.shape[2], U.shape[1], U.shape[0])
-    vh = int(np.prod(dims)) // 2
-    be = wilson.restrict(b[0], 0)
+    U = np.load(path + ".U.npy", mmap_mode="r")
+    psi = np.load(path + ".psi.npy", mmap_mode="r")
     t0 = time.perf_counter()
-    for _ in range(napply):
-        wilson.schur_dag_schur(U, be, mass, BC)
+    for _ in range(reps):
+        wilson.hop_eo(U, psi, BC, 0)
+    return time.perf_counter() - t0
+
+
+def _oracle_fields(dims, seed, tmpdir):
+    from oracle import wilson
+    from synthetic import gauge_field, gaussian_spinor
+    base = os.path.join(tmpdir, "x".join(map(str, dims)))
+    if not os.path.exists(base + ".psi.npy"):
+        np.save(base + ".U.npy", gauge_field(dims, "exp", seed, eps=0.3))
+        np.save(base + ".psi.npy", wilson.restrict(gaussian_spinor(dims, seed + 1, lead=(1,))[0], 1))
+    return base
+
+
+def cpu_baseline(budget_s=40.0):
+    """The FP64 numpy oracle, as it stands, on the host cores: even-odd hop GFLOP/s
+    (1320 flop per output site) on 8^4, 16^4 and 24^3 x 48 with one process and with
+    one process per core (a spawn pool: every process times its own hops on
+    memory-mapped shared fields; the aggregate is all processes' flops over the wall
+    time), and the oracle's unpreconditioned CG on M^dag M of config 1 (8^4, Haar
+    links, m = 0.1) to 1e-10, measured. The oracle itself runs on one thread
+    (numpy einsum and roll)."""
+    import multiprocessing as mp
+    import tempfile
+    from oracle import cg as ocg
+    from oracle import wilson
+    from synthetic import config_seed, gauge_field, gaussian_spinor
+    info = host_info()
+    cores = int(info["nproc"])
+    t_start = time.perf_counter()
+    out = {"host": info, "hop_gflops": {}}
+    tmpdir = tempfile.mkdtemp(prefix="lqcd_oracle_")
+    big_ok = info.get("mem_available_gb", 0.0) >= 3.0 * cores  # ~2 GB of temporaries per process at 24^3 x 48
+    sizes = [((8, 8, 8, 8), 20), ((16, 16, 16, 16), 3), ((24, 24, 24, 48), 1)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        for dims, reps in sizes:
+            vh = int(np.prod(dims)) // 2
+            base = _oracle_fields(dims, 7, tmpdir)
+            one = _time_oracle_hops(base, reps)
+            row = {"1_core": round(reps * FLOP_PER_SITE * vh / one / 1e9, 4), "sample_1_core_s": round(one, 2)}
+            if dims != (24, 24, 24, 48) or big_ok:
+                t0 = time.perf_counter()
+                times = pool.map(_time_oracle_hops_star, [(base, reps)] * cores)
+                wall = time.perf_counter() - t0
+                row[f"{cores}_cores"] = round(cores * reps * FLOP_PER_SITE * vh / wall / 1e9, 4)
+                row["sample_all_cores_s"] = round(wall, 2)
+                row["per_process_s_max"] = round(max(times), 2)
+            out["hop_gflops"]["x".join(map(str, dims))] = row
+    # config 1: 8^4 Haar links, m = 0.1, unpreconditioned CG on M^dag M to 1e-10 (measured)
+    dims = (8, 8, 8, 8)
+    U = gauge_field(dims, "haar", config_seed(0, 0))
+    b = gaussian_spinor(dims, config_seed(0, 1), lead=(1,))
+    t0 = time.perf_counter()
+    _, inf = ocg.cg(lambda v: wilson.dirac_dag_dirac(U, v, 0.1, BC), b, 1e-10, 5000)
     dt = time.perf_counter() - t0
-    return 4 * napply * FLOP_PER_SITE * vh / dt / 1e9, dt
+    out["cg_8x4_m0.1_unpreconditioned"] = {"seconds": round(dt, 2), "iterations": inf.iterations,
+                                          "seconds_per_iteration": round(dt / max(inf.iterations, 1), 4),
+                                          "true_rel_residual": inf.true_rel_residual, "cores": 1}
+    out["elapsed_s"] = round(time.perf_counter() - t_start, 1)
+    return out
+
+
+def _time_oracle_hops_star(args):
+    return _time_oracle_hops(*args)
 
 
 def threads_used():
@@ -207,6 +290,22 @@ def dslash_sources_hash(prec):
         with open(os.path.join(ROOT, "paper_1512_03487_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def workload_config(dims, mass, world):
+    """The workload both arms name (the GPU arm and the oracle reference arm)."""
+    return {"workload": WORKLOAD, "lattice": list(dims), "mass": mass, "bc": list(BC),
+            "solver": "lqcd_eo_solve: even-odd CGNR (CG on M_hat^dag M_hat x = M_hat^dag b_hat), "
+                      "FP16-storage / 12-real inner iteration, FP32-arithmetic residual replacements at "
+                      f"delta_mid {DELTA_MID}, reliable updates of b_hat - M_hat x in double-float arithmetic on the "
+                      f"FP64 fields at delta {DELTA_3LVL}",
+            "tol": 1e-10, "tol_applies_to": "true residual of the full system, ||b - D x|| / ||b||: the exit test "
+                                            "is ||b_hat - M_hat x_e|| <= tol ||b|| on the reliable update's "
+                                            "b_hat - M_hat x_e (the full residual's even rows; its odd rows "
+                                            "vanish once x_o is reconstructed), recomputed with the FP64 "
+                                            "operator after the step",
+            "l2": "flushed before every timed step (512 MB write, then 256 MB read)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
 
 def run_lqcd(args, world, rank, local):
@@ -343,7 +442,7 @@ def run_lqcd(args, world, rank, local):
         ms, (hops, info) = runs[2]  # median of 5 after one warm-up
         cgcmp[name] = {"ms": round(ms, 3), "iterations": info.iterations,
                        "reliable_updates": info.reliable_updates, "delta": prms[p].delta,
-                       "true_rel_residual_eo_system": info.true_rel_residual,
+                       "true_rel_residual_full_system": info.true_rel_residual,
                        "dslash_gflops": round(hops * FLOP_PER_SITE * vh / (ms * 1e-3) / 1e9, 1)}
         if p == 3:
             cgcmp[name].update({"delta_mid": prms[p].delta_mid,
@@ -379,15 +478,7 @@ def run_lqcd(args, world, rank, local):
         "dtype": "f32 arithmetic on f16 storage (per-site norm, 12-real links) in the inner iteration, "
                  "f32-arithmetic residual replacements, f64 reliable updates and true residual",
         "data": "synthetic (seeded exp(0.3 i H) links, Gaussian source)",
-        "config": {"workload": WORKLOAD, "lattice": list(dims), "mass": mass, "bc": list(BC),
-                   "solver": "lqcd_eo_solve: even-odd CGNR (CG on M_hat^dag M_hat x = M_hat^dag b_hat), "
-                             "FP16-storage / 12-real inner iteration, FP32-arithmetic residual replacements at "
-                             f"delta_mid {DELTA_MID}, FP64 reliable updates of b_hat - M_hat x at delta {DELTA_3LVL}",
-                   "tol": 1e-10, "tol_applies_to": "FP64 true residual of the even-odd system, ||b_hat - M_hat x_e|| / "
-                                                   "||b_hat|| (the full-system residual ||b - D x|| / ||b|| of the "
-                                                   "reconstructed x is reported beside it)",
-                   "l2": "flushed before every timed step (512 MB write, then 256 MB read)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "config": workload_config(dims, mass, world),
         "full_system_rel_residual": res,
         "iterations_per_step": infos[-1].iterations, "reliable_updates_per_step": infos[-1].reliable_updates,
         "fp32_replacements_per_step": infos[-1].residual_replacements,
@@ -403,11 +494,21 @@ def run_lqcd(args, world, rank, local):
     if extras is not None:
         line["extras"] = extras
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        gf, dt = oracle_gflops(U, b, mass, 1)
-        line["cpu_baseline"] = {"value": round(gf, 4), "unit": "GFLOP/s", "cores": threads_used(),
-                                "kind": "oracle",
-                                "sample": f"one M_hat^dag M_hat application (4 even-odd hops) of the FP64 numpy "
-                                          f"oracle on the same {dims} fields, {dt:.1f} s"}
+        cb = cpu_baseline()
+        big = cb["hop_gflops"]["24x24x24x48"]
+        allc = [k for k in big if k.endswith("_cores")]
+        key16 = "16x16x16x16"
+        if allc:
+            value, cores, where = big[allc[0]], cb["host"]["nproc"], "24^3 x 48"
+        else:  # not enough host memory for one 24^3 x 48 oracle process per core
+            allc16 = [k for k in cb["hop_gflops"][key16] if k.endswith("_cores")]
+            value, cores, where = cb["hop_gflops"][key16][allc16[0]], cb["host"]["nproc"], "16^4"
+        line["cpu_baseline"] = {
+            "value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"even-odd hops of the FP64 numpy oracle on {where} (exp(0.3 i H) links), one process "
+                      f"per core, each timing its own hops on memory-mapped shared fields; aggregate flops "
+                      f"(1320 per output site) over the wall time",
+            "detail": cb}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -617,15 +718,18 @@ def run_extras(L, F, flush, stream):
     bfull = F.spinor_to_device(rhs, lat, 0, 2)
     del rhs
     x = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
+    DF = L.LQCD_F64_DF
     prm = {q: L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=q, sloppy_recon=12,
-                              delta=DELTA_NORMAL_FP32 if q == 1 else DELTA[q], check_interval=64) for q in (1, 2)}
+                              delta=DELTA_NORMAL_FP32 if q == 1 else DELTA[q], check_interval=64, update_prec=DF)
+           for q in (1, 2)}
     prm[3] = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=2, sloppy_recon=12, delta=DELTA_NORMAL_FP32,
-                             delta_mid=DELTA_MID, check_interval=64)
+                             delta_mid=DELTA_MID, check_interval=64, update_prec=DF)
+    prm[0] = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=0, sloppy_recon=18, check_interval=64)
     ws = F.empty(max(L.lqcd_cg_workspace_bytes(lat, op, prm[q], 0) for q in prm))
     vh = 32 ** 4 // 2
     mr = {}
-    for q, name in ((1, "fp32_inner"), (2, "fp16_inner"), (3, "fp16_inner_three_level")):
-        g = gsl[prm[q].sloppy_prec]
+    for q, name in ((0, "fp64"), (1, "fp32_inner"), (2, "fp16_inner"), (3, "fp16_inner_three_level")):
+        g = g64 if q == 0 else gsl[prm[q].sloppy_prec]
         L.lqcd_cg_solve(x, be, g64, g, lat, op, prm[q], 0, ws)
         ms, info = _events_time(lambda: L.lqcd_cg_solve(x, be, g64, g, lat, op, prm[q], 0, ws), stream, flush)
         nop = info.iterations + info.reliable_updates + info.residual_replacements
@@ -634,10 +738,12 @@ def run_extras(L, F, flush, stream):
             "fp32_replacements": info.residual_replacements, "delta": prm[q].delta, "delta_mid": prm[q].delta_mid,
             "max_true_rel_residual_normal_eq": info.true_rel_residual,
             "dslash_gflops_in_solve": round(4 * nop * FLOP_PER_SITE * vh * nr / (ms * 1e-3) / 1e9, 1)}
+    for name in ("fp32_inner", "fp16_inner", "fp16_inner_three_level"):
+        mr["speedup_" + name + "_vs_fp64"] = round(mr["fp64"]["ms"] / mr[name]["ms"], 2)
     # the full systems D x = b of the 12 right-hand sides by lqcd_eo_solve (CGNR, tolerance on each
     # even-odd system's FP64 residual, FP16 storage with three levels)
     pe = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=2, sloppy_recon=12, delta=DELTA_3LVL,
-                         delta_mid=DELTA_MID, check_interval=64)
+                         delta_mid=DELTA_MID, check_interval=64, update_prec=DF)
     xf = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
     wse = F.empty(L.lqcd_eo_solve_workspace_bytes(lat, op, pe))
     L.lqcd_eo_solve(xf, bfull, g64, gsl[2], lat, op, pe, wse)
@@ -645,7 +751,7 @@ def run_extras(L, F, flush, stream):
     mr["eo_solve_full_systems_fp16_three_level"] = {
         "ms": round(mse, 3), "iterations": infe.iterations, "reliable_updates": infe.reliable_updates,
         "fp32_replacements": infe.residual_replacements, "delta": pe.delta, "delta_mid": pe.delta_mid,
-        "max_true_rel_residual_eo_system": infe.true_rel_residual,
+        "max_true_rel_residual_full_system": infe.true_rel_residual,
         "dslash_gflops_in_solve": round((3 + 4 * (infe.iterations + infe.reliable_updates + infe.residual_replacements))
                                         * FLOP_PER_SITE * vh * nr / (mse * 1e-3) / 1e9, 1)}
     del xf, wse, bfull
@@ -777,6 +883,13 @@ def dwf_bench(L, F, flush, stream, use_graph=1, check_interval=64, three_level=T
     if three_level:
         dwf_solve(prm3, g16)
         ms3, info3 = _events_time(lambda: dwf_solve(prm3, g16), stream, flush)
+        # the plain FP64 GPU solve of the same system (FP64 inner iteration)
+        prm64 = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=0, sloppy_recon=18,
+                                check_interval=check_interval, use_graph=use_graph)
+        ws64 = F.empty(L.lqcd_eo_solve_workspace_bytes(lat, op, prm64))
+        L.lqcd_eo_solve(x, bd, g64, g64, lat, op, prm64, ws64)
+        ms64, info64 = _events_time(lambda: L.lqcd_eo_solve(x, bd, g64, g64, lat, op, prm64, ws64), stream, flush)
+        del ws64
     dwf_solve()
     ms, info = _events_time(dwf_solve, stream, flush)
     dx = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
@@ -796,7 +909,10 @@ def dwf_bench(L, F, flush, stream, use_graph=1, check_interval=64, three_level=T
         "fp16_inner_three_level": {"ms": round(ms3, 3), "iterations": info3.iterations,
                                    "reliable_updates": info3.reliable_updates,
                                    "fp32_replacements": info3.residual_replacements,
-                                   "true_rel_residual_eo_system": info3.true_rel_residual} if three_level else None}
+                                   "true_rel_residual_full_system": info3.true_rel_residual} if three_level else None,
+        "fp64": {"ms": round(ms64, 3), "iterations": info64.iterations,
+                 "true_rel_residual_full_system": info64.true_rel_residual} if three_level else None,
+        "speedup_fp32_inner_vs_fp64": round(ms64 / ms, 2) if three_level else None}
 
 
 def su3_sweep(L, F, flush, stream):
@@ -934,40 +1050,58 @@ def mg_bench(L, F, flush, stream):
             "note": "full (not even-odd) operator; the even-odd CG of the headline needs 61 iterations here"}
 
 
-def hmc_bench(L, F, stream):
-    """One HMC trajectory on 16^4: Wilson gauge action (beta 5.6) plus one Wilson
-    pseudofermion (m = 0.2), minimum-norm integrator, tau = 1 in 10 steps (21 force
-    evaluations), FP32-inner CG to 1e-10 on the full lattice for every force."""
+def hmc_bench(L, F, stream, n_therm=12, n_meas=3):
+    """HMC on 16^4: Wilson gauge action (beta 5.6) plus one Wilson pseudofermion
+    (m = 0.2), minimum-norm integrator, tau = 1 in 10 steps (21 force
+    evaluations), FP32-inner CG to 1e-10 on the full lattice for every force.
+    Fresh Gaussian momenta and a fresh pseudofermion phi = M^dag eta before every
+    trajectory (host random numbers, seeded). The start, links exp(0.3 i H), is
+    far from equilibrium at beta 5.6, so n_therm trajectories are accepted
+    unconditionally first; the n_meas timed trajectories then take the
+    Metropolis test exp(-dH) with a seeded uniform number."""
     import torch
     from synthetic import config_seed, gauge_field, gaussian_spinor, make_rng, random_su3_algebra
     dims, beta, mass = (16, 16, 16, 16), 5.6, 0.2
     lat = L.lattice(dims, bc=BC)
     op = L.operator(mass=mass)
     U = gauge_field(dims, "exp", config_seed(50, 0), eps=0.3)
-    P = random_su3_algebra(make_rng(config_seed(50, 1)), U.size // 9).reshape(U.shape)
-    eta = gaussian_spinor(dims, config_seed(50, 2)) / np.sqrt(2.0)
+    rng = make_rng(config_seed(50, 1))
     prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=12, delta=DELTA_NORMAL_FP32,
                           check_interval=64)
     hp = L.hmc_params(beta, 1.0, 10, L.LQCD_MINNORM2, 1)
-    U0 = F.gauge_to_device(U, lat, 0, 18)
-    P0 = F.gauge_to_device(P, lat, 0, 18)
+    Ud = F.gauge_to_device(U, lat, 0, 18)
+    Uprev = torch.empty_like(Ud)
     phid = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
-    L.lqcd_M(phid, F.spinor_to_device(eta, lat, 0, 2), U0, lat, op, L.LQCD_FULL, 1, None)  # phi = M^dag eta
-    Ud, Pd = torch.empty_like(U0), torch.empty_like(P0)
     ws = F.empty(L.lqcd_hmc_workspace_bytes(lat, op, prm))
 
-    def traj():
-        Ud.copy_(U0)
-        Pd.copy_(P0)
-        return L.lqcd_hmc_trajectory(Ud, Pd, phid, lat, op, hp, prm, ws)
+    def refresh():
+        P = random_su3_algebra(rng, U.size // 9).reshape(U.shape)
+        eta = (rng.standard_normal(gaussian_shape) + 1j * rng.standard_normal(gaussian_shape)) / np.sqrt(2.0)
+        L.lqcd_M(phid, F.spinor_to_device(eta, lat, 0, 2), Ud, lat, op, L.LQCD_FULL, 1, None)  # phi = M^dag eta
+        return F.gauge_to_device(P, lat, 0, 18)
 
-    traj()
-    ms, info = _events_time(traj, stream)
-    # the synthetic start (links exp(0.3 i H)) is far from equilibrium at beta 5.6, so dH measures
-    # the integrator on large forces, not an acceptance rate
-    return {"ms_per_trajectory": round(ms, 2), "dH": info.H1 - info.H0, "H0": info.H0,
-            "force_evaluations": info.force_evaluations, "cg_iterations": info.cg_iterations,
-            "plaquette_action_share": round(info.gauge0 / info.H0, 4)}
+    gaussian_shape = F.host_spinor_shape(lat, L.LQCD_FULL)
+    dH_therm = []
+    for _ in range(n_therm):
+        Pd = refresh()
+        info = L.lqcd_hmc_trajectory(Ud, Pd, phid, lat, op, hp, prm, ws)
+        dH_therm.append(info.H1 - info.H0)
+    rows, ms_total, accepted = [], 0.0, 0
+    for _ in range(n_meas):
+        Pd = refresh()
+        Uprev.copy_(Ud)
+        ms, info = _events_time(lambda: L.lqcd_hmc_trajectory(Ud, Pd, phid, lat, op, hp, prm, ws), stream)
+        dH = info.H1 - info.H0
+        acc = bool(rng.uniform() < np.exp(min(0.0, -dH)))
+        if not acc:
+            Ud.copy_(Uprev)
+        accepted += acc
+        ms_total += ms
+        rows.append({"ms": round(ms, 2), "dH": dH, "accepted": acc, "cg_iterations": info.cg_iterations})
+    return {"ms_per_trajectory": round(ms_total / n_meas, 2), "trajectories": rows,
+            "acceptance": round(accepted / n_meas, 3), "force_evaluations": info.force_evaluations,
+            "thermalisation": {"trajectories": n_therm, "dH": [round(d, 2) for d in dH_therm]},
+            "plaquette_action_share_last": round(info.gauge1 / info.H1, 4)}
 
 
 def run_reference(args, world, rank):
@@ -991,7 +1125,7 @@ def run_reference(args, world, rank):
     line = {"metric": METRIC, "value": round(value, 4), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "lattice": list(dims), "mass": args.mass},
+            "config": workload_config(dims, args.mass, world),
             "impl": "reference",
             "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": threads_used(),
                              "kind": "oracle",

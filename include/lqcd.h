@@ -211,8 +211,16 @@ int lqcd_dslash(void* out_dev, const void* in_dev, const void* gauge_dev,
                 const lqcd_lattice* lat, const lqcd_operator* op,
                 int out_subset, int dagger, void* stream);
 
-/* Dirac operator. subset LQCD_FULL: out = D in (D_W or D_DW). subset
- * LQCD_EVEN: out = M_hat in, the even-odd Schur complement
+/* Dirac operator: the Wilson fermion operator and the five-dimensional chiral
+ * (domain-wall) operator the paper lists among its actions (Sec. 4, "Wilson
+ * Fermion Action", "Five dimensional chiral fermions") and benchmarks as
+ * "Wilson and Domain Wall fermion operators" (Sec. 3). The paper writes
+ * neither down; these are the textbook forms. subset LQCD_FULL: out = D in
+ *   Wilson  D_W  = (4 + m) - H / 2
+ *   DWF     D_DW = M5op - H / 2 (H replicated over L_s, M5op the fifth-
+ *           dimension hopping with the mf-twisted wrap).
+ * subset LQCD_EVEN: out = M_hat in, the even-odd Schur complement on the
+ * paper's single-checkerboard grids (Sec. 2.4):
  *   Wilson  M_hat = (4 + m) - H_eo H_oe / (4 (4 + m))
  *   DWF     M_hat = M5op - H_eo M5op^-1 H_oe / 4
  * with dagger giving the adjoint. tmp_dev: workspace of
@@ -220,13 +228,17 @@ int lqcd_dslash(void* out_dev, const void* in_dev, const void* gauge_dev,
 int lqcd_M(void* out_dev, const void* in_dev, const void* gauge_dev,
            const lqcd_lattice* lat, const lqcd_operator* op, int subset, int dagger,
            void* tmp_dev, void* stream);
-/* out = M^dag M in (subset FULL) or M_hat^dag M_hat in (subset EVEN). */
+/* out = M^dag M in (subset FULL) or M_hat^dag M_hat in (subset EVEN): the
+ * Hermitian positive operator the paper's conjugate gradient (Sec. 4) solves
+ * with. */
 int lqcd_MdagM(void* out_dev, const void* in_dev, const void* gauge_dev,
                const lqcd_lattice* lat, const lqcd_operator* op, int subset,
                void* tmp_dev, void* stream);
 size_t lqcd_operator_workspace_bytes(const lqcd_lattice* lat, const lqcd_operator* op, int subset);
 
-/* Even-odd helpers (FP64 fields, op->prec must be LQCD_F64):
+/* Even-odd helpers around a solve on the single-checkerboard grid (Sec. 2.4:
+ * the paper's grids may hold one checkerboard; the Schur-complement reduction
+ * itself is textbook). FP64 fields; op->prec LQCD_F64 or LQCD_F64_DF:
  *   b_hat_e = b_e + H_eo A_oo^-1 b_o / 2            (prepare)
  *   x_o     = A_oo^-1 (b_o + H_oe x_e / 2)          (reconstruct, writes the
  *                                                    odd half of x_full)
@@ -236,7 +248,11 @@ int lqcd_eo_prepare(void* bhat_even_dev, const void* b_full_dev, const void* gau
 int lqcd_eo_reconstruct(void* x_full_dev, const void* b_full_dev, const void* gauge_dev,
                         const lqcd_lattice* lat, const lqcd_operator* op, void* tmp_dev, void* stream);
 
-/* Arithmetic probe (measurement, not part of the method): `blocks` blocks of
+/* ---------------------------------------------------------------- measurement only */
+
+/* Outside the method's ABI: a probe that bench.py uses to measure the GPU's
+ * FP64 / FP32 FMA rate, the denominator of the ALU-bound kernels' rooflines.
+ * Arithmetic probe (measurement, not part of the method): `blocks` blocks of
  * 256 threads each run 8 independent chains of `iters` fused multiply-adds in
  * prec (LQCD_F64 or LQCD_F32) and store one value per thread into sink_dev
  * (blocks * 256 elements of that precision, caller-owned, 8-byte aligned).
@@ -301,12 +317,15 @@ int lqcd_cgnr_solve(void* x_dev, const void* b_dev, const void* gauge_dev, const
 /* Even-odd solve of the full system D x = b (Wilson D_W or domain wall D_DW,
  * the mass-form operators of lqcd_M; single-checkerboard fields as the paper's
  * grids allow them, Sec. 2.4, with CG, Sec. 4): b_hat = b_e - D_eo D_oo^-1 b_o (as
- * lqcd_eo_prepare), CGNR on M_hat x_e = b_hat (lqcd_cgnr_solve; the exit test
- * ||b_hat - M_hat x_e|| / ||b_hat|| <= tol is reported as true_rel_residual,
- * and the full system's residual b - D x is the same vector once the odd half
- * is in place), then x_o = D_oo^-1 (b_o - D_oe x_e). For the Wilson operator
- * the odd half takes H_oe x_e from the last FP64 reliable update (the first hop
- * of its M_hat x_e), so it needs no FP64 hop of its own. x_dev, b_dev: FP64
+ * lqcd_eo_prepare), CGNR on M_hat x_e = b_hat (lqcd_cgnr_solve), then
+ * x_o = D_oo^-1 (b_o - D_oe x_e). Once the odd half is in place the full
+ * system's residual b - D x is b_hat - M_hat x_e on the even sites and zero
+ * (up to rounding) on the odd ones, so the exit test is ||b_hat - M_hat x_e||
+ * <= tol ||b|| with the FP64 b_hat - M_hat x_e of a reliable update and ||b||
+ * of the full source: tol applies to the full system, and true_rel_residual
+ * reports ||b - D x|| / ||b||. For the Wilson operator the odd half takes
+ * H_oe x_e from the last reliable update (the first hop of its M_hat x_e), so
+ * it needs no hop of its own. x_dev, b_dev: FP64
  * full fields (x is overwritten, b is not). workspace_dev:
  * lqcd_eo_solve_workspace_bytes() bytes, 256-byte aligned. Returns the solver's
  * status; on LQCD_ERR_NOT_CONVERGED or LQCD_ERR_TIMEOUT x is still the full
@@ -467,6 +486,12 @@ size_t lqcd_reduce_workspace_bytes(const lqcd_lattice* lat);
 /* Mean plaquette: the average of Re tr U_munu(x) / 3 over sites and the six planes. */
 int lqcd_plaquette(double* plaquette_host, const void* gauge_dev, const lqcd_lattice* lat,
                    void* workspace_dev, size_t workspace_bytes, void* stream);
+/* Re <a, b> = Re sum_x a(x)^dag b(x) of two FP64 full spinor fields (n5 = 1),
+ * summed in FP64 in a fixed order (deterministic): the pseudofermion action
+ * S = phi^dag (M^dag M)^-1 phi = Re <phi, X> of the force's forward pass (HMC,
+ * Sec. 4 of the paper; the action of FermionAction). */
+int lqcd_spinor_dot_re(double* result_host, const void* a_dev, const void* b_dev, const lqcd_lattice* lat,
+                       void* workspace_dev, size_t workspace_bytes, void* stream);
 /* Kinetic energy sum over links of tr(P^2) / 2. */
 int lqcd_momentum_kinetic(double* kinetic_host, const void* mom_dev, const lqcd_lattice* lat,
                           void* workspace_dev, size_t workspace_bytes, void* stream);

@@ -137,6 +137,7 @@ SIGNATURES = {
     "lqcd_tune_load": (_I, [C.c_char_p]),
     "lqcd_tune_entries": (_I, []),
     "lqcd_tune_get": (_I, [C.c_char_p]),
+    "lqcd_spinor_dot_re": (_I, [C.POINTER(C.c_double), _P, _P, _LAT, _P, _SZ, _P]),
     "lqcd_tune_clear": (None, []),
     "lqcd_tune_set_enabled": (None, [C.c_int]),
 }

@@ -319,6 +319,14 @@ def lqcd_plaquette(gauge, lat, workspace, stream=None) -> float:
     return out.value
 
 
+def lqcd_spinor_dot_re(a, b, lat, workspace, stream=None) -> float:
+    out = C.c_double()
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(lib.lqcd_spinor_dot_re(C.byref(out), _ptr(a), _ptr(b), C.byref(lat), _ptr(workspace), nbytes,
+                                  _stream(stream)))
+    return out.value
+
+
 def lqcd_momentum_kinetic(mom, lat, workspace, stream=None) -> float:
     out = C.c_double()
     nbytes = workspace.numel() * workspace.element_size()

@@ -45,13 +45,10 @@ def _pack(U, phi, lat):
 
 
 def _action(X, phi_dev, lat):
-    """S = Re <phi, X>, read back through the host layout (padding never enters)."""
-    n = 2 * lat.dims[0] * lat.dims[1] * lat.dims[2] * lat.dims[3] * 12
-    xh = torch.empty(n, dtype=torch.float64, device="cuda")
-    ph = torch.empty(n, dtype=torch.float64, device="cuda")
-    api.lqcd_spinor_unpack(xh, X, api.LQCD_F64, api.LQCD_FULL, lat)
-    api.lqcd_spinor_unpack(ph, phi_dev, api.LQCD_F64, api.LQCD_FULL, lat)
-    return torch.dot(xh, ph)
+    """S = Re <phi, X>, reduced in FP64 by the library (lqcd_spinor_dot_re)."""
+    ws = F.empty(api.lqcd_reduce_workspace_bytes(lat))
+    S = api.lqcd_spinor_dot_re(phi_dev, X, lat, ws)
+    return torch.tensor(S, dtype=torch.float64, device=X.device)
 
 
 class FermionAction(torch.autograd.Function):

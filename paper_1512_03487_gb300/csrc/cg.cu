@@ -227,6 +227,7 @@ struct Workspace {
   double* partials;
   unsigned int* counter;
   double* ss;  // CGNR: per-system |b|^2, then |b - M x|^2 of the last reliable update
+  double* bb;  // even-odd solve: per-system |b|^2 of the full system's source
   void* g32;   // mixed solves: FP32 / 12-real copy of the FP64 links
   double* r64;
   double* ax64;
@@ -245,7 +246,8 @@ struct Workspace {
 
 static int64_t max_blocks(const Geom& g, int subset) {
   const int64_t per = (g.nsites + 63) / 64;  // smallest block size used by reducing kernels is >= 64
-  return subset == LQCD_FULL ? 2 * per : per;
+  // an even-odd solve also reduces over both checkerboards of its full source (2 x ceil(nsites / 128) blocks)
+  return subset == LQCD_FULL ? 2 * per : per + 2;
 }
 
 static Workspace carve(void* base, const Geom& g, const lqcd_operator& op, const lqcd_solver_params& p, int subset,
@@ -265,6 +267,7 @@ static Workspace carve(void* base, const Geom& g, const lqcd_operator& op, const
   w.partials = (double*)take(sizeof(double) * nsys * max_blocks(g, subset));
   w.counter = (unsigned int*)take(64);
   w.ss = (double*)take(sizeof(double) * MAX_SYS);
+  w.bb = (double*)take(sizeof(double) * MAX_SYS);
   w.r64 = (double*)take(field_bytes(g, LQCD_F64, subset));
   w.ax64 = (double*)take(field_bytes(g, LQCD_F64, subset));
   w.mid64 = (double*)take(field_bytes(g, LQCD_F64, subset));
@@ -341,6 +344,7 @@ struct Solver : CgEngine {
   int subset;
   bool mid_on = false;
   bool normal = false;  // CGNR: b is the right-hand side of M x = b, not of M^dag M x = b
+  const double* b_full = nullptr;  // even-odd solve: the full system's FP64 source (scales the exit test)
   Workspace w;
   const void* gauge64;
   const void* gauge_s;
@@ -358,6 +362,16 @@ struct Solver : CgEngine {
     }
     VecArgs a = va;
     a.red = rc_init;
+    if (b_full) {  // |b|^2 of the full system's source, over both checkerboards
+      VecArgs af = va;
+      af.full = 1;
+      af.b64 = b_full;
+      af.red = rc_ss;
+      af.red.result = w.bb;
+      k_b_minus<<<(unsigned)(2 * af.bpp), BLAS_BLOCK, 0, s>>>(af, nullptr, nullptr);
+      int st = after_launch("eo_solve: |b|^2");
+      if (st) return st;
+    }
     if (normal) {
       // |b|^2 in FP64 (the exit test's scale); r_0 = M^dag b in the inner iteration's
       // arithmetic: the FP64 operator for a plain solve, else the FP32 operator on the
@@ -512,7 +526,8 @@ namespace lqcd {
 
 static int cg_solve_impl(void* x, const void* b, const void* gauge, const void* gauge_sloppy, const lqcd_lattice* lat,
                          const lqcd_operator* op, const lqcd_solver_params* prm, int subset, lqcd_solve_info* info,
-                         void* workspace, size_t workspace_bytes, void* stream, bool normal) {
+                         void* workspace, size_t workspace_bytes, void* stream, bool normal,
+                         const void* b_full = nullptr) {
   const auto t0 = std::chrono::steady_clock::now();
   lqcd_solve_info local;
   lqcd_solve_info* inf = info ? info : &local;
@@ -534,6 +549,7 @@ static int cg_solve_impl(void* x, const void* b, const void* gauge, const void* 
   if (S.prm.check_interval <= 0) S.prm.check_interval = 16;
   S.subset = subset;
   S.normal = normal;
+  S.b_full = static_cast<const double*>(b_full);
   S.nsys = op->kind == LQCD_WILSON && !op->gparity ? S.g.n5 : 1;  // G-parity flavours form one system
   S.w = carve(workspace, S.g, *op, *prm, subset, S.nsys);
   if (workspace_bytes < S.w.total)
@@ -600,6 +616,7 @@ static int cg_solve_impl(void* x, const void* b, const void* gauge, const void* 
   if (normal) {
     S.rc_init.sysres = S.rc_reliable.sysres = 1;
     S.rc_init.result = S.rc_reliable.result = S.w.ss;
+    if (b_full) S.rc_init.scale2 = S.w.bb;
   }
   S.rc_init.delta2_mid = S.mid_on ? prm->delta_mid * prm->delta_mid : 0.0;
 
@@ -633,6 +650,7 @@ static int cg_solve_impl(void* x, const void* b, const void* gauge, const void* 
   key_append(key, S.mid_on);
   key_append(key, S.normal);
   key_append(key, S.op64.prec);
+  key_append(key, b_full);
 
   // one tuning pass per solver configuration (lattice, operator, inner formats), outside any capture
   if (S.ops.prec != LQCD_F64 && !op->gparity && hop_autotune_ready(s)) {
@@ -656,7 +674,7 @@ static int cg_solve_impl(void* x, const void* b, const void* gauge, const void* 
   if (e != cudaSuccess && out_status == LQCD_OK) out_status = cuda_fail(e, "cg: state readback");
   double worst = 0.0;
   for (int i = 0; i < S.nsys; i++) {
-    const double den = normal ? sys[i].ss0 : sys[i].rr0;  // CGNR: |b - M x| / |b|
+    const double den = normal ? sys[i].ssx : sys[i].rr0;  // CGNR: |b - M x| / |b| (full system's |b|: even-odd solve)
     double rel = den > 0 ? std::sqrt(sys[i].rr_true / den) : 0.0;
     if (rel > worst || std::isnan(rel)) worst = rel;
   }
@@ -730,7 +748,8 @@ int lqcd_eo_solve(void* x, const void* b, const void* gauge, const void* gauge_s
     return st;
   }
   // the even half of x is the first checkerboard of the full field
-  st = cg_solve_impl(x, bhat, gauge, gauge_sloppy, lat, op, prm, LQCD_EVEN, inf, workspace, cgb, stream, true);
+  // tol applies to the full system: the exit test scales by |b|^2 of the full source
+  st = cg_solve_impl(x, bhat, gauge, gauge_sloppy, lat, op, prm, LQCD_EVEN, inf, workspace, cgb, stream, true, b);
   if (st != LQCD_OK && st != LQCD_ERR_NOT_CONVERGED && st != LQCD_ERR_TIMEOUT) return st;
   int rst;
   if (op->kind == LQCD_WILSON && inf->reliable_updates > 0) {

@@ -510,6 +510,23 @@ int lqcd_plaquette(double* plaq, const void* U, const lqcd_lattice* lat, void* w
   return plaquette(g, U, w, plaq, s);
 }
 
+int lqcd_spinor_dot_re(double* result, const void* a, const void* b, const lqcd_lattice* lat, void* ws,
+                       size_t ws_bytes, void* stream) {
+  Geom g;
+  int st = make_geom(lat, &g);
+  if (st) return st;
+  if (g.n5 != 1) return fail(LQCD_ERR_UNSUPPORTED, "lqcd_spinor_dot_re: n5 must be 1");
+  if (!result || !a || !b || !ws || mis16(a) || mis16(b) || ((uintptr_t)ws & 255))
+    return fail(LQCD_ERR_ARG, "lqcd_spinor_dot_re: pointer");
+  if (ws_bytes < reduce_ws_bytes(g)) return fail(LQCD_ERR_WORKSPACE, "lqcd_spinor_dot_re: workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  const ReduceWs w = reduce_ws(ws);
+  if ((st = zero_counter(w, s))) return st;
+  dot_kernel<<<site_grid(g), HMC_BLOCK, 0, s>>>(a, b, g, (int64_t)cb_spinor_bytes(g, LQCD_F64), reduce_ctx(w));
+  if ((st = after_launch("dot_kernel"))) return st;
+  return read_result(w, result, s);
+}
+
 int lqcd_momentum_kinetic(double* kin, const void* P, const lqcd_lattice* lat, void* ws, size_t ws_bytes,
                           void* stream) {
   Geom g;

@@ -410,7 +410,8 @@ struct SysState {
   double maxrr_mid;   // max iterated |r|^2 since the last residual replacement of either level
   double delta2_mid;  // delta_mid^2 (0 disables the FP32-arithmetic replacements)
   double ss0;         // CGNR: |b|^2 of the system M x = b
-  double tol2_sys;    // CGNR: tol^2 |b|^2, the exit test on the FP64 |b - M x|^2
+  double tol2_sys;    // CGNR: tol^2 ssx, the exit test on the FP64 |b - M x|^2
+  double ssx;         // CGNR: the exit test's scale |b'|^2: ss0, or the full system's |b|^2 of an even-odd solve
   int done;
   int pad;
 };
@@ -452,6 +453,9 @@ struct ReduceCtx {
   double delta2_mid;      // FIN_INIT: delta_mid^2 (0 = no intermediate replacements)
   int sysres;             // FIN_INIT / FIN_RELIABLE of CGNR: result[s] holds |b|^2 / the FP64 |b - M x|^2,
                           // which sets and decides the exit test (tol applies to M x = b)
+  const double* scale2;   // FIN_INIT of CGNR, or null: per-system |b|^2 that the exit test scales tol by instead
+                          // of result[s] (an even-odd solve: the full system's source, so that tol applies to
+                          // ||b - D x|| / ||b||, whose even rows are b_hat - M_hat x_e and odd rows vanish)
   int maxiter;            // FIN_UPDATE: request a final FP64 residual once this many iterations ran
   int cond;               // FIN_UPDATE: 1 = set h_rel / h_mid (device-driven graph), 0 = pause for the host
   cudaGraphConditionalHandle h_rel;  // IF node running the reliable update (when cond)
@@ -529,8 +533,9 @@ __device__ inline void finalize_totals(const ReduceCtx& rc, const double* totals
         st.delta2 = rc.delta2;
         st.delta2_mid = rc.delta2_mid;
         st.ss0 = rc.sysres ? rc.result[s] : t;
-        st.tol2_sys = rc.tol2_rel * st.ss0;
-        if (!finite(t) || !finite(st.ss0)) bad = true;
+        st.ssx = rc.scale2 ? rc.scale2[s] : st.ss0;
+        st.tol2_sys = rc.tol2_rel * st.ssx;
+        if (!finite(t) || !finite(st.ss0) || !finite(st.ssx)) bad = true;
         st.done = (t == 0.0 || st.ss0 == 0.0) ? 1 : 0;
         n_done += st.done;
       }

@@ -1,5 +1,6 @@
-"""The oracle reproduces its frozen outputs in tests/golden/oracle_regression.json
-(written by tests/golden/make_golden.py from oracle/ only; see the README there)."""
+"""The oracle reproduces its frozen outputs in tests/golden/oracle_regression.json,
+written by tests/golden/make_golden.py, which imports only oracle/ and synthetic/:
+a regression freeze of the oracle, not a pin (the pins are in tests/test_oracle_*.py)."""
 import importlib.util
 import json
 import os
