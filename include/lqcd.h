@@ -386,9 +386,10 @@ int lqcd_batch_cg_solve(int n, const lqcd_batch_item* items, int recon, const lq
  *    first lqcd_batch_cg_solve of each batch shape);
  *  - "hop prec=P recon=R dagger=D epi=E red=Q full=F lat=XxYxZxT n5=N" ->
  *    launch-shape index of an FP32 / FP16 hop kernel (one site per thread
- *    with 0: 128, 1: 64, 2: 256 threads per block, 3: 128 threads and at
- *    least 6 resident blocks per SM; 4: 128 threads, two sites per thread in
- *    packed FP32x2 arithmetic, 3 blocks per SM). All shapes give
+ *    with 0: 128 threads per block, registers as the compiler chooses; 1: 128
+ *    threads and at least 7 resident blocks per SM; 2: 256 threads; 3: 128
+ *    threads and at least 5 blocks per SM; 4: 128 threads, two sites per
+ *    thread in packed FP32x2 arithmetic, 3 blocks per SM). All shapes give
  *    bit-identical hop results. A hop key is
  *    timed (one warm-up and three launches of every shape, back to back on
  *    the caller's stream, which is synchronised) on its first launch outside

@@ -174,6 +174,66 @@ template <> __device__ __forceinline__ double bc_phase<double>(const Geom& g, in
 template <> __device__ __forceinline__ float bc_phase<float>(const Geom& g, int mu) { return g.bcf[mu]; }
 template <> __device__ __forceinline__ dfl bc_phase<dfl>(const Geom& g, int mu) { return dfl(g.bcf[mu], 0.f); }
 
+// FP32 a + c and a - c for a the low (H = 0) or high (H = 1) FP16 half of the
+// word w (add / sub with an f16 and an f32 operand, sm_100 and later): the
+// conversion of a is exact, so each equals the FP32 operation on the converted
+// value, rounded once.
+template <int H> __device__ __forceinline__ float add_h(unsigned int w, float c) {
+  float d;
+  if (H == 0) asm("{.reg .b16 l, u; mov.b32 {l, u}, %1; add.rn.f32.f16 %0, l, %2;}" : "=f"(d) : "r"(w), "f"(c));
+  else asm("{.reg .b16 l, u; mov.b32 {l, u}, %1; add.rn.f32.f16 %0, u, %2;}" : "=f"(d) : "r"(w), "f"(c));
+  return d;
+}
+template <int H> __device__ __forceinline__ float sub_h(unsigned int w, float c) {
+  float d;
+  if (H == 0) asm("{.reg .b16 l, u; mov.b32 {l, u}, %1; sub.rn.f32.f16 %0, l, %2;}" : "=f"(d) : "r"(w), "f"(c));
+  else asm("{.reg .b16 l, u; mov.b32 {l, u}, %1; sub.rn.f32.f16 %0, u, %2;}" : "=f"(d) : "r"(w), "f"(c));
+  return d;
+}
+// the real (H = 0) or imaginary (H = 1) part of the complex FP16 pair in w
+template <int H> __device__ __forceinline__ float part_h(unsigned int w) {
+  const __half2 v = *reinterpret_cast<const __half2*>(&w);
+  return H == 0 ? __low2float(v) : __high2float(v);
+}
+
+// One projected complex component from FP16 data: a + C q with C = +1 (0),
+// -1 (1), +i (2), -i (3); a and q are complex FP16 pairs (re low, im high).
+template <int C>
+__device__ __forceinline__ cpx<float> proj_h(unsigned int a, unsigned int q) {
+  if (C == 0) return mk(add_h<0>(a, part_h<0>(q)), add_h<1>(a, part_h<1>(q)));
+  if (C == 1) return mk(sub_h<0>(a, part_h<0>(q)), sub_h<1>(a, part_h<1>(q)));
+  if (C == 2) return mk(sub_h<0>(a, part_h<1>(q)), add_h<1>(a, part_h<0>(q)));  // a + i q
+  return mk(add_h<0>(a, part_h<1>(q)), sub_h<1>(a, part_h<0>(q)));               // a - i q
+}
+
+// FP16 storage: (1 + S gamma_mu) applied to the stored halves (each projected
+// component one conversion and one mixed-precision add), the same values as
+// converting all 24 components and projecting in FP32; returns the site norm.
+template <int MU, int S>
+__device__ __forceinline__ float load_project_f16(const void* in, int64_t stride, int64_t idx, Half<float>& h) {
+  const uint4* b = reinterpret_cast<const uint4*>(in);
+  const float nrm = __ldg(SpinorIO<LQCD_F16>::norm_ptr(in, stride) + idx);
+  unsigned int w[12];  // complex k = spin * 3 + colour in word k
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const uint4 v = __ldg(b + c * stride + idx);
+    w[4 * c] = v.x;
+    w[4 * c + 1] = v.y;
+    w[4 * c + 2] = v.z;
+    w[4 * c + 3] = v.w;
+  }
+  // h0 = p0 + c0 p_k0, h1 = p1 + c1 p_k1 (the chiral-basis projection of project<MU, S>)
+  constexpr int K0 = MU < 2 ? 3 : 2, K1 = MU < 2 ? 2 : 3;
+  constexpr int C0 = MU == 0 ? (S > 0 ? 3 : 2) : MU == 1 ? (S > 0 ? 1 : 0) : MU == 2 ? (S > 0 ? 3 : 2) : (S > 0 ? 0 : 1);
+  constexpr int C1 = MU == 0 ? (S > 0 ? 3 : 2) : MU == 1 ? (S > 0 ? 0 : 1) : MU == 2 ? (S > 0 ? 2 : 3) : (S > 0 ? 0 : 1);
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    h.v[c] = proj_h<C0>(w[c], w[3 * K0 + c]);
+    h.v[3 + c] = proj_h<C1>(w[3 + c], w[3 * K1 + c]);
+  }
+  return nrm;
+}
+
 // Load the neighbour spinor and spin-project it with (1 + S gamma_mu). The
 // linear factor the half spinor still needs -- the boundary phase of a
 // wrapping hop and, for FP16 storage, the neighbour's site norm -- is returned
@@ -185,9 +245,8 @@ __device__ __forceinline__ typename PrecTraits<P>::real load_project(const void*
   Spinor<T> s;
   T f;
   if constexpr (P == LQCD_F16) {
-    float nrm;
-    SpinorIO<P>::load_unscaled(in, g.sstride, idx, s, nrm);
-    f = nrm;
+    f = load_project_f16<MU, S>(in, g.sstride, idx, h);
+    return wrap ? bc_phase<T>(g, MU) * f : f;
   } else {
     SpinorIO<P>::load(in, g.sstride, idx, s);
     f = T(1);

@@ -28,7 +28,7 @@ constexpr int HOP_BLOCK = 128;
 // one site per thread is fastest for the plain FP16 / 12-real hop (27 us
 // against 31-33 us for two sites per thread, whose packed FP32x2 arithmetic
 // needs 32 % fewer instructions but 168-222 registers), so it is the default.
-#define LQCD_HOP_SHAPES(X) X(0, 128, 1, 0) X(1, 64, 1, 0) X(2, 256, 1, 0) X(3, 128, 1, 6) X(4, 128, 2, 3)
+#define LQCD_HOP_SHAPES(X) X(0, 128, 1, 0) X(1, 128, 1, 7) X(2, 256, 1, 0) X(3, 128, 1, 5) X(4, 128, 2, 3)
 constexpr int HOP_SHAPES = 5;
 // The shape used when the table holds no choice for a hop.
 constexpr int HOP_SHAPE_DEFAULT = 0;
