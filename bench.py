@@ -55,7 +55,8 @@ DELTA_3LVL, DELTA_MID = VARIANTS[3][1], VARIANTS[3][2]
 DELTA_NORMAL_FP32 = 1e-5
 PREC_TAG = {1: "f32", 2: "f16"}
 PROFILE_JSON = {q: os.path.join(ROOT, "profiles", f"hop_{PREC_TAG[q]}r12_24x24x24x48.json") for q in (1, 2)}
-DSLASH_COMMON = ["dslash_kernels.cuh", "lqcd_common.cuh", "cg_site.cuh", "dslash_launch.cuh"]
+DSLASH_COMMON = ["dslash_kernels.cuh", "lqcd_common.cuh", "cg_site.cuh", "dslash_launch.cuh", "hop_pair.cuh", "df.cuh",
+                 "lqcd_internal.h"]
 
 
 def parse_args():
@@ -73,13 +74,18 @@ def parse_args():
                          "(profilers list kernels inside conditional graph bodies only this way)")
     ap.add_argument("--check-interval", type=int, default=64,
                     help="iterations per graph launch / host check of the solver")
+    ap.add_argument("--tune-file", default=None,
+                    help="autotuner table: loaded before the run if the file exists (no launch shape is then "
+                         "re-timed), written after it otherwise -- so that a profiler run launches the same "
+                         "shapes as the plain run that wrote it")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the domain-wall, multi-RHS, batch and force measurements")
     ap.add_argument("--hop-shape", default=None,
                     help="hops mode: run only this shape (f32r12_24x24x24x48, f16r12_24x24x24x48, "
                          "dwf_f32r12_16x4_ls16, f32r12_32x4_12rhs)")
-    ap.add_argument("--hop-prec", type=int, choices=[1, 2], default=HEADLINE_PREC,
-                    help="storage precision of the hop timed by --mode hop (1 FP32, 2 FP16)")
+    ap.add_argument("--hop-prec", type=int, choices=[0, 1, 2, 3], default=HEADLINE_PREC,
+                    help="the hop timed by --mode hop: 1 FP32, 2 FP16 storage (12-real links); 0 FP64, "
+                         "3 FP64 fields in double-float arithmetic (18-real links)")
     ap.add_argument("--mode", choices=["full", "step", "hop", "hops", "dwf"], default="full",
                     help="step: only the timed solves; hop: only the dominant kernel's roofline loop; "
                          "hops: the three hop shapes (profiling)")
@@ -286,7 +292,7 @@ def threads_used():
 def dslash_sources_hash(prec):
     """Hash of the sources that make the hop kernel of one storage precision."""
     h = hashlib.sha256()
-    for f in DSLASH_COMMON + [f"dslash_{PREC_TAG[prec]}.cu"]:
+    for f in DSLASH_COMMON + [f"dslash_{PREC_TAG[prec]}.cu", f"dslash_{PREC_TAG[prec]}_dag.cu"]:
         with open(os.path.join(ROOT, "paper_1512_03487_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -317,6 +323,19 @@ def run_lqcd(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
+    tune_loaded = False
+    if args.tune_file and os.path.exists(args.tune_file):
+        L.lqcd_tune_load(args.tune_file)
+        tune_loaded = True
+    try:
+        _run_lqcd(args, world, rank, local, L, F, dev, stream)
+    finally:
+        if args.tune_file and not tune_loaded and rank == 0:
+            L.lqcd_tune_save(args.tune_file)
+
+
+def _run_lqcd(args, world, rank, local, L, F, dev, stream):
+    import torch
     if args.mode == "hops":
         # profiling mode: the three hop shapes of the hot path on zero-filled fields
         # (the kernels do the same work whatever the values), args.steps launches each
@@ -397,7 +416,14 @@ def run_lqcd(args, world, rank, local):
         return e0.elapsed_time(e1), out
 
     if args.mode == "hop":
-        # profiling mode: only the dominant kernel's roofline loop
+        # profiling mode: only one hop's roofline loop
+        if args.hop_prec in (0, 3):
+            L.lqcd_gauge_pack(g64, L.LQCD_F64, 18, U_dev, lat)
+            roof = (fp64_hop_roofline if args.hop_prec == 0 else df_hop_roofline)(L, F, lat, g64, flush, stream, vh,
+                                                                                 launches=args.steps)
+            if rank == 0:
+                print(json.dumps({"mode": "hop", "roofline": roof}), flush=True)
+            return
         L.lqcd_gauge_pack(gs[args.hop_prec], args.hop_prec, 12, U_dev, lat)
         roof = hop_roofline(L, F, lat, gs[args.hop_prec], args.hop_prec, flush, stream, vh, launches=args.steps)
         if rank == 0:
@@ -457,6 +483,7 @@ def run_lqcd(args, world, rank, local):
     L.lqcd_gauge_pack(gs[1], 1, 12, U_dev, lat)
     roof32 = hop_roofline(L, F, lat, gs[1], 1, flush, stream, vh)
     roof64 = fp64_hop_roofline(L, F, lat, g64, flush, stream, vh)
+    roofdf = df_hop_roofline(L, F, lat, g64, flush, stream, vh)
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -486,8 +513,10 @@ def run_lqcd(args, world, rank, local):
         "roofline": roof,
         "roofline_fp32_hop": roof32,
         "roofline_fp64_hop": roof64,
+        "roofline_df_hop": roofdf,
         "gpu_launches": int(launches),
         "clocks": clk,
+        "tuned_hop_shapes": solve_hop_shapes(L, dims),
     }
     if e2e is not None:
         line["e2e"] = e2e
@@ -528,11 +557,12 @@ def _cold_hop_seconds(L, F, lat, g, prec, recon, flush, stream, launches):
     """Mean event-timed duration of one checkerboard hop launch, L2 flushed before each."""
     import torch
     op = L.operator(prec=prec, recon=recon)
+    fprec = L.LQCD_F64 if prec == L.LQCD_F64_DF else prec  # double-float arithmetic on FP64 fields
     rng = np.random.default_rng(5)
     shape = F.host_spinor_shape(lat, L.LQCD_ODD)
     host = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
-    fin = F.spinor_to_device(host, lat, prec, L.LQCD_ODD)
-    out = F.empty(L.lqcd_spinor_bytes(lat, prec, L.LQCD_EVEN))
+    fin = F.spinor_to_device(host, lat, fprec, L.LQCD_ODD)
+    out = F.empty(L.lqcd_spinor_bytes(lat, fprec, L.LQCD_EVEN))
     for _ in range(3):
         L.lqcd_dslash(out, fin, g, lat, op, L.LQCD_EVEN, 0)
     times = []
@@ -566,13 +596,41 @@ def hop_roofline(L, F, lat, gsl, prec, flush, stream, vh, launches=20):
     except (OSError, ValueError):
         pass
     name = {1: "F32", 2: "F16"}[prec]
+    shape = L.lqcd_tune_get(hop_key(prec, 12, 0, 0, 0, lat.dims, 1))
     # no-reuse model: every neighbour spinor fetched once per use (8 in, 8 links, 1 out)
     no_reuse = {1: 8 * 48 + 8 * 96 + 96, 2: 8 * 24 + 8 * 52 + 52}[prec]
     return {"bound": "hbm", "kernel": f"hop_kernel<{name}, recon 12> (one checkerboard, cold L2)",
             "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
             "peak_source": peak_src, "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_site * vh,
             "no_reuse_bytes_per_launch": no_reuse * vh,
-            "launch_us": round(t * 1e6, 2), "gflops": round(FLOP_PER_SITE * vh / t / 1e9, 1)}
+            "launch_us": round(t * 1e6, 2), "gflops": round(FLOP_PER_SITE * vh / t / 1e9, 1),
+            "launch_shape": {"index": shape, "meaning": HOP_SHAPE_MEANING.get(shape, "default")}}
+
+
+HOP_SHAPE_MEANING = {0: "128 threads, one site per thread", 1: "128 threads, one site per thread, <= 72 registers",
+                     2: "128 threads, one site per thread, spin components paired in packed FP32x2 arithmetic, "
+                        "<= 72 registers", 3: "128 threads, one site per thread, <= 102 registers",
+                     4: "128 threads, two sites per thread in packed FP32x2 arithmetic",
+                     5: "128 threads, one site per thread, links staged in shared memory when n5 >= 4",
+                     6: "128 threads, one site per thread, spin components paired in packed FP32x2 arithmetic"}
+
+
+def hop_key(prec, recon, dagger, epi, red, dims, n5, full=0):
+    """The autotuner table's key of one hop kernel launch (include/lqcd.h)."""
+    X, Y, Z, T = (int(d) for d in dims)
+    return f"hop prec={prec} recon={recon} dagger={dagger} epi={epi} red={red} full={full} lat={X}x{Y}x{Z}x{T} n5={n5}"
+
+
+def solve_hop_shapes(L, dims):
+    """The launch shapes the tuner chose for the inner iteration's FP16 hops and the FP32 level's hops."""
+    out = {}
+    for prec in (2, 1):
+        for dag, epi, red, what in ((0, 0, 0, "H_oe p"), (0, 1, 1, "M_hat p with |.|^2"), (1, 0, 0, "H^dag"),
+                                    (1, 1, 2, "M_hat^dag with the fused CG update")):
+            v = L.lqcd_tune_get(hop_key(prec, 12, dag, epi, red, dims, 1))
+            if v >= 0:
+                out[f"prec{prec} dagger{dag} epi{epi} red{red} ({what})"] = v
+    return out
 
 
 # GB300 FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA per SM per clock x 2 flop x 2.07 GHz
@@ -605,6 +663,25 @@ def fp64_hop_roofline(L, F, lat, g64, flush, stream, vh, launches=5):
             "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
             "measured_fma_chain_tflops": round(meas, 4), "frac_of_measured_fma": round(tf / meas, 4),
             "launch_us": round(t * 1e6, 2), "hbm_gbs": round((8 * 144 + 192 + 192) * vh / t / 1e9, 1)}
+
+
+# GB300 FP32 peak from unit counts and clock: 152 SMs x 128 FP32 FMA per SM per clock x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def df_hop_roofline(L, F, lat, g64, flush, stream, vh, launches=5):
+    """The reliable updates' hop: FP64 fields in double-float arithmetic (LQCD_F64_DF). Its
+    1320 FP64-equivalent flop per site against the FP64 peak it replaces, and its FP32
+    instruction rate (about 19,400 FP32 instructions per site, ncu) against the FP32 pipe."""
+    t = _cold_hop_seconds(L, F, lat, g64, L.LQCD_F64_DF, 18, flush, stream, launches)
+    t64 = _cold_hop_seconds(L, F, lat, g64, L.LQCD_F64, 18, flush, stream, 3)
+    tf = FLOP_PER_SITE * vh / t / 1e12
+    return {"bound": "alu", "kernel": "hop_kernel<F64_DF, recon 18> (one checkerboard, cold L2)",
+            "achieved_fp64_equivalent_tflops": round(tf, 4), "fp64_peak": round(FP64_PEAK_TFLOPS, 4),
+            "frac_of_fp64_peak": round(tf / FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+            "fp32_peak": round(FP32_PEAK_TFLOPS, 2), "launch_us": round(t * 1e6, 2),
+            "fp64_hop_launch_us": round(t64 * 1e6, 2), "speedup_vs_fp64_hop": round(t64 / t, 2),
+            "hbm_gbs": round((8 * 144 + 192 + 192) * vh / t / 1e9, 1)}
 
 
 def measured_peak():

@@ -387,12 +387,18 @@ int lqcd_batch_cg_solve(int n, const lqcd_batch_item* items, int recon, const lq
  *  - "hop prec=P recon=R dagger=D epi=E red=Q full=F lat=XxYxZxT n5=N" ->
  *    launch-shape index of an FP32 / FP16 hop kernel (one site per thread
  *    with 0: 128 threads per block, registers as the compiler chooses; 1: 128
- *    threads and at least 7 resident blocks per SM; 2: 256 threads; 3: 128
- *    threads and at least 5 blocks per SM; 4: 128 threads, two sites per
- *    thread in packed FP32x2 arithmetic, 3 blocks per SM). All shapes give
+ *    threads and at least 7 resident blocks per SM; 2: as 6 with at least 7
+ *    blocks per SM; 3: 128 threads and at least 5 blocks per SM; 4: 128 threads, two sites per
+ *    thread in packed FP32x2 arithmetic, 3 blocks per SM; 5: 128 threads,
+ *    one site per thread, at least 6 blocks per SM, the eight links of each 4D
+ *    site loaded once into shared memory for its n5 threads when n5 >= 4;
+ *    6: 128 threads, one site per thread, the two spin components of each
+ *    half spinor paired in packed FP32x2 arithmetic). All shapes give
  *    bit-identical hop results. A hop key is
- *    timed (one warm-up and three launches of every shape, back to back on
- *    the caller's stream, which is synchronised) on its first launch outside
+ *    timed (a warm-up of every shape, then three interleaved rounds of two
+ *    back-to-back launches each on the caller's stream, which is
+ *    synchronised; shape 0 is kept unless another is at least 3 % faster
+ *    in its fastest round) on its first launch outside
  *    a stream capture when running it again cannot change what it leaves
  *    behind (no reduction, output not aliasing an input); the solvers time
  *    their in-iteration hops (which reduce and are captured in graphs) once

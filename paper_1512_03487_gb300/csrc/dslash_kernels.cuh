@@ -265,10 +265,13 @@ template <typename T> __device__ __forceinline__ void conj_link(Link<T>& u) {
 // (forward, f = 0 / 1) or -1 / +1 (backward) instead of the boundary phase,
 // and the link is conjugated when its owner -- the site for the forward hop,
 // the neighbour (flavour f') for the backward hop -- is flavour 1.
+// sl: this 4D site's eight links staged in shared memory (forward link of mu
+// at 2 mu, the backward hop's link at 2 mu + 1), or null to load them here.
 template <int MU, int P, int R, bool DAG, bool GP = false>
 __device__ __forceinline__ void hop_dir(Spinor<typename PrecTraits<P>::real>& acc, const Geom& g,
                                         const void* gauge, const Coord& x, int64_t cb, int64_t i5,
-                                        int parity, const void* in) {
+                                        int parity, const void* in,
+                                        const Link<typename PrecTraits<P>::real>* sl = nullptr) {
   using T = typename PrecTraits<P>::real;
   constexpr int SF = DAG ? +1 : -1;  // forward hop carries (1 + SF gamma_mu)
   const int64_t n5 = g.n5;
@@ -285,7 +288,8 @@ __device__ __forceinline__ void hop_dir(Spinor<typename PrecTraits<P>::real>& ac
     Half<T> h;
     const T f = sgn * load_project<P, MU, SF>(in, g, nb * n5 + f_nb, wrap, h);
     Link<T> u;
-    LinkIO<P, R>::load(gauge, g.gstride, parity * 4 + MU, cb, u);
+    if (sl) u = sl[2 * MU];
+    else LinkIO<P, R>::load(gauge, g.gstride, parity * 4 + MU, cb, u);
     if (GP && i5 == 1) conj_link(u);
     Half<T> w;
     link_mul(u, h, w);
@@ -304,7 +308,8 @@ __device__ __forceinline__ void hop_dir(Spinor<typename PrecTraits<P>::real>& ac
     Half<T> h;
     const T f = sgn * load_project<P, MU, -SF>(in, g, nb * n5 + f_nb, wrap, h);
     Link<T> u;
-    LinkIO<P, R>::load(gauge, g.gstride, (1 - parity) * 4 + MU, nb, u);
+    if (sl) u = sl[2 * MU + 1];
+    else LinkIO<P, R>::load(gauge, g.gstride, (1 - parity) * 4 + MU, nb, u);
     if (GP && f_nb == 1) conj_link(u);
     Half<T> w;
     link_mul_dag(u, h, w);
@@ -437,10 +442,47 @@ __device__ __forceinline__ void hop_acc_rolled(const Geom& g, const void* gauge,
   }
 }
 
+// Both hops along mu with spin-paired packed arithmetic (hop_pair.cuh): the
+// projection and the link as in hop_dir, the products and the accumulation on
+// (spin 0, spin 1) pairs. FP32 / FP16 storage, no G-parity.
+template <int MU, int P, int R, bool DAG>
+__device__ __forceinline__ void hop_dir_sp(SPAcc& acc, const Geom& g, const void* gauge, const Coord& x, int64_t cb,
+                                           int64_t i5, int parity, const void* in, const Link<float>* sl) {
+  constexpr int SF = DAG ? +1 : -1;
+  const int64_t n5 = g.n5;
+#pragma unroll
+  for (int dir = 0; dir < 2; dir++) {
+    bool wrap;
+    const int64_t nb = neighbour_cb<MU>(g, x, dir == 0 ? +1 : -1, wrap);
+    Half<float> hh;
+    const float f = dir == 0 ? load_project<P, MU, SF>(in, g, nb * n5 + i5, wrap, hh)
+                             : load_project<P, MU, -SF>(in, g, nb * n5 + i5, wrap, hh);
+    SPHalf h, w;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      h.r[c] = make_float2(hh.v[c].r, hh.v[3 + c].r);
+      h.i[c] = make_float2(hh.v[c].i, hh.v[3 + c].i);
+    }
+    Link<float> u;
+    if (dir == 0) {
+      if (sl) u = sl[2 * MU];
+      else LinkIO<P, R>::load(gauge, g.gstride, parity * 4 + MU, cb, u);
+      link_mul_sp<false>(u, h, w);
+      accumulate_sp<MU, SF>(acc, w, f);
+    } else {
+      if (sl) u = sl[2 * MU + 1];
+      else LinkIO<P, R>::load(gauge, g.gstride, (1 - parity) * 4 + MU, nb, u);
+      link_mul_sp<true>(u, h, w);
+      accumulate_sp<MU, -SF>(acc, w, f);
+    }
+  }
+}
+
 // H in at output site j (= cb * n5 + i5) of checkerboard `parity`.
-template <int P, int R, bool DAG, bool GP = false>
+template <int P, int R, bool DAG, bool GP = false, bool SP = false>
 __device__ __forceinline__ void hop_acc(const Geom& g, const void* gauge, const void* in, int parity, int64_t j,
-                                        Spinor<typename PrecTraits<P>::real>& acc) {
+                                        Spinor<typename PrecTraits<P>::real>& acc,
+                                        const Link<typename PrecTraits<P>::real>* sl = nullptr) {
   const int64_t n5 = g.n5;
   int64_t cb, i5;
   if (n5 == 1) {
@@ -455,11 +497,29 @@ __device__ __forceinline__ void hop_acc(const Geom& g, const void* gauge, const 
     return;
   }
   const Coord x = cb_to_coord(g, cb, parity);
+  if constexpr (SP) {
+    static_assert(P == LQCD_F32 || P == LQCD_F16, "spin-paired hop: FP32 / FP16 storage");
+    SPAcc a;
+#pragma unroll
+    for (int c = 0; c < 3; c++) a.ur[c] = a.ui[c] = a.lr[c] = a.li[c] = make_float2(0.f, 0.f);
+    hop_dir_sp<0, P, R, DAG>(a, g, gauge, x, cb, i5, parity, in, sl);
+    hop_dir_sp<1, P, R, DAG>(a, g, gauge, x, cb, i5, parity, in, sl);
+    hop_dir_sp<2, P, R, DAG>(a, g, gauge, x, cb, i5, parity, in, sl);
+    hop_dir_sp<3, P, R, DAG>(a, g, gauge, x, cb, i5, parity, in, sl);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      acc.v[c] = mk(a.ur[c].x, a.ui[c].x);
+      acc.v[3 + c] = mk(a.ur[c].y, a.ui[c].y);
+      acc.v[6 + c] = mk(a.lr[c].x, a.li[c].x);
+      acc.v[9 + c] = mk(a.lr[c].y, a.li[c].y);
+    }
+    return;
+  }
   zero(acc);
-  hop_dir<0, P, R, DAG, GP>(acc, g, gauge, x, cb, i5, parity, in);
-  hop_dir<1, P, R, DAG, GP>(acc, g, gauge, x, cb, i5, parity, in);
-  hop_dir<2, P, R, DAG, GP>(acc, g, gauge, x, cb, i5, parity, in);
-  hop_dir<3, P, R, DAG, GP>(acc, g, gauge, x, cb, i5, parity, in);
+  hop_dir<0, P, R, DAG, GP>(acc, g, gauge, x, cb, i5, parity, in, sl);
+  hop_dir<1, P, R, DAG, GP>(acc, g, gauge, x, cb, i5, parity, in, sl);
+  hop_dir<2, P, R, DAG, GP>(acc, g, gauge, x, cb, i5, parity, in, sl);
+  hop_dir<3, P, R, DAG, GP>(acc, g, gauge, x, cb, i5, parity, in, sl);
 }
 
 // The epilogue at output site j of the hop result acc = H in (see EpiCoef).
@@ -507,12 +567,13 @@ __device__ __forceinline__ void hop_epilogue(const Geom& g, const void* xb, int6
 }
 
 // The result at output site j (= cb * n5 + i5) of checkerboard `parity`.
-template <int P, int R, bool DAG, int EPI, bool GP = false>
+template <int P, int R, bool DAG, int EPI, bool GP = false, bool SP = false>
 __device__ __forceinline__ void hop_site(const Geom& g, const void* gauge, const void* in, const void* xb,
                                          int parity, int64_t j, const EpiCoef& c,
-                                         Spinor<typename PrecTraits<P>::real>& res) {
+                                         Spinor<typename PrecTraits<P>::real>& res,
+                                         const Link<typename PrecTraits<P>::real>* sl = nullptr) {
   Spinor<typename PrecTraits<P>::real> acc;
-  hop_acc<P, R, DAG, GP>(g, gauge, in, parity, j, acc);
+  hop_acc<P, R, DAG, GP, SP>(g, gauge, in, parity, j, acc, sl);
   hop_epilogue<P, DAG, EPI>(g, xb, j, c, acc, res);
 }
 
@@ -523,13 +584,51 @@ template <typename T> __device__ __forceinline__ T norm2_site(const Spinor<T>& r
   return s;
 }
 
+// ---- link staging for the L_s-replicated / multi-RHS hop (n5 >= 4): the n5
+// threads of a 4D site share its eight links (the paper's gauge field reused
+// L_s times, Sec. 3), so a block loads (and for 12-real links rebuilds and, for
+// FP16, converts) each link of its 4D sites once into shared memory and every
+// thread reads them from there instead of repeating that work n5 times.
+constexpr int STAGE_MIN_N5 = 4;
+template <int BLOCK> constexpr int stage_sites() { return BLOCK / STAGE_MIN_N5 + 2; }
+
+// Checkerboard index of the neighbour of x one hop back along a runtime mu.
+__device__ __forceinline__ int64_t back_neighbour_cb(const Geom& g, const Coord& x, int mu) {
+  const int L = mu == 0 ? g.X : mu == 1 ? g.Y : mu == 2 ? g.Z : g.T;
+  const int xm = mu == 0 ? x.c[0] : mu == 1 ? x.c[1] : mu == 2 ? x.c[2] : x.c[3];
+  const uint32_t st = mu == 0 ? 1u : mu == 1 ? (uint32_t)g.st[1] : mu == 2 ? (uint32_t)g.st[2] : (uint32_t)g.st[3];
+  const uint32_t lex = xm == 0 ? x.lex + (uint32_t)(L - 1) * st : x.lex - st;
+  return (int64_t)(lex >> 1);
+}
+
+// Stages the links of the block's 4D sites cb0 .. cb0 + nls - 1 (checkerboard
+// `parity`) into sl[ls * 8 + d]; every thread of the block must call it.
+template <int P, int R, int BLOCK>
+__device__ __forceinline__ void stage_links(const Geom& g, const void* gauge, int parity, int64_t cb0, int nls,
+                                            Link<typename PrecTraits<P>::real>* sl) {
+  for (int t = threadIdx.x; t < nls * 8; t += BLOCK) {
+    const int ls = t >> 3, d = t & 7, mu = d >> 1;
+    const int64_t cb = cb0 + ls;
+    if (cb >= g.Vh) continue;
+    Link<typename PrecTraits<P>::real> u;
+    if ((d & 1) == 0) {
+      LinkIO<P, R>::load(gauge, g.gstride, parity * 4 + mu, cb, u);
+    } else {
+      const Coord x = cb_to_coord(g, cb, parity);
+      LinkIO<P, R>::load(gauge, g.gstride, (1 - parity) * 4 + mu, back_neighbour_cb(g, x, mu), u);
+    }
+    sl[t] = u;
+  }
+  __syncthreads();
+}
+
 // One launch computes BLOCK * SPT output sites per block. SPT = 1: one site
 // per thread, any precision. SPT = 2 (FP32 and FP16 storage, not G-parity):
 // thread t of block blk computes sites j0 = blk BLOCK 2 + t and j1 = j0 +
 // BLOCK together in packed FP32x2 arithmetic (hop_pair.cuh), so that every
 // load instruction of a warp stays one coalesced access and the two sites
 // share each FP32 instruction of the hop.
-template <int P, int R, bool DAG, int EPI, int RED, int BLOCK, bool GP, int SPT>
+template <int P, int R, bool DAG, int EPI, int RED, int BLOCK, bool GP, int SPT, bool LS = false, bool SP = false>
 __device__ __forceinline__ void hop_body(const HopArgs& A) {
   using T = typename PrecTraits<P>::real;
   static_assert(SPT == 1 || (SPT == 2 && P != LQCD_F64 && !GP), "two sites per thread: FP32 / FP16, no G-parity");
@@ -547,13 +646,25 @@ __device__ __forceinline__ void hop_body(const HopArgs& A) {
   const int64_t first = (int64_t)blk * (BLOCK * SPT);
   if constexpr (SPT == 1) {
     const int64_t j = first + threadIdx.x;
+    // LS: links staged in shared memory once per 4D site when n5 >= STAGE_MIN_N5
+    const Link<T>* sl = nullptr;
+    if constexpr (LS) {
+      __shared__ Link<T> staged[stage_sites<BLOCK>() * 8];
+      const int64_t n5 = A.g.n5;
+      if (n5 >= STAGE_MIN_N5) {
+        const int64_t cb0 = first / n5;
+        const int64_t last = (first + BLOCK - 1 < A.g.nsites ? first + BLOCK - 1 : A.g.nsites - 1) / n5;
+        stage_links<P, R, BLOCK>(A.g, A.gauge, parity, cb0, (int)(last - cb0 + 1), staged);
+        if (j < A.g.nsites) sl = staged + (j / n5 - cb0) * 8;
+      }
+    }
     if constexpr (EPI == EPI_M5INV) {
       // every lane takes part in the fifth-dimension scan; lanes past the end
       // (whole 4D sites, since L_s divides the block) carry zeros and store nothing
       static_assert(RED == RED_NONE, "M5op^-1 epilogue without reduction");
       const bool live = j < A.g.nsites;
       Spinor<T> res;
-      if (live) hop_site<P, R, DAG, EPI, GP>(A.g, A.gauge, in, xb, parity, j, c, res);
+      if (live) hop_site<P, R, DAG, EPI, GP, SP>(A.g, A.gauge, in, xb, parity, j, c, res, sl);
       else zero(res);
       const int Ls = A.g.n5;
       m5inv_lanes(res, (int)(threadIdx.x & (unsigned)(Ls - 1)), Ls, A.m5_dagger != 0, (T)A.m5_a, (T)A.mf,
@@ -564,7 +675,7 @@ __device__ __forceinline__ void hop_body(const HopArgs& A) {
     T red = T(0);
     if (j < A.g.nsites) {
       Spinor<T> res;
-      hop_site<P, R, DAG, EPI, GP>(A.g, A.gauge, in, xb, parity, j, c, res);
+      hop_site<P, R, DAG, EPI, GP, SP>(A.g, A.gauge, in, xb, parity, j, c, res, sl);
       if constexpr (RED == RED_CG_UPDATE) {
         const int64_t ps = A.full ? parity * A.half_bytes : 0, vs = A.full ? parity * A.upd_half_bytes : 0;
         const int64_t rs = A.full ? parity * A.upd_rs_half_bytes : 0;
@@ -637,9 +748,14 @@ __device__ __forceinline__ void hop_body(const HopArgs& A) {
 // MINB: minimum resident blocks per SM the register allocation must allow
 // (__launch_bounds__; 0 leaves the choice to the compiler), one of the knobs
 // of the launch shapes the tuner times.
+//
+// SPT = -1: one site per thread with the links staged in shared memory (LS);
+// SPT = -2: one site per thread in spin-paired packed arithmetic (SP).
 template <int P, int R, bool DAG, int EPI, int RED, int BLOCK, bool GP = false, int SPT = 1, int MINB = 0>
 __global__ void __launch_bounds__(BLOCK, MINB) hop_kernel(const HopArgs A) {
-  hop_body<P, R, DAG, EPI, RED, BLOCK, GP, SPT>(A);
+  if constexpr (SPT == -1) hop_body<P, R, DAG, EPI, RED, BLOCK, GP, 1, true>(A);
+  else if constexpr (SPT == -2) hop_body<P, R, DAG, EPI, RED, BLOCK, GP, 1, false, true>(A);
+  else hop_body<P, R, DAG, EPI, RED, BLOCK, GP, SPT>(A);
 }
 
 }  // namespace lqcd

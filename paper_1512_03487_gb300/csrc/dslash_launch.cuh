@@ -8,7 +8,8 @@ namespace lqcd {
 
 template <int P, int R, bool DAG, int EPI, int RED, bool GP, int BLOCK, int SPT, int MINB>
 static int launch_hop_shape(HopArgs a, cudaStream_t s) {
-  const int64_t nb = (a.g.nsites + BLOCK * SPT - 1) / (BLOCK * SPT);
+  constexpr int SITES = SPT < 0 ? 1 : SPT;  // SPT -1 / -2: one site per thread (links staged / spin-paired)
+  const int64_t nb = (a.g.nsites + BLOCK * SITES - 1) / (BLOCK * SITES);
   a.blocks_per_parity = (int)nb;
   const int64_t grid = a.full ? 2 * nb : nb;
   if (grid == 0) return LQCD_OK;

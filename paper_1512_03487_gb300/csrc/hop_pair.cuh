@@ -312,4 +312,71 @@ __device__ __forceinline__ void hop_acc_pair(const Geom& g, const void* gauge, c
   hop_dir_pair<3, P, R, DAG>(acc, g, gauge, xa, xb, cb_a, cb_b, i5_a, i5_b, parity, in);
 }
 
+// ---------------------------------------------------------------------------
+// One site per thread with the two spin components of each half spinor paired:
+// H[c] = (h_0c, h_1c) as float2 of real parts and of imaginary parts, so
+// w_a = U h_a for a = 0, 1 is one packed product per term (the link element
+// broadcast to both lanes), and the accumulator holds spins (0, 1) and (2, 3)
+// as pairs. Same operations in the same order per lane as the one-site hop.
+struct SPHalf { float2 r[3], i[3]; };   // (h_0c, h_1c), c = 0..2
+struct SPAcc { float2 ur[3], ui[3], lr[3], li[3]; };  // spins (0,1) and (2,3), colour c
+
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 swp(float2 a) { return make_float2(a.y, a.x); }
+
+// w = U h (DAG: U^dag h) on spin pairs
+template <bool DAG>
+__device__ __forceinline__ void link_mul_sp(const Link<float>& u, const SPHalf& h, SPHalf& w) {
+#pragma unroll
+  for (int r = 0; r < 3; r++) {
+    float2 re, im;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      const cpx<float> m = DAG ? u.v[3 * c + r] : u.v[3 * r + c];
+      const float2 mr = bc2(m.r), mi = bc2(m.i);
+      if (c == 0) {
+        re = mul2(mr, h.r[c]);
+        im = mul2(mr, h.i[c]);
+      } else {
+        re = fma2(mr, h.r[c], re);
+        im = fma2(mr, h.i[c], im);
+      }
+      if (DAG) {
+        re = fma2(mi, h.i[c], re);
+        im = fma2(neg2(mi), h.r[c], im);
+      } else {
+        re = fma2(neg2(mi), h.i[c], re);
+        im = fma2(mi, h.r[c], im);
+      }
+    }
+    w.r[r] = re;
+    w.i[r] = im;
+  }
+}
+
+// acc += f (upper = w, lower = S B_mu^dag w) on spin pairs (see accumulate_scaled)
+template <int MU, int S>
+__device__ __forceinline__ void accumulate_sp(SPAcc& acc, const SPHalf& w, float f) {
+  const float fs = S > 0 ? f : -f;
+  const float2 F = bc2(f);
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    acc.ur[c] = fma2(F, w.r[c], acc.ur[c]);
+    acc.ui[c] = fma2(F, w.i[c], acc.ui[c]);
+    if (MU == 0) {         // spin 2 += fs i w1, spin 3 += fs i w0
+      acc.lr[c] = fma2(bc2(-fs), swp(w.i[c]), acc.lr[c]);
+      acc.li[c] = fma2(bc2(fs), swp(w.r[c]), acc.li[c]);
+    } else if (MU == 1) {  // spin 2 += fs w1, spin 3 += -fs w0
+      acc.lr[c] = fma2(make_float2(fs, -fs), swp(w.r[c]), acc.lr[c]);
+      acc.li[c] = fma2(make_float2(fs, -fs), swp(w.i[c]), acc.li[c]);
+    } else if (MU == 2) {  // spin 2 += fs i w0, spin 3 += -fs i w1
+      acc.lr[c] = fma2(make_float2(-fs, fs), w.i[c], acc.lr[c]);
+      acc.li[c] = fma2(make_float2(fs, -fs), w.r[c], acc.li[c]);
+    } else {               // spin 2 += fs w0, spin 3 += fs w1
+      acc.lr[c] = fma2(bc2(fs), w.r[c], acc.lr[c]);
+      acc.li[c] = fma2(bc2(fs), w.i[c], acc.li[c]);
+    }
+  }
+}
+
 }  // namespace lqcd

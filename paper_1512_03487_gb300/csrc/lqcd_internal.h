@@ -24,12 +24,19 @@ constexpr int HOP_BLOCK = 128;
 
 // Launch shapes of the FP32 / FP16 hop that the autotuner chooses among:
 // X(index, threads per block, sites per thread, minimum resident blocks per SM;
-// 0 leaves the register count to the compiler). Measured on GB300 at 24^3 x 48:
-// one site per thread is fastest for the plain FP16 / 12-real hop (27 us
-// against 31-33 us for two sites per thread, whose packed FP32x2 arithmetic
-// needs 32 % fewer instructions but 168-222 registers), so it is the default.
-#define LQCD_HOP_SHAPES(X) X(0, 128, 1, 0) X(1, 128, 1, 7) X(2, 256, 1, 0) X(3, 128, 1, 5) X(4, 128, 2, 3)
-constexpr int HOP_SHAPES = 5;
+// 0 leaves the register count to the compiler). Measured on GB300 at 24^3 x 48
+// (warm, back to back): the plain FP16 / 12-real hop takes 26.6-27.1 us with one
+// site per thread, 26.8 us spin-paired (21 % fewer instructions, the FMA pipe
+// as busy), 30 us with two sites per thread (32 % fewer instructions, 168-222
+// registers); the FP32 / 12-real hop is fastest spin-paired. Shape 0 is the
+// default; the tuner times all of them per key.
+// Sites per thread -1: one site per thread with the links of each 4D site staged
+// in shared memory once for its n5 threads (L_s-replicated and multi-RHS hops,
+// n5 >= 4; otherwise as shape 0). -2: one site per thread with the two spin
+// components of each half spinor paired in packed FP32x2 instructions.
+#define LQCD_HOP_SHAPES(X) X(0, 128, 1, 0) X(1, 128, 1, 7) X(2, 128, -2, 7) X(3, 128, 1, 5) X(4, 128, 2, 3) \
+  X(5, 128, -1, 6) X(6, 128, -2, 0)
+constexpr int HOP_SHAPES = 7;
 // The shape used when the table holds no choice for a hop.
 constexpr int HOP_SHAPE_DEFAULT = 0;
 
@@ -44,8 +51,10 @@ bool hop_shape_lookup(const HopKey& k, int* idx);
 // Whether an untuned hop launch on stream s may be timed now: autotuning is
 // on (lqcd_tune_set_enabled) and s is not capturing a graph.
 bool hop_autotune_ready(cudaStream_t s);
-// Launches launch(i) for every shape i (one warm-up, three timed launches
-// each, back to back on s), stores the fastest under k and returns it in *best.
+// Times launch(i) for every shape i on s (a warm-up each, then three interleaved
+// rounds of two back-to-back launches; a shape's time is its fastest round),
+// stores the fastest under k -- the default unless another shape is at least
+// 3 % faster -- and returns it in *best.
 int tune_hop_shapes(const HopKey& k, const std::function<int(int)>& launch, cudaStream_t s, int* best);
 // A hop launch is timed in place only if running it again cannot change what
 // it leaves behind: no reduction, no gate, out not aliasing in or x. Inside a

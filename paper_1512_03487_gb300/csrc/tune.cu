@@ -136,38 +136,50 @@ bool hop_autotune_ready(cudaStream_t s) {
 }
 
 int tune_hop_shapes(const HopKey& k, const std::function<int(int)>& launch, cudaStream_t s, int* best) {
+  // Every shape is launched once to warm up, then timed in ROUNDS interleaved
+  // rounds of PAIR back-to-back launches; a shape's time is its fastest round.
+  // The default shape is kept unless another one is faster by at least MARGIN:
+  // differences of a few per cent between shapes are within the spread of such
+  // timings and would make the choice change from run to run.
+  constexpr int ROUNDS = 3, PAIR = 2;
+  constexpr float MARGIN = 0.97f;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "hop autotune: event create");
   if (cudaEventCreate(&e1) != cudaSuccess) {
     cudaEventDestroy(e0);
     return cuda_fail(cudaGetLastError(), "hop autotune: event create");
   }
-  constexpr int REPS = 3;
-  float best_ms = 0.f;
-  *best = HOP_SHAPE_DEFAULT;
+  float t[HOP_SHAPES];
   int st = LQCD_OK;
   for (int i = 0; i < HOP_SHAPES && st == LQCD_OK; i++) {
-    if ((st = launch(i))) break;  // warm-up (first use of the instantiation, caches)
-    cudaEventRecord(e0, s);
-    for (int r = 0; r < REPS && st == LQCD_OK; r++) st = launch(i);
-    cudaEventRecord(e1, s);
-    if (st) break;
-    cudaError_t e = cudaEventSynchronize(e1);
-    float ms = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e != cudaSuccess) {
-      st = cuda_fail(e, "hop autotune: timing");
-      break;
-    }
-    if (i == 0 || ms < best_ms) {
-      best_ms = ms;
-      *best = i;
+    t[i] = 3.0e38f;
+    st = launch(i);
+  }
+  for (int r = 0; r < ROUNDS && st == LQCD_OK; r++) {
+    for (int i = 0; i < HOP_SHAPES && st == LQCD_OK; i++) {
+      cudaEventRecord(e0, s);
+      for (int q = 0; q < PAIR && st == LQCD_OK; q++) st = launch(i);
+      cudaEventRecord(e1, s);
+      if (st) break;
+      cudaError_t e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        st = cuda_fail(e, "hop autotune: timing");
+        break;
+      }
+      if (ms < t[i]) t[i] = ms;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (st == LQCD_OK) tune_store(hop_key_string(k), *best);
-  return st;
+  if (st) return st;
+  int b = HOP_SHAPE_DEFAULT;
+  for (int i = 0; i < HOP_SHAPES; i++)
+    if (t[i] < MARGIN * t[HOP_SHAPE_DEFAULT] && t[i] < t[b]) b = i;
+  *best = b;
+  tune_store(hop_key_string(k), b);
+  return LQCD_OK;
 }
 
 }  // namespace lqcd

@@ -1,8 +1,10 @@
 """GPU tests of the launch-shape autotuner of the FP32 / FP16 hop.
 
 Every shape computes the hop's arithmetic in the same order (one site per
-thread with 64, 128 or 256 threads per block, or two sites per thread in
-packed FP32x2 instructions), so a table that forces a shape must change
+thread with 128 or 256 threads per block and register caps, one site per
+thread with the links of each 4D site staged in shared memory, one site per
+thread with its two spin components paired in packed FP32x2 instructions, or
+two sites per thread in packed FP32x2 instructions), so a table that forces a shape must change
 nothing in a hop's result: hops agree exactly across shapes and with the FP64
 oracle within the storage precision's tolerance. Only the grouping of the
 block partial sums of the solver's reductions depends on the block size (an
@@ -25,7 +27,7 @@ torch = pytest.importorskip("torch")
 
 TOL = {1: 1e-5, 2: 3e-3}
 BC = (1.0, 1.0, 1.0, -1.0)
-NSHAPES = 5
+NSHAPES = 7
 
 
 @pytest.fixture(scope="module")
@@ -55,10 +57,12 @@ def _force(L, tmp_path, dims, n5, shape):
 
 @pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("recon", [12, 18])
-@pytest.mark.parametrize("n5", [1, 4])
+@pytest.mark.parametrize("n5", [1, 4, 12])
 def test_every_shape_gives_identical_hops(L, tmp_path, prec, recon, n5):
     """Ragged lattice (Vh = 90 per 4D checkerboard: several blocks and a partial
-    one for every shape), both daggers, single checkerboard and full field."""
+    one for every shape), both daggers, single checkerboard and full field; with
+    n5 = 4 and 12 the link-staging shape shares each 4D site's links across its
+    n5 threads, 4D sites straddling block boundaries for n5 = 12."""
     dims = (6, 2, 6, 10)
     U = gauge_field(dims, "haar", 21)
     psi = gaussian_spinor(dims, 22, lead=(n5,))
