@@ -542,6 +542,21 @@ def _run_lqcd(args, world, rank, local, L, F, dev, stream):
         print(json.dumps(line), flush=True)
 
 
+def packed_full_residual(L, F, lat, op64, g64, x, bd):
+    """||b - M x|| / ||b|| for x and b both in the FP64 device layout (full lattice):
+    M x with the FP64 operator, both unpacked to the host layout, whose size is
+    2 x the complex entries of host_spinor_shape (padding sites never enter)."""
+    import torch
+    dx = F.empty(L.lqcd_spinor_bytes(lat, 0, L.LQCD_FULL))
+    L.lqcd_M(dx, x, g64, lat, op64, L.LQCD_FULL, 0, None)
+    n = 2 * int(np.prod(F.host_spinor_shape(lat, L.LQCD_FULL)))
+    a = torch.empty(n, dtype=torch.float64, device="cuda")
+    bb = torch.empty(n, dtype=torch.float64, device="cuda")
+    L.lqcd_spinor_unpack(a, dx, L.LQCD_F64, L.LQCD_FULL, lat)
+    L.lqcd_spinor_unpack(bb, bd, L.LQCD_F64, L.LQCD_FULL, lat)
+    return float(torch.linalg.vector_norm(a - bb) / torch.linalg.vector_norm(bb))
+
+
 def full_residual(L, F, lat, op64, g64, x, b_dev, tmp):
     """||b - D_W x|| / ||b|| of the step's result, computed with the FP64 operator
     and compared in the host layout (padding sites never enter)."""
@@ -864,7 +879,9 @@ def run_extras(L, F, flush, stream):
     prm = L.solver_params(tol=1e-10, maxiter=5000, sloppy_prec=1, sloppy_recon=12, delta=DELTA_NORMAL_FP32,
                           check_interval=64)
     wsb = F.empty(L.lqcd_batch_cg_workspace_bytes(len(entries), items, 18, prm))
-    L.lqcd_batch_cg_solve(len(entries), items, 18, prm, wsb)  # tunes the grid, captures the graph
+    L.lqcd_batch_cg_solve(len(entries), items, 18, prm, wsb)  # tunes the tile and grid, captures the graph
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    bkey = f"sms={sms} prec=1 recon=12 : " + " ".join("x".join(map(str, d)) for d in shapes)
     ms_b, infos = _events_time(lambda: L.lqcd_batch_cg_solve(len(entries), items, 18, prm, wsb), stream, flush)
     op = L.operator(mass=0.05)
     wss = [F.empty(L.lqcd_cg_workspace_bytes(e["lat"], op, prm, 0)) for e in entries]
@@ -882,7 +899,9 @@ def run_extras(L, F, flush, stream):
         "speedup": round(ms_s / ms_b, 2), "iterations": infos[0].iterations,
         "reliable_updates": infos[0].reliable_updates,
         "max_true_rel_residual_normal_eq": max(i.true_rel_residual for i in infos),
-        "tuned_shapes": L.lqcd_tune_entries()}
+        "tuned_tile_sites": [64, 128, 256][L.lqcd_tune_get("batch_tile " + bkey)],
+        "tuned_blocks_per_sm": L.lqcd_tune_get("batch_hop " + bkey),
+        "tune_table_entries": L.lqcd_tune_entries()}
     del entries, items, wsb, wss
     torch.cuda.empty_cache()
 
@@ -969,18 +988,11 @@ def dwf_bench(L, F, flush, stream, use_graph=1, check_interval=64, three_level=T
         del ws64
     dwf_solve()
     ms, info = _events_time(dwf_solve, stream, flush)
-    dx = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
-    L.lqcd_M(dx, x, g64, lat, op, L.LQCD_FULL, 0, None)
-    n = 2 * 16 ** 4 * Ls * 24
-    a = torch.empty(n, dtype=torch.float64, device="cuda")
-    bb = torch.empty(n, dtype=torch.float64, device="cuda")
-    L.lqcd_spinor_unpack(a, dx, 0, 2, lat)
-    L.lqcd_spinor_unpack(bb, bd, 0, 2, lat)
-    res = float(torch.linalg.vector_norm(a - bb) / torch.linalg.vector_norm(bb))
+    res = packed_full_residual(L, F, lat, op, g64, x, bd)
     hops = 1 + 2 + 4 * (info.iterations + info.reliable_updates) + 1
     return {
         "ms": round(ms, 3), "iterations": info.iterations, "reliable_updates": info.reliable_updates,
-        "full_system_rel_residual": res,
+        "full_system_rel_residual": res, "reported_rel_residual_full_system": info.true_rel_residual,
         "dslash_gflops_in_solve": round(hops * FLOP_PER_SITE * 16 ** 4 // 2 * Ls / (ms * 1e-3) / 1e9, 1),
         "hop_f32r12_ls16": _hop_gbs(L, F, lat, 1, 12, 8 * 48 / Ls + 96 + 96, flush, stream, kind=L.LQCD_DWF),
         "fp16_inner_three_level": {"ms": round(ms3, 3), "iterations": info3.iterations,
@@ -1071,14 +1083,7 @@ def gparity_bench(L, F, flush, stream):
 
     solve()
     ms, info = _events_time(solve, stream, flush)
-    dx = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
-    L.lqcd_M(dx, x, g64, lat, op, L.LQCD_FULL, 0, None)
-    n = 2 * int(np.prod(dims)) * 24
-    a = torch.empty(n, dtype=torch.float64, device="cuda")
-    bb = torch.empty(n, dtype=torch.float64, device="cuda")
-    L.lqcd_spinor_unpack(a, dx, 0, 2, lat)
-    L.lqcd_spinor_unpack(bb, bd, 0, 2, lat)
-    res = float(torch.linalg.vector_norm(a - bb) / torch.linalg.vector_norm(bb))
+    res = packed_full_residual(L, F, lat, op, g64, x, bd)
     vh = int(np.prod(dims)) // 2
     hops = 1 + 2 + 4 * (info.iterations + info.reliable_updates)  # the odd half reuses the last update's hop
     opg = L.operator(prec=1, recon=12, gparity=mask)

@@ -368,8 +368,9 @@ typedef struct {
  * instances at once with the CG of lqcd_cg_solve (FP64 or mixed precision,
  * per-instance alpha, beta, reliable updates and convergence). Every phase of
  * an iteration is one persistent launch over a work list of (instance, tile)
- * pairs; the number of resident blocks per SM is chosen by timing candidates
- * on the first solve of each batch shape (see lqcd_tune_save). infos: n
+ * pairs; the tile size (64, 128 or 256 sites) and the number of resident
+ * blocks per SM are chosen together by timing candidates on the first solve
+ * of each batch shape (see lqcd_tune_save). infos: n
  * entries (iterations and reliable updates are shared, true residuals are per
  * instance). Synchronises the stream. workspace: lqcd_batch_cg_workspace_bytes()
  * bytes, 256-byte aligned. */
@@ -382,8 +383,10 @@ int lqcd_batch_cg_solve(int n, const lqcd_batch_item* items, int recon, const lq
  * Sec. 2.4 "Nsimd"; here launch parameters are timed on the GPU at run time).
  * Its table maps a text key to the integer choice made for it:
  *  - "batch_hop sms=... prec=... recon=... : <dims of every instance>" ->
- *    resident blocks per SM of the persistent batch launch (timed on the
- *    first lqcd_batch_cg_solve of each batch shape);
+ *    resident blocks per SM of the persistent batch launch, and "batch_tile"
+ *    with the same tail -> its tile size (0: 64, 1: 128, 2: 256 sites and
+ *    threads per block), timed together on the first lqcd_batch_cg_solve of
+ *    each batch shape;
  *  - "hop prec=P recon=R dagger=D epi=E red=Q full=F lat=XxYxZxT n5=N" ->
  *    launch-shape index of an FP32 / FP16 hop kernel (one site per thread
  *    with 0: 128 threads per block, registers as the compiler chooses; 1: 128

@@ -3,15 +3,16 @@
 // All instances advance in lockstep, each with its own alpha, beta,
 // reliable-update and convergence state (one SysState per instance). Every
 // phase of an iteration is ONE persistent launch over a work list of tiles
-// (instance, 128 consecutive sites): a fixed grid of resident blocks strides
+// (instance, TILE consecutive sites): a fixed grid of resident blocks strides
 // through the list, finds each tile's instance from a prefix table held in
 // shared memory, and runs the same per-site code as the single-lattice
 // kernels (hop_site, cg_site.cuh). Reductions accumulate per instance in
 // shared memory, write one partial per (instance, block), and the last block
-// to finish sums them per instance in a fixed order. The grid size (resident
-// blocks per SM) is chosen by timing candidates on the first solve of a given
-// batch shape (the autotuner); the choice is cached per shape and can be saved
-// and loaded. The iteration loop is the shared conditional-graph driver.
+// to finish sums them per instance in a fixed order. The tile (64, 128 or 256
+// sites, one thread per site) and the grid size (resident blocks per SM) are
+// chosen together by timing candidates on the first solve of a given batch
+// shape (the autotuner); the choice is cached per shape and can be saved and
+// loaded. The iteration loop is the shared conditional-graph driver.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -26,7 +27,10 @@
 
 namespace lqcd {
 
-constexpr int TILE = 128;  // sites per tile == threads per block
+// Tile sizes the tuner chooses among (sites per tile == threads per block).
+constexpr int NTILES = 3;
+constexpr int TILES[NTILES] = {64, 128, 256};
+template <int TILE> constexpr int tile_slot() { return TILE == 64 ? 0 : TILE == 128 ? 1 : 2; }
 constexpr int MAX_BATCH = MAX_SYS;
 
 // field selectors of a batch instance
@@ -39,7 +43,7 @@ struct BInst {
   double c;  // 4 + m
   double b;  // -1 / (4 c), the Schur hop's coefficient
   void* f[12];
-  int64_t tile0;
+  int64_t tile0[NTILES];  // first tile of this instance in the work list, per tile size
 };
 
 struct BatchArgs {
@@ -64,6 +68,7 @@ __device__ __forceinline__ int find_inst(const int64_t* t0, int n, int64_t t) {
 }
 
 // Sum of v over the block, added by thread 0 to acc (all threads call it).
+template <int TILE>
 __device__ __forceinline__ void block_add(double v, double* sh, double* acc) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -79,7 +84,7 @@ __device__ __forceinline__ void block_add(double v, double* sh, double* acc) {
 
 // RED: RED_NONE, RED_NORM (|out|^2 per instance) or RED_CG_UPDATE (out = A p is
 // not stored; x_s += alpha p, r_s -= alpha A p and |r_s|^2 per instance instead).
-template <int P, int R, bool DAG, int EPI, int RED>
+template <int P, int R, bool DAG, int EPI, int RED, int TILE>
 __global__ void __launch_bounds__(TILE) batch_hop_kernel(const BatchArgs A) {
   using T = typename PrecTraits<P>::real;
   if (gate_closed(A.gate)) return;
@@ -87,7 +92,7 @@ __global__ void __launch_bounds__(TILE) batch_hop_kernel(const BatchArgs A) {
   __shared__ double s_acc[MAX_BATCH];
   __shared__ double sh[TILE];
   for (int i = threadIdx.x; i < A.ninst; i += TILE) {
-    s_t0[i] = A.inst[i].tile0;
+    s_t0[i] = A.inst[i].tile0[tile_slot<TILE>()];
     s_acc[i] = 0.0;
   }
   __syncthreads();
@@ -112,7 +117,7 @@ __global__ void __launch_bounds__(TILE) batch_hop_kernel(const BatchArgs A) {
         if (RED == RED_NORM) v = norm2_site(res);
       }
     }
-    if (RED) block_add(v, sh, &s_acc[k]);
+    if (RED) block_add<TILE>(v, sh, &s_acc[k]);
   }
   if (RED) {
     for (int i = threadIdx.x; i < A.ninst; i += TILE) A.red.partials[(int64_t)i * gridDim.x + blockIdx.x] = s_acc[i];
@@ -122,7 +127,7 @@ __global__ void __launch_bounds__(TILE) batch_hop_kernel(const BatchArgs A) {
 
 enum BatchVec { BV_INIT, BV_UPDATE, BV_PUPDATE, BV_ACCUM, BV_RESIDUAL };
 
-template <int VF, int SF, int KIND>
+template <int VF, int SF, int KIND, int TILE>
 __global__ void __launch_bounds__(TILE) batch_vec_kernel(const BatchArgs A) {
   constexpr bool RED = KIND == BV_INIT || KIND == BV_UPDATE || KIND == BV_RESIDUAL;
   constexpr bool GATED = KIND == BV_UPDATE || KIND == BV_PUPDATE;
@@ -131,7 +136,7 @@ __global__ void __launch_bounds__(TILE) batch_vec_kernel(const BatchArgs A) {
   __shared__ double s_acc[MAX_BATCH];
   __shared__ double sh[TILE];
   for (int i = threadIdx.x; i < A.ninst; i += TILE) {
-    s_t0[i] = A.inst[i].tile0;
+    s_t0[i] = A.inst[i].tile0[tile_slot<TILE>()];
     s_acc[i] = 0.0;
   }
   __syncthreads();
@@ -155,7 +160,7 @@ __global__ void __launch_bounds__(TILE) batch_vec_kernel(const BatchArgs A) {
         v = residual_site<VF>(I.g, j, (const double*)f[BF_B64], (const double*)f[BF_AX64], (double*)f[BF_R64],
                               f[BF_RS]);
     }
-    if (RED) block_add(v, sh, &s_acc[k]);
+    if (RED) block_add<TILE>(v, sh, &s_acc[k]);
   }
   if (RED) {
     for (int i = threadIdx.x; i < A.ninst; i += TILE) A.red.partials[(int64_t)i * gridDim.x + blockIdx.x] = s_acc[i];
@@ -165,9 +170,9 @@ __global__ void __launch_bounds__(TILE) batch_vec_kernel(const BatchArgs A) {
 
 // ------------------------------------------------------------------ launchers
 
-template <int P, int R>
+template <int P, int R, int TILE>
 static void launch_bhop_pr(bool dag, int epi, int red, unsigned grid, const BatchArgs& a, cudaStream_t s) {
-#define LQCD_BHOP(DG, EP, RD) batch_hop_kernel<P, R, DG, EP, RD><<<grid, TILE, 0, s>>>(a)
+#define LQCD_BHOP(DG, EP, RD) batch_hop_kernel<P, R, DG, EP, RD, TILE><<<grid, TILE, 0, s>>>(a)
   if (epi == EPI_PLAIN) {
     if (dag) LQCD_BHOP(true, EPI_PLAIN, RED_NONE);
     else LQCD_BHOP(false, EPI_PLAIN, RED_NONE);
@@ -183,36 +188,52 @@ static void launch_bhop_pr(bool dag, int epi, int red, unsigned grid, const Batc
 #undef LQCD_BHOP
 }
 
-static int launch_bhop(int prec, int recon, bool dag, int epi, int red, unsigned grid, const BatchArgs& a,
-                       cudaStream_t s) {
+template <int TILE>
+static void launch_bhop_t(int prec, int recon, bool dag, int epi, int red, unsigned grid, const BatchArgs& a,
+                          cudaStream_t s) {
   if (prec == LQCD_F64) {
-    if (recon == 18) launch_bhop_pr<LQCD_F64, 18>(dag, epi, red, grid, a, s);
-    else launch_bhop_pr<LQCD_F64, 12>(dag, epi, red, grid, a, s);
+    if (recon == 18) launch_bhop_pr<LQCD_F64, 18, TILE>(dag, epi, red, grid, a, s);
+    else launch_bhop_pr<LQCD_F64, 12, TILE>(dag, epi, red, grid, a, s);
   } else if (prec == LQCD_F32) {
-    if (recon == 18) launch_bhop_pr<LQCD_F32, 18>(dag, epi, red, grid, a, s);
-    else launch_bhop_pr<LQCD_F32, 12>(dag, epi, red, grid, a, s);
+    if (recon == 18) launch_bhop_pr<LQCD_F32, 18, TILE>(dag, epi, red, grid, a, s);
+    else launch_bhop_pr<LQCD_F32, 12, TILE>(dag, epi, red, grid, a, s);
   } else {
-    if (recon == 18) launch_bhop_pr<LQCD_F16, 18>(dag, epi, red, grid, a, s);
-    else launch_bhop_pr<LQCD_F16, 12>(dag, epi, red, grid, a, s);
+    if (recon == 18) launch_bhop_pr<LQCD_F16, 18, TILE>(dag, epi, red, grid, a, s);
+    else launch_bhop_pr<LQCD_F16, 12, TILE>(dag, epi, red, grid, a, s);
   }
+}
+
+// tile: index into TILES; a.total_tiles is that tile size's count
+static int launch_bhop(int tile, int prec, int recon, bool dag, int epi, int red, unsigned grid, const BatchArgs& a,
+                       cudaStream_t s) {
+  if (tile == 0) launch_bhop_t<64>(prec, recon, dag, epi, red, grid, a, s);
+  else if (tile == 1) launch_bhop_t<128>(prec, recon, dag, epi, red, grid, a, s);
+  else launch_bhop_t<256>(prec, recon, dag, epi, red, grid, a, s);
   return after_launch("batch_hop_kernel");
 }
 
-template <int VF, int SF>
-static void launch_bvec_t(int kind, unsigned grid, const BatchArgs& a, cudaStream_t s) {
+template <int VF, int SF, int TILE>
+static void launch_bvec_tt(int kind, unsigned grid, const BatchArgs& a, cudaStream_t s) {
   switch (kind) {
-    case BV_INIT: batch_vec_kernel<VF, SF, BV_INIT><<<grid, TILE, 0, s>>>(a); break;
-    case BV_UPDATE: batch_vec_kernel<VF, SF, BV_UPDATE><<<grid, TILE, 0, s>>>(a); break;
-    case BV_PUPDATE: batch_vec_kernel<VF, SF, BV_PUPDATE><<<grid, TILE, 0, s>>>(a); break;
-    case BV_ACCUM: batch_vec_kernel<VF, SF, BV_ACCUM><<<grid, TILE, 0, s>>>(a); break;
-    case BV_RESIDUAL: batch_vec_kernel<VF, SF, BV_RESIDUAL><<<grid, TILE, 0, s>>>(a); break;
+    case BV_INIT: batch_vec_kernel<VF, SF, BV_INIT, TILE><<<grid, TILE, 0, s>>>(a); break;
+    case BV_UPDATE: batch_vec_kernel<VF, SF, BV_UPDATE, TILE><<<grid, TILE, 0, s>>>(a); break;
+    case BV_PUPDATE: batch_vec_kernel<VF, SF, BV_PUPDATE, TILE><<<grid, TILE, 0, s>>>(a); break;
+    case BV_ACCUM: batch_vec_kernel<VF, SF, BV_ACCUM, TILE><<<grid, TILE, 0, s>>>(a); break;
+    case BV_RESIDUAL: batch_vec_kernel<VF, SF, BV_RESIDUAL, TILE><<<grid, TILE, 0, s>>>(a); break;
   }
 }
 
-static int launch_bvec(int kind, int sloppy, unsigned grid, const BatchArgs& a, cudaStream_t s) {
-  if (sloppy == LQCD_F64) launch_bvec_t<LQCD_F64, LQCD_F64>(kind, grid, a, s);
-  else if (sloppy == LQCD_F32) launch_bvec_t<LQCD_F32, LQCD_F32>(kind, grid, a, s);
-  else launch_bvec_t<LQCD_F32, LQCD_F16>(kind, grid, a, s);
+template <int VF, int SF>
+static void launch_bvec_t(int tile, int kind, unsigned grid, const BatchArgs& a, cudaStream_t s) {
+  if (tile == 0) launch_bvec_tt<VF, SF, 64>(kind, grid, a, s);
+  else if (tile == 1) launch_bvec_tt<VF, SF, 128>(kind, grid, a, s);
+  else launch_bvec_tt<VF, SF, 256>(kind, grid, a, s);
+}
+
+static int launch_bvec(int tile, int kind, int sloppy, unsigned grid, const BatchArgs& a, cudaStream_t s) {
+  if (sloppy == LQCD_F64) launch_bvec_t<LQCD_F64, LQCD_F64>(tile, kind, grid, a, s);
+  else if (sloppy == LQCD_F32) launch_bvec_t<LQCD_F32, LQCD_F32>(tile, kind, grid, a, s);
+  else launch_bvec_t<LQCD_F32, LQCD_F16>(tile, kind, grid, a, s);
   return after_launch("batch_vec_kernel");
 }
 
@@ -292,10 +313,17 @@ struct BatchSolver : CgEngine {
   int n;
   int sloppy, sloppy_recon, recon;
   unsigned grid;
-  int64_t total_tiles;
+  int tile;                         // index into TILES
+  int64_t total_tiles;              // of the chosen tile size
+  int64_t tiles_by_size[NTILES];    // work-list length per tile size
   BatchArgs base;
   ReduceCtx rc_init, rc_alpha, rc_update, rc_reliable;
 
+  void set_tile(int t) {
+    tile = t;
+    total_tiles = tiles_by_size[t];
+    base.total_tiles = total_tiles;
+  }
   BatchArgs args(int f_out, int f_in, int f_x, int use64, int parity, const Control* gate) const {
     BatchArgs a = base;
     a.f_out = f_out;
@@ -313,18 +341,18 @@ struct BatchSolver : CgEngine {
     const int P = use64 ? LQCD_F64 : sloppy;
     const int R = use64 ? recon : sloppy_recon;
     BatchArgs a1 = args(f_tmp, f_in, BF_NONE, use64, LQCD_ODD, gate);
-    int st = launch_bhop(P, R, dag, EPI_PLAIN, RED_NONE, grid, a1, s);
+    int st = launch_bhop(tile, P, R, dag, EPI_PLAIN, RED_NONE, grid, a1, s);
     if (st) return st;
     BatchArgs a2 = args(f_out, f_tmp, f_in, use64, LQCD_EVEN, gate);
     if (red) a2.red = *red;
-    return launch_bhop(P, R, dag, EPI_XPAY, red ? red_mode : RED_NONE, grid, a2, s);
+    return launch_bhop(tile, P, R, dag, EPI_XPAY, red ? red_mode : RED_NONE, grid, a2, s);
   }
   int init(cudaStream_t s) override {
     cudaError_t e = cudaMemsetAsync(base.red.counter, 0, 64, s);
     if (e != cudaSuccess) return cuda_fail(e, "batch: memset");
     BatchArgs a = base;
     a.red = rc_init;
-    return launch_bvec(BV_INIT, sloppy, grid, a, s);
+    return launch_bvec(tile, BV_INIT, sloppy, grid, a, s);
   }
   // M_hat p with |M_hat p|^2 = p^dag A p -> alpha; M_hat^dag (M_hat p) = A p whose last
   // hop applies x_s += alpha p, r_s -= alpha A p and reduces |r_s|^2 instead of storing A p
@@ -339,16 +367,16 @@ struct BatchSolver : CgEngine {
   int tail(cudaStream_t s) override {
     BatchArgs a = base;
     a.gate = ctrl;
-    return launch_bvec(BV_PUPDATE, sloppy, grid, a, s);
+    return launch_bvec(tile, BV_PUPDATE, sloppy, grid, a, s);
   }
   int reliable(cudaStream_t s) override {
     BatchArgs a = base;
-    int st = launch_bvec(BV_ACCUM, sloppy, grid, a, s);
+    int st = launch_bvec(tile, BV_ACCUM, sloppy, grid, a, s);
     if (st) return st;
     if ((st = schur(BF_MID64, BF_X64, BF_T1_64, false, true, nullptr, nullptr, s))) return st;
     if ((st = schur(BF_AX64, BF_MID64, BF_T1_64, true, true, nullptr, nullptr, s))) return st;
     a.red = rc_reliable;
-    return launch_bvec(BV_RESIDUAL, sloppy, grid, a, s);
+    return launch_bvec(tile, BV_RESIDUAL, sloppy, grid, a, s);
   }
 };
 
@@ -360,37 +388,43 @@ static int sm_count(int* sms) {
   return LQCD_OK;
 }
 
-// Time the sloppy plain hop phase for several resident-block counts and keep the fastest.
-static int autotune_grid(BatchSolver& S, int sms, int* best_bps, cudaStream_t s) {
+// Time the sloppy plain hop phase for every tile size and several resident-block
+// counts and keep the fastest pair (tile index into TILES, blocks per SM).
+static int autotune_batch(BatchSolver& S, int sms, int* best_tile, int* best_bps, cudaStream_t s) {
   const int candidates[] = {1, 2, 4, 6, 8, 12, 16};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return fail(LQCD_ERR_CUDA, "batch autotune: event create");
   float best = 1e30f;
+  *best_tile = 1;
   *best_bps = 4;
   int st = LQCD_OK;
-  for (int bps : candidates) {
-    int64_t g = (int64_t)bps * sms;
-    if (g > S.total_tiles) g = S.total_tiles;
-    if (g > MAX_GRID) g = MAX_GRID;
-    const unsigned grid = (unsigned)g;
-    BatchArgs a = S.args(BF_T1S, BF_P, BF_NONE, 0, LQCD_ODD, nullptr);
-    float ms_total = 0.f;
-    for (int rep = 0; rep < 4 && st == LQCD_OK; rep++) {
-      cudaEventRecord(e0, s);
-      st = launch_bhop(S.sloppy, S.sloppy_recon, false, EPI_PLAIN, false, grid, a, s);
-      cudaEventRecord(e1, s);
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (rep > 0) ms_total += ms;  // first launch warms up
+  for (int tile = 0; tile < NTILES && st == LQCD_OK; tile++) {
+    S.set_tile(tile);
+    for (int bps : candidates) {
+      int64_t g = (int64_t)bps * sms;
+      if (g > S.total_tiles) g = S.total_tiles;
+      if (g > MAX_GRID) g = MAX_GRID;
+      const unsigned grid = (unsigned)g;
+      BatchArgs a = S.args(BF_T1S, BF_P, BF_NONE, 0, LQCD_ODD, nullptr);
+      float ms_total = 0.f;
+      for (int rep = 0; rep < 4 && st == LQCD_OK; rep++) {
+        cudaEventRecord(e0, s);
+        st = launch_bhop(tile, S.sloppy, S.sloppy_recon, false, EPI_PLAIN, RED_NONE, grid, a, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) ms_total += ms;  // first launch warms up
+      }
+      if (st) break;
+      if (ms_total < best) {
+        best = ms_total;
+        *best_tile = tile;
+        *best_bps = bps;
+      }
+      if (g == S.total_tiles) break;  // larger grids cannot differ
     }
-    if (st) break;
-    if (ms_total < best) {
-      best = ms_total;
-      *best_bps = bps;
-    }
-    if (g == S.total_tiles) break;  // larger grids cannot differ
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -448,7 +482,7 @@ int lqcd_batch_cg_solve(int n, const lqcd_batch_item* items, int recon, const lq
   // descriptors
   const int VF = prm->sloppy_prec == LQCD_F64 ? LQCD_F64 : LQCD_F32;
   BInst host[MAX_BATCH];
-  int64_t tiles = 0;
+  int64_t tiles_by[NTILES] = {0, 0, 0};
   for (int i = 0; i < n; i++) {
     const Geom& g = geoms[i];
     BInst& I = host[i];
@@ -458,8 +492,10 @@ int lqcd_batch_cg_solve(int n, const lqcd_batch_item* items, int recon, const lq
     I.gauge_s = (prm->sloppy_prec == LQCD_F64 || !items[i].gauge_sloppy) ? items[i].gauge : items[i].gauge_sloppy;
     I.c = 4.0 + items[i].mass;
     I.b = -1.0 / (4.0 * I.c);
-    I.tile0 = tiles;
-    tiles += (g.nsites + TILE - 1) / TILE;
+    for (int t = 0; t < NTILES; t++) {
+      I.tile0[t] = tiles_by[t];
+      tiles_by[t] += (g.nsites + TILES[t] - 1) / TILES[t];
+    }
     char* f = base + lay.fields_offset[i];
     size_t o = 0;
     auto take = [&](size_t bytes) -> void* {
@@ -492,11 +528,11 @@ int lqcd_batch_cg_solve(int n, const lqcd_batch_item* items, int recon, const lq
   // the FP64 inner operator runs on the FP64 fields themselves, in their format
   S.sloppy_recon = prm->sloppy_prec == LQCD_F64 ? recon : prm->sloppy_recon;
   S.recon = recon;
-  S.total_tiles = tiles;
   memset(&S.base, 0, sizeof(S.base));
   S.base.inst = lay.inst;
   S.base.ninst = n;
-  S.base.total_tiles = tiles;
+  for (int t = 0; t < NTILES; t++) S.tiles_by_size[t] = tiles_by[t];
+  S.set_tile(1);
   ReduceCtx rc;
   memset(&rc, 0, sizeof(rc));
   rc.partials = lay.partials;
@@ -517,19 +553,22 @@ int lqcd_batch_cg_solve(int n, const lqcd_batch_item* items, int recon, const lq
   S.rc_reliable = rc;
   S.rc_reliable.fin = FIN_RELIABLE;
 
-  // persistent grid: autotuned resident blocks per SM for this batch shape
+  // persistent grid: autotuned tile size and resident blocks per SM for this batch shape
   int sms = 0;
   if ((st = sm_count(&sms))) return finish(st, 0, 0);
   const std::string skey = shape_key(n, geoms, S.sloppy, S.sloppy_recon, sms);
-  int bps = 0;
-  if (!tune_lookup(skey, &bps) || bps <= 0) {
+  const std::string tkey = "batch_tile " + skey.substr(10);  // "batch_hop " -> "batch_tile "
+  int bps = 0, tile = 1;
+  if (!tune_lookup(skey, &bps) || bps <= 0 || !tune_lookup(tkey, &tile) || tile < 0 || tile >= NTILES) {
     bps = 0;
-    S.grid = (unsigned)std::min<int64_t>(std::min<int64_t>((int64_t)4 * sms, tiles), MAX_GRID);
+    S.grid = (unsigned)std::min<int64_t>(std::min<int64_t>((int64_t)4 * sms, S.total_tiles), MAX_GRID);
     if ((st = S.init(s))) return finish(st, 0, 0);  // gives p a defined value to time the hop on
-    if ((st = autotune_grid(S, sms, &bps, s))) return finish(st, 0, 0);
+    if ((st = autotune_batch(S, sms, &tile, &bps, s))) return finish(st, 0, 0);
     tune_store(skey, bps);
+    tune_store(tkey, tile);
   }
-  S.grid = (unsigned)std::min<int64_t>(std::min<int64_t>((int64_t)bps * sms, tiles), MAX_GRID);
+  S.set_tile(tile);
+  S.grid = (unsigned)std::min<int64_t>(std::min<int64_t>((int64_t)bps * sms, S.total_tiles), MAX_GRID);
 
   std::vector<unsigned char> key;
   int dev = 0;
@@ -544,6 +583,7 @@ int lqcd_batch_cg_solve(int n, const lqcd_batch_item* items, int recon, const lq
   key_append(key, prm->check_interval);
   key_append(key, prm->maxiter);
   key_append(key, S.grid);
+  key_append(key, S.tile);
   for (int i = 0; i < n; i++) {
     key_append(key, geoms[i].X);
     key_append(key, geoms[i].Y);

@@ -95,3 +95,30 @@ def test_tune_table_roundtrip(L, tmp_path):
     L.lqcd_tune_load(path)
     assert L.lqcd_tune_entries() == n0
     assert os.path.getsize(path) > 0
+
+
+@pytest.mark.parametrize("tile", [0, 1, 2])
+def test_forced_tile_sizes(L, tmp_path, tile):
+    """A loaded table that sets the batch's tile size (64, 128 or 256 sites per
+    block, key "batch_tile ...") and its grid (key "batch_hop ...") changes the
+    launch; every instance still reaches the oracle-recomputed FP64 residual,
+    and the loaded entries are not re-timed."""
+    shapes = [(4, 4, 4, 4), (6, 6, 6, 6), (8, 4, 4, 8)]
+    masses = [0.05, 0.05, 0.1]
+    entries, keep = _setup(L, shapes, masses, 1, 12)
+    items = L.batch_items(entries)
+    prm = L.solver_params(tol=1e-10, maxiter=3000, sloppy_prec=1, sloppy_recon=12, delta=0.01, check_interval=32)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    tail = f"sms={sms} prec=1 recon=12 : " + " ".join("x".join(map(str, d)) for d in shapes)
+    path = tmp_path / "batch_tune.txt"
+    path.write_text(f"{tile}\tbatch_tile {tail}\n2\tbatch_hop {tail}\n")
+    L.lqcd_tune_load(str(path))
+    L.lqcd_release_caches()
+    ws = L.fields.empty(L.lqcd_batch_cg_workspace_bytes(len(entries), items, 18, prm))
+    infos = L.lqcd_batch_cg_solve(len(entries), items, 18, prm, ws)
+    assert L.lqcd_tune_get(f"batch_tile {tail}") == tile and L.lqcd_tune_get(f"batch_hop {tail}") == 2
+    for e, (U, b, lat, dims, m), info in zip(entries, keep, infos):
+        assert info.status == 0
+        x = L.fields.spinor_to_host(e["x"], lat, 0, 0)
+        res = ocg.true_residual(lambda v: wilson.schur_dag_schur(U, v, m, BC), from_cb(x, 0), from_cb(b, 0))
+        assert res <= 1e-10, (tile, dims, m, res)
