@@ -56,7 +56,7 @@ DELTA_NORMAL_FP32 = 1e-5
 PREC_TAG = {1: "f32", 2: "f16"}
 PROFILE_JSON = {q: os.path.join(ROOT, "profiles", f"hop_{PREC_TAG[q]}r12_24x24x24x48.json") for q in (1, 2)}
 DSLASH_COMMON = ["dslash_kernels.cuh", "lqcd_common.cuh", "cg_site.cuh", "dslash_launch.cuh", "hop_pair.cuh", "df.cuh",
-                 "lqcd_internal.h"]
+                 "hop_async.cuh", "lqcd_internal.h"]
 
 
 def parse_args():
@@ -568,8 +568,20 @@ def full_residual(L, F, lat, op64, g64, x, b_dev, tmp):
     return float(torch.linalg.vector_norm(a - b_dev) / torch.linalg.vector_norm(b_dev))
 
 
-def _cold_hop_seconds(L, F, lat, g, prec, recon, flush, stream, launches):
-    """Mean event-timed duration of one checkerboard hop launch, L2 flushed before each."""
+L2_BYTES = 129e6  # GB300 L2 (nvidia-smi / device properties: 126.5 MiB)
+
+
+def _cold_hop_seconds(L, F, lat, g, prec, recon, flush, stream, launches, rotate=True):
+    """Event-timed duration of one checkerboard hop launch with its inputs not in L2.
+
+    rotate=True: the launches run back to back, one event pair around all of
+    them, cycling through enough copies of the links and the input spinor that
+    the copy a launch reads was last touched more than 2 x L2 bytes of traffic
+    earlier (inputs larger than L2); the mean per launch carries no event or
+    launch latency. rotate=False: the L2 is flushed before every launch, each
+    launch timed alone with its own event pair (that adds the events' and the
+    launch's own latency, a few us, and the timer's resolution), mean over the
+    launches."""
     import torch
     op = L.operator(prec=prec, recon=recon)
     fprec = L.LQCD_F64 if prec == L.LQCD_F64_DF else prec  # double-float arithmetic on FP64 fields
@@ -580,6 +592,23 @@ def _cold_hop_seconds(L, F, lat, g, prec, recon, flush, stream, launches):
     out = F.empty(L.lqcd_spinor_bytes(lat, fprec, L.LQCD_EVEN))
     for _ in range(3):
         L.lqcd_dslash(out, fin, g, lat, op, L.LQCD_EVEN, 0)
+    if rotate:
+        per_copy = g.numel() * g.element_size() + fin.numel() * fin.element_size()
+        ncopy = max(2, int(np.ceil(2 * L2_BYTES / per_copy)) + 1)
+        gs, fins = [g] + [g.clone() for _ in range(ncopy - 1)], [fin] + [fin.clone() for _ in range(ncopy - 1)]
+        for k in range(ncopy):
+            L.lqcd_dslash(out, fins[k], gs[k], lat, op, L.LQCD_EVEN, 0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(launches):
+            L.lqcd_dslash(out, fins[i % ncopy], gs[i % ncopy], lat, op, L.LQCD_EVEN, 0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / launches
+        del gs, fins
+        return t * 1e-3
     times = []
     for _ in range(launches):
         # flush queued behind a synchronize, events and launch queued while it runs: e0 -> e1
@@ -596,8 +625,9 @@ def _cold_hop_seconds(L, F, lat, g, prec, recon, flush, stream, launches):
     return float(np.mean(times)) * 1e-3
 
 
-def hop_roofline(L, F, lat, gsl, prec, flush, stream, vh, launches=20):
+def hop_roofline(L, F, lat, gsl, prec, flush, stream, vh, launches=40):
     t = _cold_hop_seconds(L, F, lat, gsl, prec, 12, flush, stream, launches)
+    t_flush = _cold_hop_seconds(L, F, lat, gsl, prec, 12, flush, stream, 20, rotate=False)
     # 8 links of 12 reals + input and output spinor, in the inner precision
     bytes_per_site = {1: 8 * 48 + 96 + 96, 2: 8 * 24 + 52 + 52}[prec]
     achieved = bytes_per_site * vh / t / 1e9
@@ -614,11 +644,15 @@ def hop_roofline(L, F, lat, gsl, prec, flush, stream, vh, launches=20):
     shape = L.lqcd_tune_get(hop_key(prec, 12, 0, 0, 0, lat.dims, 1))
     # no-reuse model: every neighbour spinor fetched once per use (8 in, 8 links, 1 out)
     no_reuse = {1: 8 * 48 + 8 * 96 + 96, 2: 8 * 24 + 8 * 52 + 52}[prec]
-    return {"bound": "hbm", "kernel": f"hop_kernel<{name}, recon 12> (one checkerboard, cold L2)",
+    return {"bound": "hbm", "kernel": f"hop_kernel<{name}, recon 12> (one checkerboard, inputs not in L2)",
             "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
             "peak_source": peak_src, "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_site * vh,
             "no_reuse_bytes_per_launch": no_reuse * vh,
             "launch_us": round(t * 1e6, 2), "gflops": round(FLOP_PER_SITE * vh / t / 1e9, 1),
+            "timing": f"{launches} launches back to back, inputs rotated over copies totalling more than 2 x L2, "
+                      f"one event pair (mean per launch)",
+            "launch_us_flush_each": round(t_flush * 1e6, 2),
+            "frac_flush_each": round(bytes_per_site * vh / t_flush / 1e9 / peak, 4),
             "launch_shape": {"index": shape, "meaning": HOP_SHAPE_MEANING.get(shape, "default")}}
 
 
@@ -627,7 +661,11 @@ HOP_SHAPE_MEANING = {0: "128 threads, one site per thread", 1: "128 threads, one
                         "<= 72 registers", 3: "128 threads, one site per thread, <= 102 registers",
                      4: "128 threads, two sites per thread in packed FP32x2 arithmetic",
                      5: "128 threads, one site per thread, links staged in shared memory when n5 >= 4",
-                     6: "128 threads, one site per thread, spin components paired in packed FP32x2 arithmetic"}
+                     6: "128 threads, one site per thread, spin components paired in packed FP32x2 arithmetic",
+                     7: "128 threads, one site per thread, <= 72 registers, neighbour spinors and links copied "
+                        "asynchronously (cp.async) through a shared-memory ring",
+                     8: "128 threads, one site per thread, spin-paired packed FP32x2 arithmetic, <= 72 registers, "
+                        "neighbour data copied asynchronously through a shared-memory ring"}
 
 
 def hop_key(prec, recon, dagger, epi, red, dims, n5, full=0):

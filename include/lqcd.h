@@ -396,7 +396,10 @@ int lqcd_batch_cg_solve(int n, const lqcd_batch_item* items, int recon, const lq
  *    one site per thread, at least 6 blocks per SM, the eight links of each 4D
  *    site loaded once into shared memory for its n5 threads when n5 >= 4;
  *    6: 128 threads, one site per thread, the two spin components of each
- *    half spinor paired in packed FP32x2 arithmetic). All shapes give
+ *    half spinor paired in packed FP32x2 arithmetic; 7 / 8: as 1 / 2 with
+ *    each direction's neighbour spinor and link copied asynchronously into a
+ *    per-thread ring in shared memory while an earlier direction is computed,
+ *    29-37 KB of shared memory per block). All shapes give
  *    bit-identical hop results. A hop key is
  *    timed (a warm-up of every shape, then three interleaved rounds of two
  *    back-to-back launches each on the caller's stream, which is

@@ -208,20 +208,10 @@ __device__ __forceinline__ cpx<float> proj_h(unsigned int a, unsigned int q) {
 
 // FP16 storage: (1 + S gamma_mu) applied to the stored halves (each projected
 // component one conversion and one mixed-precision add), the same values as
-// converting all 24 components and projecting in FP32; returns the site norm.
+// converting all 24 components and projecting in FP32. w: the 12 complex FP16
+// pairs, complex k = spin * 3 + colour in word k.
 template <int MU, int S>
-__device__ __forceinline__ float load_project_f16(const void* in, int64_t stride, int64_t idx, Half<float>& h) {
-  const uint4* b = reinterpret_cast<const uint4*>(in);
-  const float nrm = __ldg(SpinorIO<LQCD_F16>::norm_ptr(in, stride) + idx);
-  unsigned int w[12];  // complex k = spin * 3 + colour in word k
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    const uint4 v = __ldg(b + c * stride + idx);
-    w[4 * c] = v.x;
-    w[4 * c + 1] = v.y;
-    w[4 * c + 2] = v.z;
-    w[4 * c + 3] = v.w;
-  }
+__device__ __forceinline__ void project_f16_words(const unsigned int (&w)[12], Half<float>& h) {
   // h0 = p0 + c0 p_k0, h1 = p1 + c1 p_k1 (the chiral-basis projection of project<MU, S>)
   constexpr int K0 = MU < 2 ? 3 : 2, K1 = MU < 2 ? 2 : 3;
   constexpr int C0 = MU == 0 ? (S > 0 ? 3 : 2) : MU == 1 ? (S > 0 ? 1 : 0) : MU == 2 ? (S > 0 ? 3 : 2) : (S > 0 ? 0 : 1);
@@ -231,6 +221,23 @@ __device__ __forceinline__ float load_project_f16(const void* in, int64_t stride
     h.v[c] = proj_h<C0>(w[c], w[3 * K0 + c]);
     h.v[3 + c] = proj_h<C1>(w[3 + c], w[3 * K1 + c]);
   }
+}
+
+// The FP16 neighbour at idx loaded and projected; returns its site norm.
+template <int MU, int S>
+__device__ __forceinline__ float load_project_f16(const void* in, int64_t stride, int64_t idx, Half<float>& h) {
+  const uint4* b = reinterpret_cast<const uint4*>(in);
+  const float nrm = __ldg(SpinorIO<LQCD_F16>::norm_ptr(in, stride) + idx);
+  unsigned int w[12];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const uint4 v = __ldg(b + c * stride + idx);
+    w[4 * c] = v.x;
+    w[4 * c + 1] = v.y;
+    w[4 * c + 2] = v.z;
+    w[4 * c + 3] = v.w;
+  }
+  project_f16_words<MU, S>(w, h);
   return nrm;
 }
 
@@ -478,11 +485,23 @@ __device__ __forceinline__ void hop_dir_sp(SPAcc& acc, const Geom& g, const void
   }
 }
 
-// H in at output site j (= cb * n5 + i5) of checkerboard `parity`.
-template <int P, int R, bool DAG, bool GP = false, bool SP = false>
+}  // namespace lqcd
+
+#include "hop_async.cuh"  // the staged hop uses the projections and products above
+
+namespace lqcd {
+
+// H in at output site j (= cb * n5 + i5) of checkerboard `parity`. AS: neighbour
+// data streamed through the shared-memory ring `ring` (hop_async.cuh).
+template <int P, int R, bool DAG, bool GP = false, bool SP = false, bool AS = false, int BLOCK = 128>
 __device__ __forceinline__ void hop_acc(const Geom& g, const void* gauge, const void* in, int parity, int64_t j,
                                         Spinor<typename PrecTraits<P>::real>& acc,
-                                        const Link<typename PrecTraits<P>::real>* sl = nullptr) {
+                                        const Link<typename PrecTraits<P>::real>* sl = nullptr,
+                                        unsigned char* ring = nullptr) {
+  if constexpr (AS) {
+    hop_acc_async<P, R, DAG, SP, BLOCK>(g, gauge, in, parity, j, acc, ring);
+    return;
+  }
   const int64_t n5 = g.n5;
   int64_t cb, i5;
   if (n5 == 1) {
@@ -567,13 +586,14 @@ __device__ __forceinline__ void hop_epilogue(const Geom& g, const void* xb, int6
 }
 
 // The result at output site j (= cb * n5 + i5) of checkerboard `parity`.
-template <int P, int R, bool DAG, int EPI, bool GP = false, bool SP = false>
+template <int P, int R, bool DAG, int EPI, bool GP = false, bool SP = false, bool AS = false, int BLOCK = 128>
 __device__ __forceinline__ void hop_site(const Geom& g, const void* gauge, const void* in, const void* xb,
                                          int parity, int64_t j, const EpiCoef& c,
                                          Spinor<typename PrecTraits<P>::real>& res,
-                                         const Link<typename PrecTraits<P>::real>* sl = nullptr) {
+                                         const Link<typename PrecTraits<P>::real>* sl = nullptr,
+                                         unsigned char* ring = nullptr) {
   Spinor<typename PrecTraits<P>::real> acc;
-  hop_acc<P, R, DAG, GP, SP>(g, gauge, in, parity, j, acc, sl);
+  hop_acc<P, R, DAG, GP, SP, AS, BLOCK>(g, gauge, in, parity, j, acc, sl, ring);
   hop_epilogue<P, DAG, EPI>(g, xb, j, c, acc, res);
 }
 
@@ -628,7 +648,8 @@ __device__ __forceinline__ void stage_links(const Geom& g, const void* gauge, in
 // BLOCK together in packed FP32x2 arithmetic (hop_pair.cuh), so that every
 // load instruction of a warp stays one coalesced access and the two sites
 // share each FP32 instruction of the hop.
-template <int P, int R, bool DAG, int EPI, int RED, int BLOCK, bool GP, int SPT, bool LS = false, bool SP = false>
+template <int P, int R, bool DAG, int EPI, int RED, int BLOCK, bool GP, int SPT, bool LS = false, bool SP = false,
+          bool AS = false>
 __device__ __forceinline__ void hop_body(const HopArgs& A) {
   using T = typename PrecTraits<P>::real;
   static_assert(SPT == 1 || (SPT == 2 && P != LQCD_F64 && !GP), "two sites per thread: FP32 / FP16, no G-parity");
@@ -658,13 +679,19 @@ __device__ __forceinline__ void hop_body(const HopArgs& A) {
         if (j < A.g.nsites) sl = staged + (j / n5 - cb0) * 8;
       }
     }
+    // AS: the ring of asynchronously copied neighbour data
+    unsigned char* ring = nullptr;
+    if constexpr (AS) {
+      __shared__ __align__(16) unsigned char stage_ring[stage_nslot<P>() * stage_slot_bytes<P, R>() * BLOCK];
+      ring = stage_ring;
+    }
     if constexpr (EPI == EPI_M5INV) {
       // every lane takes part in the fifth-dimension scan; lanes past the end
       // (whole 4D sites, since L_s divides the block) carry zeros and store nothing
       static_assert(RED == RED_NONE, "M5op^-1 epilogue without reduction");
       const bool live = j < A.g.nsites;
       Spinor<T> res;
-      if (live) hop_site<P, R, DAG, EPI, GP, SP>(A.g, A.gauge, in, xb, parity, j, c, res, sl);
+      if (live) hop_site<P, R, DAG, EPI, GP, SP, AS, BLOCK>(A.g, A.gauge, in, xb, parity, j, c, res, sl, ring);
       else zero(res);
       const int Ls = A.g.n5;
       m5inv_lanes(res, (int)(threadIdx.x & (unsigned)(Ls - 1)), Ls, A.m5_dagger != 0, (T)A.m5_a, (T)A.mf,
@@ -675,7 +702,7 @@ __device__ __forceinline__ void hop_body(const HopArgs& A) {
     T red = T(0);
     if (j < A.g.nsites) {
       Spinor<T> res;
-      hop_site<P, R, DAG, EPI, GP, SP>(A.g, A.gauge, in, xb, parity, j, c, res, sl);
+      hop_site<P, R, DAG, EPI, GP, SP, AS, BLOCK>(A.g, A.gauge, in, xb, parity, j, c, res, sl, ring);
       if constexpr (RED == RED_CG_UPDATE) {
         const int64_t ps = A.full ? parity * A.half_bytes : 0, vs = A.full ? parity * A.upd_half_bytes : 0;
         const int64_t rs = A.full ? parity * A.upd_rs_half_bytes : 0;
@@ -750,11 +777,15 @@ __device__ __forceinline__ void hop_body(const HopArgs& A) {
 // of the launch shapes the tuner times.
 //
 // SPT = -1: one site per thread with the links staged in shared memory (LS);
-// SPT = -2: one site per thread in spin-paired packed arithmetic (SP).
+// SPT = -2: one site per thread in spin-paired packed arithmetic (SP);
+// SPT = -3 / -4: as 1 / -2 with the neighbour data copied asynchronously
+// through a shared-memory ring (AS, hop_async.cuh).
 template <int P, int R, bool DAG, int EPI, int RED, int BLOCK, bool GP = false, int SPT = 1, int MINB = 0>
 __global__ void __launch_bounds__(BLOCK, MINB) hop_kernel(const HopArgs A) {
   if constexpr (SPT == -1) hop_body<P, R, DAG, EPI, RED, BLOCK, GP, 1, true>(A);
   else if constexpr (SPT == -2) hop_body<P, R, DAG, EPI, RED, BLOCK, GP, 1, false, true>(A);
+  else if constexpr (SPT == -3) hop_body<P, R, DAG, EPI, RED, BLOCK, GP, 1, false, false, true>(A);
+  else if constexpr (SPT == -4) hop_body<P, R, DAG, EPI, RED, BLOCK, GP, 1, false, true, true>(A);
   else hop_body<P, R, DAG, EPI, RED, BLOCK, GP, SPT>(A);
 }
 

@@ -8,11 +8,19 @@ namespace lqcd {
 
 template <int P, int R, bool DAG, int EPI, int RED, bool GP, int BLOCK, int SPT, int MINB>
 static int launch_hop_shape(HopArgs a, cudaStream_t s) {
-  constexpr int SITES = SPT < 0 ? 1 : SPT;  // SPT -1 / -2: one site per thread (links staged / spin-paired)
+  constexpr int SITES = SPT < 0 ? 1 : SPT;  // SPT -1 .. -4: one site per thread
   const int64_t nb = (a.g.nsites + BLOCK * SITES - 1) / (BLOCK * SITES);
   a.blocks_per_parity = (int)nb;
   const int64_t grid = a.full ? 2 * nb : nb;
   if (grid == 0) return LQCD_OK;
+  if constexpr (SPT <= -3) {
+    // the staged hop's ring: ask for the largest shared-memory carveout so that
+    // MINB blocks of it fit an SM
+    static const cudaError_t carve = cudaFuncSetAttribute(hop_kernel<P, R, DAG, EPI, RED, BLOCK, GP, SPT, MINB>,
+                                                          cudaFuncAttributePreferredSharedMemoryCarveout,
+                                                          (int)cudaSharedmemCarveoutMaxShared);
+    if (carve != cudaSuccess) return cuda_fail(carve, "hop_kernel: shared-memory carveout");
+  }
   hop_kernel<P, R, DAG, EPI, RED, BLOCK, GP, SPT, MINB><<<(unsigned)grid, BLOCK, 0, s>>>(a);
   return after_launch("hop_kernel");
 }

@@ -26,17 +26,23 @@ constexpr int HOP_BLOCK = 128;
 // X(index, threads per block, sites per thread, minimum resident blocks per SM;
 // 0 leaves the register count to the compiler). Measured on GB300 at 24^3 x 48
 // (warm, back to back): the plain FP16 / 12-real hop takes 26.6-27.1 us with one
-// site per thread, 26.8 us spin-paired (21 % fewer instructions, the FMA pipe
-// as busy), 30 us with two sites per thread (32 % fewer instructions, 168-222
-// registers); the FP32 / 12-real hop is fastest spin-paired. Shape 0 is the
-// default; the tuner times all of them per key.
+// site per thread, 25.2-26.8 us spin-paired (21 % fewer instructions, the FMA
+// pipe as busy), 25.7 us with the neighbour data staged asynchronously (long-
+// scoreboard stalls 3.6 -> 0.5 per issue, issue slots 69 -> 77 % busy, 9 % more
+// instructions), 30 us with two sites per thread (32 % fewer instructions,
+// 168-222 registers); the FP32 / 12-real hop is fastest staged (34.8 us cold,
+// 0.81 of the copy bandwidth, against 36.9 us). Shape 0 is the default; the
+// tuner times all of them per key.
 // Sites per thread -1: one site per thread with the links of each 4D site staged
 // in shared memory once for its n5 threads (L_s-replicated and multi-RHS hops,
 // n5 >= 4; otherwise as shape 0). -2: one site per thread with the two spin
-// components of each half spinor paired in packed FP32x2 instructions.
+// components of each half spinor paired in packed FP32x2 instructions. -3 / -4:
+// as 1 / -2 with each direction's neighbour spinor and link copied with
+// cp.async into a per-thread shared-memory ring while an earlier direction is
+// computed (hop_async.cuh).
 #define LQCD_HOP_SHAPES(X) X(0, 128, 1, 0) X(1, 128, 1, 7) X(2, 128, -2, 7) X(3, 128, 1, 5) X(4, 128, 2, 3) \
-  X(5, 128, -1, 6) X(6, 128, -2, 0)
-constexpr int HOP_SHAPES = 7;
+  X(5, 128, -1, 6) X(6, 128, -2, 0) X(7, 128, -3, 7) X(8, 128, -4, 7)
+constexpr int HOP_SHAPES = 9;
 // The shape used when the table holds no choice for a hop.
 constexpr int HOP_SHAPE_DEFAULT = 0;
 

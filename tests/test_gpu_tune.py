@@ -27,7 +27,7 @@ torch = pytest.importorskip("torch")
 
 TOL = {1: 1e-5, 2: 3e-3}
 BC = (1.0, 1.0, 1.0, -1.0)
-NSHAPES = 7
+NSHAPES = 9
 
 
 @pytest.fixture(scope="module")
