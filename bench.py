@@ -691,15 +691,17 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def fma_peak(L, F, prec, stream):
-    """Measured FMA-chain rate (TFLOP/s) of lqcd_fma_probe: 152 x 8 blocks of 256 threads, best of 3."""
+    """Measured FMA-chain rate (TFLOP/s) of the FMA probe (paper_1512_03487_gb300/measure, a library of its
+    own): 152 x 8 blocks of 256 threads, best of 3."""
     import torch
+    from paper_1512_03487_gb300 import measure as probe
     blocks = 152 * 8
     iters = 4096 if prec == 0 else 262144
     sink = torch.empty(blocks * 256, dtype=torch.float64 if prec == 0 else torch.float32, device="cuda")
-    L.lqcd_fma_probe(sink, prec, iters, blocks)
+    probe.fma_probe(sink, prec, iters, blocks)
     best = None
     for _ in range(3):
-        t, _ = _events_time(lambda: L.lqcd_fma_probe(sink, prec, iters, blocks), stream)
+        t, _ = _events_time(lambda: probe.fma_probe(sink, prec, iters, blocks), stream)
         best = t if best is None else min(best, t)
     return 16.0 * iters * blocks * 256 / (best * 1e-3) / 1e12
 

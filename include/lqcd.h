@@ -248,19 +248,6 @@ int lqcd_eo_prepare(void* bhat_even_dev, const void* b_full_dev, const void* gau
 int lqcd_eo_reconstruct(void* x_full_dev, const void* b_full_dev, const void* gauge_dev,
                         const lqcd_lattice* lat, const lqcd_operator* op, void* tmp_dev, void* stream);
 
-/* ---------------------------------------------------------------- measurement only */
-
-/* Outside the method's ABI: a probe that bench.py uses to measure the GPU's
- * FP64 / FP32 FMA rate, the denominator of the ALU-bound kernels' rooflines.
- * Arithmetic probe (measurement, not part of the method): `blocks` blocks of
- * 256 threads each run 8 independent chains of `iters` fused multiply-adds in
- * prec (LQCD_F64 or LQCD_F32) and store one value per thread into sink_dev
- * (blocks * 256 elements of that precision, caller-owned, 8-byte aligned).
- * 16 * iters * blocks * 256 flop per call; timed by the caller on `stream`, it
- * gives the FP64 / FP32 FMA rate that ALU-bound kernels are compared with.
- * Asynchronous. */
-int lqcd_fma_probe(void* sink_dev, int prec, int64_t iters, int blocks, void* stream);
-
 /* ---------------------------------------------------------------- solvers */
 
 /* Conjugate gradient (Grid paper Sec. 4 lists CG) for A x = b with

@@ -104,7 +104,6 @@ SIGNATURES = {
     "lqcd_cgnr_solve": (_I, [_P, _P, _P, _P, _LAT, _OP, _PRM, _I, _INFO, _P, _SZ, _P]),
     "lqcd_eo_solve_workspace_bytes": (_SZ, [_LAT, _OP, _PRM]),
     "lqcd_eo_solve": (_I, [_P, _P, _P, _P, _LAT, _OP, _PRM, _INFO, _P, _SZ, _P]),
-    "lqcd_fma_probe": (_I, [_P, _I, C.c_int64, _I, _P]),
     "lqcd_force": (_I, [_P, _P, _P, _P, _LAT, _OP, _I, _P]),
     "lqcd_colour_matrix_bytes": (_SZ, [_LAT, _I]),
     "lqcd_colour_matrix_pack": (_I, [_P, _I, _P, _LAT, _P]),

@@ -216,10 +216,6 @@ def lqcd_eo_solve(x, b, gauge, gauge_sloppy, lat, op, params, workspace, stream=
     return info
 
 
-def lqcd_fma_probe(sink, prec, iters, blocks, stream=None):
-    _check(lib.lqcd_fma_probe(_ptr(sink), prec, iters, blocks, _stream(stream)))
-
-
 def lqcd_block_cg_workspace_bytes(lat, op, params) -> int:
     return int(lib.lqcd_block_cg_workspace_bytes(C.byref(lat), C.byref(op), C.byref(params)))
 

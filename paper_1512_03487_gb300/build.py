@@ -82,7 +82,27 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         if res.returncode != 0:
             raise RuntimeError(f"link failed:\n{res.stderr}")
         os.replace(tmp, LIB_PATH)
+    build_probe(force, verbose, extra_flags)
     return LIB_PATH
+
+
+PROBE_SRC = os.path.join(PKG_DIR, "measure", "fma_probe.cu")
+PROBE_LIB = os.path.join(PKG_DIR, "libfma_probe.so")
+
+
+def build_probe(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+    """The bench's FMA-rate probe, a library of its own (not part of liblqcd's ABI)."""
+    if force or not os.path.exists(PROBE_LIB) or os.path.getmtime(PROBE_LIB) < os.path.getmtime(PROBE_SRC):
+        tmp = PROBE_LIB + ".tmp"
+        cmd = [nvcc()] + ARCH + ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared"] + list(extra_flags) + \
+            [PROBE_SRC, "-o", tmp]
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError(f"nvcc failed for fma_probe.cu:\n{res.stderr}")
+        if verbose and res.stderr:
+            sys.stderr.write(res.stderr)
+        os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
 
 
 def main() -> None:

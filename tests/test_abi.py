@@ -76,14 +76,25 @@ def test_workspace_queries(api):
         assert api.lqcd_cg_workspace_bytes(lat, op, api.solver_params(delta_mid=d), api.LQCD_EVEN) == 0
 
 
-def test_fma_probe_rejects_bad_arguments(api):
-    """Host-side validation of the probe, before any launch."""
+def test_fma_probe_is_outside_the_abi_and_rejects_bad_arguments(api):
+    """The bench's FMA probe lives in its own library, not in liblqcd, and
+    validates its arguments on the host before any launch."""
     import ctypes as C
-    lib = api.lib
-    assert lib.lqcd_fma_probe(None, 0, 10, 1, None) != 0
-    assert lib.lqcd_fma_probe(C.c_void_p(4096), 2, 10, 1, None) != 0  # FP16 is not a probe precision
-    assert lib.lqcd_fma_probe(C.c_void_p(4096), 0, 0, 1, None) != 0
-    assert lib.lqcd_fma_probe(C.c_void_p(4100), 0, 10, 1, None) != 0  # misaligned
+    from paper_1512_03487_gb300 import measure
+    assert not hasattr(api.lib, "lqcd_fma_probe") or _not_exported(api.lib, "lqcd_fma_probe")
+    lib = measure.lib()
+    assert lib.fma_probe(None, 0, 10, 1, None) == -1
+    assert lib.fma_probe(C.c_void_p(4096), 2, 10, 1, None) == -1  # FP16 is not a probe precision
+    assert lib.fma_probe(C.c_void_p(4096), 0, 0, 1, None) == -1
+    assert lib.fma_probe(C.c_void_p(4100), 0, 10, 1, None) == -1  # misaligned
+
+
+def _not_exported(lib, name):
+    try:
+        getattr(lib, name)
+        return False
+    except AttributeError:
+        return True
 
 
 def test_struct_layouts_match_the_header(api):

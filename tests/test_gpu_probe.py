@@ -9,19 +9,19 @@ torch = pytest.importorskip("torch")
 
 
 @pytest.fixture(scope="module")
-def L():
+def probe():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    import paper_1512_03487_gb300 as L
-    return L
+    from paper_1512_03487_gb300 import measure
+    return measure
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_fma_chains(L, prec):
+def test_fma_chains(probe, prec):
     blocks, iters = 3, 200
     dt = torch.float64 if prec == 0 else torch.float32
     sink = torch.empty(blocks * 256, dtype=dt, device="cuda")
-    L.lqcd_fma_probe(sink, prec, iters, blocks)
+    probe.fma_probe(sink, prec, iters, blocks)
     got = sink.cpu().numpy()
     a, b = (0.999999, 1e-6) if prec == 0 else (np.float32(0.9999), np.float32(1e-4))
     npdt = np.float64 if prec == 0 else np.float32
