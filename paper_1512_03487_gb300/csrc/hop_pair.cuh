@@ -93,20 +93,25 @@ template <> struct PairSpinorIO<LQCD_F16> {
 };
 
 // ---- links of the two sites (blocks blk_a / blk_b at checkerboard sites cb_a / cb_b)
-// a b, rounded like cmul of the one-site hop
-__device__ __forceinline__ pc pmul(pc a, pc b) {
-  return pmk(fma2(neg2(a.i), b.i, mul2(a.r, b.r)), fma2(a.i, b.r, mul2(a.r, b.i)));
+// conj(a b - c d) with the one-site hop's rounding (conj_cross)
+__device__ __forceinline__ pc conj_cross_pair(pc a, pc b, pc c, pc d) {
+  float2 re = mul2(a.r, b.r);
+  re = fma2(neg2(a.i), b.i, re);
+  re = fma2(neg2(c.r), d.r, re);
+  re = fma2(c.i, d.i, re);
+  float2 im = neg2(mul2(a.r, b.i));
+  im = fma2(neg2(a.i), b.r, im);
+  im = fma2(c.r, d.i, im);
+  im = fma2(c.i, d.r, im);
+  return pmk(re, im);
 }
 
 // row 2 = conj(row 0 x row 1), with the one-site hop's rounding (rebuild_row2),
 // so that both launch shapes give bit-identical results
 __device__ __forceinline__ void rebuild_row2_pair(PLink& u) {
-  const int A[3] = {1, 2, 0}, B[3] = {5, 3, 4}, C[3] = {2, 0, 1}, D[3] = {4, 5, 3};
-#pragma unroll
-  for (int k = 0; k < 3; k++) {
-    const pc ab = pmul(u.v[A[k]], u.v[B[k]]), cd = pmul(u.v[C[k]], u.v[D[k]]);
-    u.v[6 + k] = pmk(sub2(ab.r, cd.r), sub2(cd.i, ab.i));
-  }
+  u.v[6] = conj_cross_pair(u.v[1], u.v[5], u.v[2], u.v[4]);
+  u.v[7] = conj_cross_pair(u.v[2], u.v[3], u.v[0], u.v[5]);
+  u.v[8] = conj_cross_pair(u.v[0], u.v[4], u.v[1], u.v[3]);
 }
 
 template <int P, int R> struct PairLinkIO;

@@ -258,11 +258,24 @@ template <> struct SpinorIO<LQCD_F16> {
 // Gauge block (parity, mu) starts at chunk (parity * 4 + mu) * NCHUNK.
 template <int P, int R> struct LinkIO;
 
+// conj(a b - c d) as two chains of a multiply and three fused multiply-adds
+template <typename T> __device__ __forceinline__ cpx<T> conj_cross(cpx<T> a, cpx<T> b, cpx<T> c, cpx<T> d) {
+  T re = a.r * b.r;
+  re = fma(-a.i, b.i, re);
+  re = fma(-c.r, d.r, re);
+  re = fma(c.i, d.i, re);
+  T im = -(a.r * b.i);
+  im = fma(-a.i, b.r, im);
+  im = fma(c.r, d.i, im);
+  im = fma(c.i, d.r, im);
+  return mk(re, im);
+}
+
 template <typename T> __device__ __forceinline__ void rebuild_row2(Link<T>& u) {
-  // row2 = conj(row0 x row1)
-  u.v[6] = conj(cmul(u.v[1], u.v[5]) - cmul(u.v[2], u.v[4]));
-  u.v[7] = conj(cmul(u.v[2], u.v[3]) - cmul(u.v[0], u.v[5]));
-  u.v[8] = conj(cmul(u.v[0], u.v[4]) - cmul(u.v[1], u.v[3]));
+  // row2 = conj(row0 x row1) (SU(3): the rows are orthonormal and det = 1)
+  u.v[6] = conj_cross(u.v[1], u.v[5], u.v[2], u.v[4]);
+  u.v[7] = conj_cross(u.v[2], u.v[3], u.v[0], u.v[5]);
+  u.v[8] = conj_cross(u.v[0], u.v[4], u.v[1], u.v[3]);
 }
 
 template <> struct LinkIO<LQCD_F64, 18> {
