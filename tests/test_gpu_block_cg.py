@@ -24,13 +24,13 @@ def L():
     return L
 
 
-def _block_solve(L, U, b, dims, m, sloppy, recon=12, tol=1e-10, maxiter=3000):
+def _block_solve(L, U, b, dims, m, sloppy, recon=12, tol=1e-10, maxiter=3000, update_prec=0):
     F = L.fields
     n = b.shape[0]
     lat = L.lattice(dims, n5=n, bc=BC)
     op = L.operator(mass=m)
     prm = L.solver_params(tol=tol, maxiter=maxiter, sloppy_prec=sloppy, sloppy_recon=recon, delta=0.01,
-                          check_interval=16)
+                          check_interval=16, update_prec=update_prec)
     g64 = F.gauge_to_device(U, lat, 0, 18)
     gs = F.gauge_to_device(U, lat, sloppy, recon) if sloppy else g64
     bd = F.spinor_to_device(b, lat, 0, 0)
@@ -50,15 +50,31 @@ def _check_columns(U, x, b, m, tol=1e-10):
         assert res <= tol, (k, res)
 
 
-@pytest.mark.parametrize("sloppy", [0, 1, 2])
-def test_block_cg_reaches_tolerance(L, sloppy):
+@pytest.mark.parametrize("sloppy,update_prec", [(0, 0), (1, 0), (2, 0), (1, 3), (2, 3)])
+def test_block_cg_reaches_tolerance(L, sloppy, update_prec):
+    """FP64, FP32 and FP16 inner operators; reliable updates on the FP64 pipe or
+    in double-float arithmetic (update_prec 3)."""
     dims, m, n = (4, 4, 4, 8), 0.05, 6
     U = gauge_field(dims, "haar", 701)
     b = to_cb(gaussian_spinor(dims, 702, lead=(n,)), 0)
-    x, info = _block_solve(L, U, b, dims, m, sloppy)
+    x, info = _block_solve(L, U, b, dims, m, sloppy, update_prec=update_prec)
     assert info.status == 0, L.lqcd_last_error()
     _check_columns(U, x, b, m)
     assert info.true_rel_residual <= 1e-10
+
+
+@pytest.mark.parametrize("n", [1, 3, 5, 9, 13, 16])
+@pytest.mark.parametrize("sloppy", [0, 1])
+def test_block_cg_every_gram_tile(L, n, sloppy):
+    """Block sizes that take each register tile of the Gram kernel (1 x 1 for
+    N <= 4 up to 4 x 4 for N <= 16, with ragged last tiles), on a lattice whose
+    40 4D sites per checkerboard leave a partial last pass of staged sites."""
+    dims, m = (2, 2, 2, 10), 0.1
+    U = gauge_field(dims, "haar", 731 + n)
+    b = to_cb(gaussian_spinor(dims, 732 + n, lead=(n,)), 0)
+    x, info = _block_solve(L, U, b, dims, m, sloppy, update_prec=3 if sloppy else 0)
+    assert info.status == 0, L.lqcd_last_error()
+    _check_columns(U, x, b, m)
 
 
 def test_block_cg_needs_no_more_iterations_than_independent_cg(L):
