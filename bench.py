@@ -86,7 +86,7 @@ def parse_args():
     ap.add_argument("--hop-prec", type=int, choices=[0, 1, 2, 3], default=HEADLINE_PREC,
                     help="the hop timed by --mode hop: 1 FP32, 2 FP16 storage (12-real links); 0 FP64, "
                          "3 FP64 fields in double-float arithmetic (18-real links)")
-    ap.add_argument("--mode", choices=["full", "step", "hop", "hops", "dwf"], default="full",
+    ap.add_argument("--mode", choices=["full", "step", "hop", "hops", "dwf", "blockcg"], default="full",
                     help="step: only the timed solves; hop: only the dominant kernel's roofline loop; "
                          "hops: the three hop shapes (profiling)")
     return ap.parse_args()
@@ -348,6 +348,14 @@ def _run_lqcd(args, world, rank, local, L, F, dev, stream):
         res = {name: shapes[name]() for name in names}
         if rank == 0:
             print(json.dumps({"mode": "hops", "hops": res}), flush=True)
+        return
+    if args.mode == "blockcg":
+        # profiling mode: one block CG solve of the 32^4 x 12-RHS workload (FP32 inner, double-float
+        # updates), honouring --no-graph / --check-interval
+        res = block_cg_bench(L, F, L2Flush(dev), stream, use_graph=0 if args.no_graph else 1,
+                             check_interval=args.check_interval)
+        if rank == 0:
+            print(json.dumps({"mode": "blockcg", "block_cg": res}), flush=True)
         return
     if args.mode == "dwf":
         # profiling mode: the domain-wall solve alone (FP32 inner), honouring --no-graph / --check-interval
@@ -818,6 +826,29 @@ def _hop_gbs(L, F, lat, prec, recon, bytes_per_site, flush, stream, kind=0, n=10
     gbs = bytes_per_site * nsites / t / 1e9
     return {"launch_us": round(t * 1e6, 2), "algorithmic_bytes_per_site": bytes_per_site, "achieved_gbs": round(gbs, 1),
             "frac_of_measured_hbm": round(gbs / peak, 4), "gflops": round(FLOP_PER_SITE * nsites / t / 1e9, 1)}
+
+
+def block_cg_bench(L, F, flush, stream, use_graph=1, check_interval=64):
+    """32^4, 12 Gaussian right-hand sides, Haar links, m = 0.01: block CG on
+    M_hat^dag M_hat X = B_e to 1e-10, FP32 / 12-real inner, double-float updates
+    (delta 1e-5); one warm-up and one timed solve."""
+    from synthetic import config_seed, gauge_field, gaussian_spinor
+    dims, nr = (32, 32, 32, 32), 12
+    U = gauge_field(dims, "haar", config_seed(3, 0))
+    lat = L.lattice(dims, n5=nr, bc=BC)
+    op = L.operator(mass=0.01)
+    g64 = F.gauge_to_device(U, lat, 0, 18)
+    g32 = F.gauge_to_device(U, lat, 1, 12)
+    del U
+    be = F.spinor_to_device(F.checkerboard(gaussian_spinor(dims, config_seed(3, 1), lead=(nr,)), 0), lat, 0, 0)
+    x = F.empty(L.lqcd_spinor_bytes(lat, 0, 0))
+    prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=12, delta=DELTA_NORMAL_FP32,
+                          check_interval=check_interval, use_graph=use_graph, update_prec=L.LQCD_F64_DF)
+    ws = F.empty(L.lqcd_block_cg_workspace_bytes(lat, op, prm))
+    L.lqcd_block_cg_solve(x, be, g64, g32, lat, op, prm, ws)
+    ms, info = _events_time(lambda: L.lqcd_block_cg_solve(x, be, g64, g32, lat, op, prm, ws), stream, flush)
+    return {"ms": round(ms, 3), "iterations": info.iterations, "reliable_updates": info.reliable_updates,
+            "max_true_rel_residual_normal_eq": info.true_rel_residual}
 
 
 def run_extras(L, F, flush, stream):
