@@ -1019,7 +1019,8 @@ def run_extras(L, F, flush, stream):
 
 def dwf_bench(L, F, flush, stream, use_graph=1, check_interval=64, three_level=True):
     """16^4 x L_s = 16 domain wall, M5 = 1.8, mf = 0.02, Haar links: even-odd CGNR to 1e-10 with FP32
-    inner storage (delta 1e-5) and, optionally, FP16 storage with three levels; one warm-up, one timed run."""
+    inner storage (delta 3e-6) and, optionally, FP16 storage with three levels, reliable updates in
+    double-float arithmetic; one warm-up, one timed run (and the plain FP64 solve beside them)."""
     import torch
     from synthetic import config_seed, gauge_field, gaussian_spinor
     dims, Ls = (16, 16, 16, 16), 16
@@ -1033,9 +1034,10 @@ def dwf_bench(L, F, flush, stream, use_graph=1, check_interval=64, three_level=T
     del b
     x = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
     prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=12, delta=DELTA[1],
-                          check_interval=check_interval, use_graph=use_graph)
+                          check_interval=check_interval, use_graph=use_graph, update_prec=L.LQCD_F64_DF)
     prm3 = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=2, sloppy_recon=12, delta=DELTA_3LVL,
-                           delta_mid=DELTA_MID, check_interval=check_interval, use_graph=use_graph)
+                           delta_mid=DELTA_MID, check_interval=check_interval, use_graph=use_graph,
+                           update_prec=L.LQCD_F64_DF)
     g16 = F.gauge_to_device(U, lat, 2, 12)
     ws = F.empty(max(L.lqcd_eo_solve_workspace_bytes(lat, op, q) for q in (prm, prm3)))
 

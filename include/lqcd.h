@@ -74,8 +74,10 @@ extern "C" {
 #define LQCD_F64_DF 3  /* FP64 storage (the LQCD_F64 layout) with double-float arithmetic: each
                           real a pair of FP32 numbers (about 48 bits; results within a few 1e-15
                           of the FP64 arithmetic), for GPUs whose FP64 units are few. An operator
-                          precision only (op->prec; Wilson, no G-parity: lqcd_dslash, lqcd_M,
-                          lqcd_MdagM, lqcd_eo_prepare, lqcd_eo_reconstruct); fields are LQCD_F64 */
+                          precision only (op->prec: lqcd_dslash, lqcd_M, lqcd_MdagM, and for Wilson
+                          lqcd_eo_prepare, lqcd_eo_reconstruct); Wilson without G-parity, or domain
+                          wall on 18-real links with L_s dividing 32 (LQCD_ERR_UNSUPPORTED
+                          otherwise); fields are LQCD_F64 */
 
 #define LQCD_EVEN 0  /* field subset: even checkerboard */
 #define LQCD_ODD  1  /* odd checkerboard */
@@ -129,10 +131,12 @@ typedef struct {
     double timeout_ms;     /* wall-clock limit; 0 = none */
     double delta_mid;      /* lqcd_cg_solve with sloppy_prec LQCD_F16 only (0 = off): threshold of the
                               intermediate FP32-arithmetic residual replacement (e.g. 0.003); see below */
-    int update_prec;       /* mixed Wilson solves: arithmetic of the FP64-field operator of the reliable
-                              updates and of lqcd_eo_solve's source preparation, LQCD_F64 (0, the
-                              default) or LQCD_F64_DF (double-float: the true residual b - A x within a
-                              few 1e-15 |b| of the FP64 one, several times faster on GB300) */
+    int update_prec;       /* mixed solves: arithmetic of the FP64-field operator of the reliable
+                              updates (and of lqcd_eo_solve's Wilson source preparation), LQCD_F64 (0,
+                              the default) or LQCD_F64_DF (double-float: the true residual b - A x within
+                              a few 1e-15 |b| of the FP64 one, about 1.8x faster on GB300). Applies to
+                              Wilson operators without G-parity and to domain wall on 18-real links with
+                              L_s dividing 32; other operators keep FP64 updates */
     int reserved;          /* 0 */
 } lqcd_solver_params;
 
@@ -238,7 +242,8 @@ size_t lqcd_operator_workspace_bytes(const lqcd_lattice* lat, const lqcd_operato
 
 /* Even-odd helpers around a solve on the single-checkerboard grid (Sec. 2.4:
  * the paper's grids may hold one checkerboard; the Schur-complement reduction
- * itself is textbook). FP64 fields; op->prec LQCD_F64 or LQCD_F64_DF:
+ * itself is textbook). FP64 fields; op->prec LQCD_F64 (or LQCD_F64_DF for
+ * Wilson; the domain-wall helpers' separate M5op^-1 has no double-float form):
  *   b_hat_e = b_e + H_eo A_oo^-1 b_o / 2            (prepare)
  *   x_o     = A_oo^-1 (b_o + H_oe x_e / 2)          (reconstruct, writes the
  *                                                    odd half of x_full)

@@ -5,6 +5,7 @@
 #include <cstring>
 
 #include "lqcd_internal.h"
+#include "m5_scan.cuh"
 
 namespace lqcd {
 
@@ -91,8 +92,14 @@ int check_operator(const lqcd_operator* op, Geom& g) {
   if (op->kind != LQCD_WILSON && op->kind != LQCD_DWF) return fail(LQCD_ERR_ARG, "bad operator kind %d", op->kind);
   if (op->prec != LQCD_F64 && op->prec != LQCD_F32 && op->prec != LQCD_F16 && op->prec != LQCD_F64_DF)
     return fail(LQCD_ERR_ARG, "bad precision %d", op->prec);
-  if (op->prec == LQCD_F64_DF && (op->kind != LQCD_WILSON || op->gparity))
-    return fail(LQCD_ERR_UNSUPPORTED, "double-float arithmetic: Wilson operator without G-parity only");
+  // double-float arithmetic: Wilson without G-parity, or domain wall on 18-real links whose L_s
+  // divides 32 (M5op^-1 fused into the hop's epilogue; the separate M5op^-1 kernels have no
+  // double-float form)
+  if (op->prec == LQCD_F64_DF &&
+      (op->gparity || (op->kind == LQCD_DWF && (op->recon != 18 || !m5_scan_ok(g.n5)))))
+    return fail(LQCD_ERR_UNSUPPORTED,
+                "double-float arithmetic: Wilson without G-parity, or domain wall with 18-real links and L_s "
+                "dividing 32");
   if (op->recon != 18 && op->recon != 12) return fail(LQCD_ERR_ARG, "bad recon %d", op->recon);
   if (op->kind == LQCD_DWF) {
     if (g.n5 > MAX_SYS * 4) return fail(LQCD_ERR_ARG, "L_s = %d too large", g.n5);

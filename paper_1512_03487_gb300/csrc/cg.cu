@@ -48,6 +48,7 @@
 #include <vector>
 
 #include "cg_engine.h"
+#include "m5_scan.cuh"
 #include "cg_site.cuh"
 
 namespace lqcd {
@@ -288,9 +289,12 @@ static Workspace carve(void* base, const Geom& g, const lqcd_operator& op, const
   return w;
 }
 
-// Whether a solve runs its FP64-field operator (reliable updates, even-odd source) in double-float arithmetic.
-static bool update_df(const lqcd_operator& op, const lqcd_solver_params& p) {
-  return p.sloppy_prec != LQCD_F64 && p.update_prec == LQCD_F64_DF && op.kind == LQCD_WILSON && !op.gparity;
+// Whether a solve runs its FP64-field operator (reliable updates, even-odd source) in double-float
+// arithmetic: Wilson without G-parity, or domain wall on 18-real links with L_s dividing 32 (the
+// double-float hop fuses M5op^-1 into its epilogue; check_operator states the same rule).
+static bool update_df(const lqcd_operator& op, const lqcd_solver_params& p, int n5) {
+  if (p.sloppy_prec == LQCD_F64 || p.update_prec != LQCD_F64_DF || op.gparity) return false;
+  return op.kind == LQCD_WILSON || (op.kind == LQCD_DWF && op.recon == 18 && m5_scan_ok(n5));
 }
 
 static int validate(const lqcd_lattice* lat, const lqcd_operator* op, const lqcd_solver_params* p, int subset,
@@ -558,7 +562,7 @@ static int cg_solve_impl(void* x, const void* b, const void* gauge, const void* 
   S.sys = S.w.sys;
   S.op64 = *op;
   // mixed Wilson solves may run the reliable updates' FP64-field operator in double-float arithmetic
-  if (update_df(*op, *prm)) S.op64.prec = LQCD_F64_DF;
+  if (update_df(*op, *prm, lat->n5)) S.op64.prec = LQCD_F64_DF;
   S.ops = *op;
   S.ops.prec = prm->sloppy_prec;
   // the FP64 inner operator runs on the FP64 field itself, in that field's format
@@ -740,7 +744,9 @@ int lqcd_eo_solve(void* x, const void* b, const void* gauge, const void* gauge_s
   void* tmp = off(bhat, round_up((int64_t)cb, 256));
   cudaStream_t s = (cudaStream_t)stream;
   lqcd_operator opp = *op;
-  if (update_df(*op, *prm)) opp.prec = LQCD_F64_DF;  // same FP64 fields, double-float arithmetic
+  // same FP64 fields, double-float arithmetic (Wilson: the domain-wall preparation's separate
+  // M5op^-1 kernel has no double-float form)
+  if (update_df(*op, *prm, lat->n5) && op->kind == LQCD_WILSON) opp.prec = LQCD_F64_DF;
   int st = lqcd_eo_prepare(bhat, b, gauge, lat, &opp, tmp, stream);
   if (st) {
     memset(inf, 0, sizeof(*inf));

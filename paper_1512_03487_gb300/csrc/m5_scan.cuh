@@ -26,6 +26,28 @@ template <typename T>
 __device__ __forceinline__ cpx<T> shfl_idx_c(cpx<T> v, int lane, int width) {
   return mk(__shfl_sync(0xffffffffu, v.r, lane, width), __shfl_sync(0xffffffffu, v.i, lane, width));
 }
+// double-float values: both halves of each part
+__device__ __forceinline__ dfl shfl_up_df(dfl v, int o, int width) {
+  return dfl(__shfl_up_sync(0xffffffffu, v.hi, o, width), __shfl_up_sync(0xffffffffu, v.lo, o, width));
+}
+__device__ __forceinline__ dfl shfl_down_df(dfl v, int o, int width) {
+  return dfl(__shfl_down_sync(0xffffffffu, v.hi, o, width), __shfl_down_sync(0xffffffffu, v.lo, o, width));
+}
+__device__ __forceinline__ dfl shfl_idx_df(dfl v, int lane, int width) {
+  return dfl(__shfl_sync(0xffffffffu, v.hi, lane, width), __shfl_sync(0xffffffffu, v.lo, lane, width));
+}
+template <>
+__device__ __forceinline__ cpx<dfl> shfl_up_c<dfl>(cpx<dfl> v, int o, int width) {
+  return mk(shfl_up_df(v.r, o, width), shfl_up_df(v.i, o, width));
+}
+template <>
+__device__ __forceinline__ cpx<dfl> shfl_down_c<dfl>(cpx<dfl> v, int o, int width) {
+  return mk(shfl_down_df(v.r, o, width), shfl_down_df(v.i, o, width));
+}
+template <>
+__device__ __forceinline__ cpx<dfl> shfl_idx_c<dfl>(cpx<dfl> v, int lane, int width) {
+  return mk(shfl_idx_df(v.r, lane, width), shfl_idx_df(v.i, lane, width));
+}
 
 // v[q0..q0+5] <- (d - L)^-1 of one chirality, in place. up: L shifts s-1 -> s
 // (the recurrence runs upward in s), else s+1 -> s. t = distance of this lane
@@ -41,7 +63,7 @@ __device__ __forceinline__ void m5_scan(Spinor<T>& v, int q0, bool up, int t, in
       const cpx<T> w = up ? shfl_up_c(v.v[q0 + q], o, Ls) : shfl_down_c(v.v[q0 + q], o, Ls);
       if (t >= o) v.v[q0 + q] = mk(fma(ao, w.r, v.v[q0 + q].r), fma(ao, w.i, v.v[q0 + q].i));
     }
-    ao *= ao;
+    ao = ao * ao;
   }
   // wrap: x = y - corr_t y_end, corr_t = mf a^(t+1) / (1 + mf a^Ls)
   const int end = up ? Ls - 1 : 0;
@@ -57,8 +79,8 @@ template <typename T>
 __device__ __forceinline__ T m5_corr(int t, T a, T mf, T den_inv) {
   T p = T(1), base = a;
   for (int e = t + 1; e; e >>= 1) {
-    if (e & 1) p *= base;
-    base *= base;
+    if (e & 1) p = p * base;
+    base = base * base;
   }
   return mf * p * den_inv;
 }

@@ -220,15 +220,18 @@ def test_autograd_rejects_host_tensors(api):
 
 
 def test_double_float_operator_rejections_on_host(api):
-    """LQCD_F64_DF is a Wilson-only operator precision: domain wall and
+    """LQCD_F64_DF serves Wilson without G-parity and domain wall on 18-real
+    links with L_s dividing 32: domain wall with L_s = 6 or 12-real links and
     G-parity are refused before any CUDA call, and a solver's update_prec
     accepts only LQCD_F64 and LQCD_F64_DF."""
     buf = 4096
-    lat4 = api.lattice((4, 4, 4, 4), n5=4)
-    with pytest.raises(api.LqcdError) as ei:
-        api.lqcd_dslash(buf, buf + 8192, buf + 16384, lat4, api.operator(kind=api.LQCD_DWF, prec=api.LQCD_F64_DF),
-                        api.LQCD_EVEN, 0, stream=0)
-    assert ei.value.status == -6
+    for n5, recon in ((6, 18), (4, 12)):
+        lat5 = api.lattice((4, 4, 4, 4), n5=n5)
+        with pytest.raises(api.LqcdError) as ei:
+            api.lqcd_dslash(buf, buf + 8192, buf + 16384, lat5,
+                            api.operator(kind=api.LQCD_DWF, prec=api.LQCD_F64_DF, recon=recon), api.LQCD_EVEN, 0,
+                            stream=0)
+        assert ei.value.status == -6
     lat2 = api.lattice((4, 4, 4, 4), n5=2)
     with pytest.raises(api.LqcdError) as ei:
         api.lqcd_dslash(buf, buf + 8192, buf + 16384, lat2, api.operator(prec=api.LQCD_F64_DF, gparity=1),

@@ -12,7 +12,7 @@ within a few 1e-15 |b| of the FP64 value.
 import numpy as np
 import pytest
 
-from oracle import wilson
+from oracle import dwf, wilson
 from synthetic import gauge_field, gaussian_spinor
 from tests.layout import rel_l2, to_cb
 
@@ -138,3 +138,74 @@ def test_df_reliable_updates_solve(L, sloppy):
         assert res <= 1e-10, (up, res)
         infos[up] = info
     assert abs(infos[DF].reliable_updates - infos[0].reliable_updates) <= 1
+
+
+@pytest.mark.parametrize("Ls", [4, 8])
+@pytest.mark.parametrize("subset", [0, 2])
+@pytest.mark.parametrize("dagger", [0, 1])
+def test_df_domain_wall_operator_matches_oracle(L, Ls, subset, dagger):
+    """Domain wall in double-float arithmetic (18-real links, L_s dividing 32):
+    the full operator (M5op epilogue) and the Schur complement (M5op^-1 fused
+    into the first hop by the warp-shuffle scan on double-float pairs, then the
+    M5op hop), against the oracle's dense-LU M5op^-1 and the FP64 operator."""
+    dims, M5, mf = (4, 2, 6, 8), 1.8, 0.02
+    U = gauge_field(dims, "haar", 41)
+    psi = gaussian_spinor(dims, 42, lead=(Ls,))
+    lat = L.lattice(dims, n5=Ls, bc=BC)
+    F = L.fields
+    g = F.gauge_to_device(U, lat, 0, 18)
+    if subset == L.LQCD_FULL:
+        fin = F.spinor_to_device(psi, lat, 0, L.LQCD_FULL)
+        expect = dwf.dirac(U, psi, M5, mf, BC, dagger)
+    else:
+        fin = F.spinor_to_device(to_cb(psi, 0), lat, 0, L.LQCD_EVEN)
+        expect = to_cb(dwf.schur(U, wilson.restrict(psi, 0), M5, mf, BC, dagger), 0)
+    got = {}
+    for prec in (0, DF):
+        op = L.operator(kind=L.LQCD_DWF, M5=M5, mf=mf, prec=prec, recon=18)
+        tmp = None if subset == L.LQCD_FULL else F.empty(L.lqcd_operator_workspace_bytes(lat, op, L.LQCD_EVEN))
+        out = F.empty(L.lqcd_spinor_bytes(lat, 0, subset))
+        L.lqcd_M(out, fin, g, lat, op, subset, dagger, tmp)
+        got[prec] = F.spinor_to_host(out, lat, 0, subset)
+    assert rel_l2(got[DF], expect) <= 1e-12
+    assert rel_l2(got[DF], got[0]) <= 1e-13
+
+
+def test_df_domain_wall_rejections(L):
+    """Double-float domain wall needs 18-real links and L_s dividing 32 (the
+    fused M5op^-1): other forms are rejected on the host, before any launch."""
+    dims = (4, 2, 2, 4)
+    F = L.fields
+    for Ls, recon in ((6, 18), (4, 12)):
+        lat = L.lattice(dims, n5=Ls, bc=BC)
+        op = L.operator(kind=L.LQCD_DWF, M5=1.8, mf=0.02, prec=DF, recon=recon)
+        g = F.empty(L.lqcd_gauge_bytes(lat, 0, recon))
+        fin = F.empty(L.lqcd_spinor_bytes(lat, 0, L.LQCD_FULL))
+        out = F.empty(L.lqcd_spinor_bytes(lat, 0, L.LQCD_FULL))
+        with pytest.raises(L.LqcdError):
+            L.lqcd_M(out, fin, g, lat, op, L.LQCD_FULL, 0, None)
+
+
+@pytest.mark.parametrize("Ls", [4, 6])
+def test_df_domain_wall_solve(L, Ls):
+    """lqcd_eo_solve on a domain-wall system with FP32 inner storage and
+    update_prec = LQCD_F64_DF: double-float reliable updates where L_s divides 32
+    (4), FP64 ones otherwise (6); the oracle's full-system residual of x meets
+    the tolerance either way."""
+    dims, M5, mf = (4, 4, 2, 8), 1.8, 0.05
+    U = gauge_field(dims, "haar", 51)
+    b = gaussian_spinor(dims, 52, lead=(Ls,))
+    lat = L.lattice(dims, n5=Ls, bc=BC)
+    op = L.operator(kind=L.LQCD_DWF, M5=M5, mf=mf)
+    F = L.fields
+    g64 = F.gauge_to_device(U, lat, 0, 18)
+    g32 = F.gauge_to_device(U, lat, 1, 12)
+    bd = F.spinor_to_device(b, lat, 0, L.LQCD_FULL)
+    prm = L.solver_params(tol=1e-10, maxiter=5000, sloppy_prec=1, sloppy_recon=12, delta=1e-3, update_prec=DF)
+    ws = F.empty(L.lqcd_eo_solve_workspace_bytes(lat, op, prm))
+    x = F.empty(L.lqcd_spinor_bytes(lat, 0, L.LQCD_FULL))
+    info = L.lqcd_eo_solve(x, bd, g64, g32, lat, op, prm, ws)
+    xh = F.spinor_to_host(x, lat, 0, L.LQCD_FULL)
+    res = np.linalg.norm(b - dwf.dirac(U, xh, M5, mf, BC)) / np.linalg.norm(b)
+    assert res <= 1e-10, res
+    assert info.true_rel_residual <= 1e-10
