@@ -17,11 +17,13 @@
 // factorisation still breaks down (linearly dependent columns) that step and
 // the next beta fall back to per-column (independent CG) coefficients.
 // With update_prec = LQCD_F64_DF the reliable updates' A X runs in double-float
-// arithmetic on the FP64 fields; the FP64 Gram matrices are always accumulated
-// in double-float arithmetic (k_gram): both FP64-accurate on the FP32 pipe.
+// arithmetic on the FP64 fields. The Gram matrices of FP64 fields are summed in
+// double-float arithmetic in the plain FP64 solve and in FP32 in a mixed one
+// (they steer the sloppy recurrence; convergence is a sum of squares).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "cg_engine.h"
 #include "cg_site.cuh"
@@ -282,9 +284,10 @@ template <> struct GramArith<double> {
 // columns write consecutive words), its stride padded by one against bank
 // conflicts between the two site lanes of a warp; SB sites per pass fit 40 KB
 // of shared memory for u and v together.
-template <int FU, int TT> struct GramShape {
+template <int FU, int TT, bool LOWP = false> struct GramShape {
   using TU = typename PrecTraits<FU>::real;
-  using S2 = typename GramArith<TU>::S2;
+  using TA = typename std::conditional<LOWP, float, TU>::type;  // arithmetic / staging type
+  using S2 = typename GramArith<TA>::S2;
   static constexpr int NC = 4 * TT;
   static constexpr int SSTR = 12 * NC + 1;
   static constexpr int SB0 = 40960 / (2 * SSTR * (int)sizeof(S2));
@@ -295,11 +298,14 @@ template <int FU, int TT> struct GramShape {
   static constexpr int SMEM = STAGE_BYTES > RED_BYTES ? STAGE_BYTES : RED_BYTES;
 };
 
-template <int FU, int TT>
-__global__ void __launch_bounds__(GramShape<FU, TT>::NTH) k_gram(const BlockArgs a) {
-  using Sh = GramShape<FU, TT>;
+// LOWP (FP64 operands of a mixed solve, whose Gram matrices only steer the
+// sloppy recurrence and test convergence): FP32 products and sums.
+template <int FU, int TT, bool LOWP = false>
+__global__ void __launch_bounds__(GramShape<FU, TT, LOWP>::NTH) k_gram(const BlockArgs a) {
+  using Sh = GramShape<FU, TT, LOWP>;
   using TU = typename Sh::TU;
-  using GA = GramArith<TU>;
+  using TA = typename Sh::TA;
+  using GA = GramArith<TA>;
   using A = typename GA::A;
   using S2 = typename Sh::S2;
   constexpr int SB = Sh::SB, NTH = Sh::NTH, SSTR = Sh::SSTR;
@@ -335,12 +341,12 @@ __global__ void __launch_bounds__(GramShape<FU, TT>::NTH) k_gram(const BlockArgs
         SpinorIO<FU>::load(a.v, a.g.sstride, j, y);
 #pragma unroll
         for (int k = 0; k < 12; k++) {
-          du[k * Sh::NC] = GA::stage(x.v[k].r, x.v[k].i);
-          dv[k * Sh::NC] = GA::stage(y.v[k].r, y.v[k].i);
+          du[k * Sh::NC] = GA::stage((TA)x.v[k].r, (TA)x.v[k].i);
+          dv[k * Sh::NC] = GA::stage((TA)y.v[k].r, (TA)y.v[k].i);
         }
       } else {
 #pragma unroll
-        for (int k = 0; k < 12; k++) du[k * Sh::NC] = dv[k * Sh::NC] = GA::stage(TU(0), TU(0));
+        for (int k = 0; k < 12; k++) du[k * Sh::NC] = dv[k * Sh::NC] = GA::stage(TA(0), TA(0));
       }
     }
     __syncthreads();
@@ -585,28 +591,28 @@ static BlockWorkspace block_carve(void* base, const Geom& g, int sloppy) {
 
 // One wave of resident blocks (every block makes the same number of passes, so
 // none runs alone at the end), at most GRAM_GRID (the partials' capacity).
-template <int FU, int TT>
+template <int FU, int TT, bool LOWP>
 static void launch_gram_tt(const BlockArgs& a, cudaStream_t s) {
-  using Sh = GramShape<FU, TT>;
+  using Sh = GramShape<FU, TT, LOWP>;
   static const int resident = [] {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram<FU, TT>, Sh::NTH, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram<FU, TT, LOWP>, Sh::NTH, 0);
     return std::max(1, sms * per_sm);
   }();
   const int64_t want = std::min<int64_t>(std::min<int64_t>(GRAM_GRID, resident), (a.g.Vh + Sh::SB - 1) / Sh::SB);
-  k_gram<FU, TT><<<(unsigned)std::max<int64_t>(1, want), Sh::NTH, 0, s>>>(a);
+  k_gram<FU, TT, LOWP><<<(unsigned)std::max<int64_t>(1, want), Sh::NTH, 0, s>>>(a);
 }
 
 // tile edge TT = ceil(N / 4): NT = ceil(N / TT) <= 4 tiles per dimension fill the 16 tile slots
-template <int FU>
+template <int FU, bool LOWP = false>
 static void launch_gram_t(const BlockArgs& a, cudaStream_t s) {
   const int tt = (a.N + 3) / 4;
-  if (tt <= 1) launch_gram_tt<FU, 1>(a, s);
-  else if (tt == 2) launch_gram_tt<FU, 2>(a, s);
-  else if (tt == 3) launch_gram_tt<FU, 3>(a, s);
-  else launch_gram_tt<FU, 4>(a, s);
+  if (tt <= 1) launch_gram_tt<FU, 1, LOWP>(a, s);
+  else if (tt == 2) launch_gram_tt<FU, 2, LOWP>(a, s);
+  else if (tt == 3) launch_gram_tt<FU, 3, LOWP>(a, s);
+  else launch_gram_tt<FU, 4, LOWP>(a, s);
 }
 
 struct BlockSolver : CgEngine {
@@ -632,7 +638,11 @@ struct BlockSolver : CgEngine {
   }
   int gram(int fu, int fv, const BlockArgs& a, cudaStream_t s) {
     // formats: FP64 x FP64, VF x VF, SF x SF
-    if (fu == LQCD_F64) launch_gram_t<LQCD_F64>(a, s);
+    // the FP64 residual's Gram in a mixed solve steers the sloppy recurrence and tests
+    // convergence (a sum of squares on the diagonal): FP32 arithmetic serves; the plain
+    // FP64 solve keeps double-float
+    if (fu == LQCD_F64 && sloppy != LQCD_F64) launch_gram_t<LQCD_F64, true>(a, s);
+    else if (fu == LQCD_F64) launch_gram_t<LQCD_F64>(a, s);
     else if (fu == LQCD_F32) launch_gram_t<LQCD_F32>(a, s);
     else launch_gram_t<LQCD_F16>(a, s);
     (void)fv;
