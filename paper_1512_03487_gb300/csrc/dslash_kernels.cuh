@@ -747,28 +747,28 @@ __device__ __forceinline__ void hop_body(const HopArgs& A) {
                     (T)A.m5_den_inv);
         if (live[s]) SpinorIO<P>::store(out, A.g.sstride, j[s], res);
       }
-      return;
-    }
-    T red[SPT];
+    } else {
+      T red[SPT];
 #pragma unroll
-    for (int s = 0; s < SPT; s++) {
-      red[s] = T(0);
-      if (!live[s]) continue;
-      Spinor<T> res;
-      hop_epilogue<P, DAG, EPI>(A.g, xb, j[s], c, acc[s], res);
-      if constexpr (RED == RED_CG_UPDATE) {
-        const int64_t ps = A.full ? parity * A.half_bytes : 0, vs = A.full ? parity * A.upd_half_bytes : 0;
-        const int64_t rs = A.full ? parity * A.upd_rs_half_bytes : 0;
-        red[s] = update_site_ap<vec_prec(P), P, rs_prec(P)>(A.g, j[s], A.red.sys[sys_of(j[s], A.red.nsys)].alpha,
-                                                            static_cast<const char*>(A.upd_p) + ps, res,
-                                                            static_cast<char*>(A.upd_xs) + vs,
-                                                            static_cast<char*>(A.upd_rs) + rs);
-      } else {
-        SpinorIO<P>::store(out, A.g.sstride, j[s], res);
-        if constexpr (RED == RED_NORM) red[s] = norm2_site(res);
+      for (int s = 0; s < SPT; s++) {
+        red[s] = T(0);
+        if (!live[s]) continue;
+        Spinor<T> res;
+        hop_epilogue<P, DAG, EPI>(A.g, xb, j[s], c, acc[s], res);
+        if constexpr (RED == RED_CG_UPDATE) {
+          const int64_t ps = A.full ? parity * A.half_bytes : 0, vs = A.full ? parity * A.upd_half_bytes : 0;
+          const int64_t rs = A.full ? parity * A.upd_rs_half_bytes : 0;
+          red[s] = update_site_ap<vec_prec(P), P, rs_prec(P)>(A.g, j[s], A.red.sys[sys_of(j[s], A.red.nsys)].alpha,
+                                                              static_cast<const char*>(A.upd_p) + ps, res,
+                                                              static_cast<char*>(A.upd_xs) + vs,
+                                                              static_cast<char*>(A.upd_rs) + rs);
+        } else {
+          SpinorIO<P>::store(out, A.g.sstride, j[s], res);
+          if constexpr (RED == RED_NORM) red[s] = norm2_site(res);
+        }
       }
+      if constexpr (RED != RED_NONE) block_reduce_finalize_n<BLOCK, SPT>(red, first, A.red);
     }
-    if constexpr (RED != RED_NONE) block_reduce_finalize_n<BLOCK, SPT>(red, first, A.red);
   }
 }
 
