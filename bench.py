@@ -931,7 +931,8 @@ def run_extras(L, F, flush, stream):
     out["hmc_16x4"] = hmc_bench(L, F, stream)
     out["multigrid_24x3x48_m0.01"] = mg_bench(L, F, flush, stream)
 
-    # uneven batch: 4 each of 8^4, 12^4, 16^4, 20^4, Haar links, m = 0.05, FP32-inner, one persistent launch per phase
+    # uneven batch: 4 each of 8^4, 12^4, 16^4, 20^4, Haar links, m = 0.05, FP32-inner, one persistent launch per
+    # phase, double-float reliable updates (the 16 sequential solves likewise)
     shapes = [(n_, n_, n_, n_) for n_ in (8, 12, 16, 20) for _ in range(4)]
     entries = []
     for k, dims in enumerate(shapes):
@@ -943,7 +944,7 @@ def run_extras(L, F, flush, stream):
                             x=F.empty(L.lqcd_spinor_bytes(lat, 0, 0)), b=F.spinor_to_device(bsrc, lat, 0, 0)))
     items = L.batch_items(entries)
     prm = L.solver_params(tol=1e-10, maxiter=5000, sloppy_prec=1, sloppy_recon=12, delta=DELTA_NORMAL_FP32,
-                          check_interval=64)
+                          check_interval=64, update_prec=L.LQCD_F64_DF)
     wsb = F.empty(L.lqcd_batch_cg_workspace_bytes(len(entries), items, 18, prm))
     L.lqcd_batch_cg_solve(len(entries), items, 18, prm, wsb)  # tunes the tile and grid, captures the graph
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count

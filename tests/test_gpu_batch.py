@@ -41,14 +41,16 @@ def _setup(L, shapes, masses, sloppy, recon_s):
     return entries, keep
 
 
-@pytest.mark.parametrize("sloppy,recon_s", [(0, 18), (1, 12), (2, 12)])
-def test_uneven_batch_reaches_tolerance(L, sloppy, recon_s):
+@pytest.mark.parametrize("sloppy,recon_s,update_prec", [(0, 18, 0), (1, 12, 0), (2, 12, 0), (1, 12, 3), (2, 12, 3)])
+def test_uneven_batch_reaches_tolerance(L, sloppy, recon_s, update_prec):
+    """FP64, FP32 and FP16 inner operators; reliable updates on the FP64 pipe or
+    in double-float arithmetic (update_prec 3)."""
     shapes = [(4, 4, 4, 4), (6, 6, 6, 6), (8, 4, 4, 8), (4, 4, 2, 2), (6, 6, 6, 6)]
     masses = [0.05, 0.05, 0.1, 0.2, 0.01]
     entries, keep = _setup(L, shapes, masses, sloppy, recon_s)
     items = L.batch_items(entries)
     prm = L.solver_params(tol=1e-10, maxiter=3000, sloppy_prec=sloppy, sloppy_recon=recon_s, delta=0.01,
-                          check_interval=32)
+                          check_interval=32, update_prec=update_prec)
     ws = L.fields.empty(L.lqcd_batch_cg_workspace_bytes(len(entries), items, 18, prm))
     infos = L.lqcd_batch_cg_solve(len(entries), items, 18, prm, ws)
     for e, (U, b, lat, dims, m), info in zip(entries, keep, infos):
