@@ -986,7 +986,7 @@ def run_extras(L, F, flush, stream):
         Y = F.empty(L.lqcd_spinor_bytes(lat, 0, 2))
         Fo = F.empty(L.lqcd_gauge_bytes(lat, 0, 18))
         prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=18, delta=DELTA_NORMAL_FP32,
-                              check_interval=64)
+                              check_interval=64, update_prec=L.LQCD_F64_DF)
         ws = F.empty(L.lqcd_cg_workspace_bytes(lat, op, prm, 2))
 
         def force_step():
@@ -1218,7 +1218,7 @@ def hmc_bench(L, F, stream, n_therm=12, n_meas=3):
     U = gauge_field(dims, "exp", config_seed(50, 0), eps=0.3)
     rng = make_rng(config_seed(50, 1))
     prm = L.solver_params(tol=1e-10, maxiter=20000, sloppy_prec=1, sloppy_recon=12, delta=DELTA_NORMAL_FP32,
-                          check_interval=64)
+                          check_interval=64, update_prec=L.LQCD_F64_DF)
     hp = L.hmc_params(beta, 1.0, 10, L.LQCD_MINNORM2, 1)
     Ud = F.gauge_to_device(U, lat, 0, 18)
     Uprev = torch.empty_like(Ud)
